@@ -1,0 +1,471 @@
+#!/usr/bin/env python3
+"""Benchmark of the CKKS hot path on GB300.
+
+Headline metric: negacyclic NTT limb-transforms per second at N = 2^15 on the
+paper's NTT workload (1024 instances x 8 RNS limbs; 60- and 50-bit primes),
+batched (one launch per direction for all 8192 limbs). A step is one forward
+and one inverse transform of the whole batch, in place, inputs resident in
+HBM (2 GiB per direction, far larger than the 129 MB L2, so no flush is
+needed). The same run also measures, as sub-results:
+  * the plain form (one launch per polynomial) and the CUDA-graph form;
+  * the naive radix-2 baseline of the paper (one launch per stage);
+  * mul-relin-rescale (MulLinRS) per second on the CKKS workload (N = 16384,
+    one 60-bit + six 50-bit data primes, 60-bit special prime, 64 ciphertext
+    pairs), batched versus one call per pair;
+  * the end-to-end NTT rate through host buffers (pinned host -> device,
+    forward, inverse, device -> host, every step);
+  * the register-resident butterfly probe (integer roof) and the roofline of
+    the forward transform kernel;
+  * the CPU oracle on a bounded sample (cpu_baseline).
+
+`--impl reference` times the CPU oracle alone on the same metric.
+Under torchrun each rank runs the full workload on its own GPU (independent
+replicas; the transform needs no communication) and rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NTT_LOG_N = 15
+NTT_LIMBS = 8
+NTT_INSTANCES = 1024
+MRR_N = 16384
+MRR_BITS = [60] + [50] * 6
+MRR_COUNT = 64
+METRIC = "NTT limbs/s at N=2^15 + HE mul-relin-rescale/s, batched vs plain; p99 latency"
+UNIT = "limb-NTT/s"
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle sample")
+    return ap.parse_args()
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _ntt_moduli(cpu_oracle: bool = False):
+    """Four 60-bit then four 50-bit primes = 1 mod 2N (the CPU legs take the
+    oracle's own prime search, the GPU leg the library's; both give the same
+    primes)."""
+    two_n = 2 << NTT_LOG_N
+    if cpu_oracle:
+        import oracle
+        return oracle.find_primes(60, two_n, NTT_LIMBS // 2) + oracle.find_primes(50, two_n, NTT_LIMBS // 2)
+    from paper_2109_14704_gb300 import he
+    return he.primes_generate(60, two_n, NTT_LIMBS // 2) + he.primes_generate(50, two_n, NTT_LIMBS // 2)
+
+
+# ----------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clock and throttle samples while the timed regions run."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "50"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 10:
+                continue
+            try:
+                rows.append({"sm": float(parts[1]), "max": float(parts[2]), "util": float(parts[4]),
+                             "hw": parts[6], "hw_th": parts[7], "sw_th": parts[8], "pcap": parts[9]})
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        loaded = [r for r in rows if r["util"] > 0] or rows
+        reasons = set()
+        for r in loaded:
+            for key, name in (("hw", "hw_slowdown"), ("hw_th", "hw_thermal_slowdown"),
+                              ("sw_th", "sw_thermal_slowdown"), ("pcap", "sw_power_cap")):
+                if r[key].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in loaded) if loaded else None,
+                "sm_max_mhz": max(r["max"] for r in loaded) if loaded else None,
+                "reasons": sorted(reasons), "samples": len(loaded)}
+
+
+# ---------------------------------------------------------- GPU timing
+
+def _time_steps(fn, steps, warmup, stream, barrier):
+    import torch
+    for _ in range(warmup):
+        fn()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(steps):
+        fn()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    return t0.elapsed_time(t1) / steps
+
+
+def run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+
+    from paper_2109_14704_gb300 import he
+    from paper_2109_14704_gb300.synth import Rng
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+        def barrier():
+            dist.barrier()
+
+        def max_over_ranks(x):
+            t = torch.tensor([x], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            return float(t.item())
+    else:
+        def barrier():
+            pass
+
+        def max_over_ranks(x):
+            return x
+
+    he.load()
+    stream = torch.cuda.current_stream()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    N = 1 << NTT_LOG_N
+    qs = _ntt_moduli()
+    tables = he.NttTables(N, qs)
+    r = Rng(1000 + rank)
+    host = np.stack([r.uniform_limbs(qs, N) for _ in range(NTT_INSTANCES)])
+    pinned = torch.from_numpy(host.view(np.int64)).pin_memory()
+    d = torch.empty(pinned.shape, dtype=torch.int64, device=dev)
+    d.copy_(pinned)
+    limbs_total = NTT_INSTANCES * NTT_LIMBS
+    bytes_per_launch = 16 * N * limbs_total          # read + write every word once
+
+    def step_batched():
+        he.ntt_fwd(d, N, NTT_LIMBS, NTT_INSTANCES, tables, stream=stream)
+        he.ntt_inv(d, N, NTT_LIMBS, NTT_INSTANCES, tables, stream=stream)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.2)
+    ms = _time_steps(step_batched, args.steps, args.warmup, stream, barrier)
+    ms = max_over_ranks(ms)
+
+    # per-kernel durations for the roofline (events on the launching stream)
+    fwd_ms, inv_ms = [], []
+    for _ in range(max(3, min(args.steps, 10))):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        he.ntt_fwd(d, N, NTT_LIMBS, NTT_INSTANCES, tables, stream=stream)
+        e[1].record(stream)
+        he.ntt_inv(d, N, NTT_LIMBS, NTT_INSTANCES, tables, stream=stream)
+        e[2].record(stream)
+        torch.cuda.synchronize()
+        fwd_ms.append(e[0].elapsed_time(e[1]))
+        inv_ms.append(e[1].elapsed_time(e[2]))
+    fwd = statistics.mean(fwd_ms)
+    inv = statistics.mean(inv_ms)
+
+    # CUDA-graph form of the batched step
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream(device=dev)
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        step_batched()
+        with torch.cuda.graph(g, stream=side):
+            he.ntt_fwd(d, N, NTT_LIMBS, NTT_INSTANCES, tables, stream=side)
+            he.ntt_inv(d, N, NTT_LIMBS, NTT_INSTANCES, tables, stream=side)
+    stream.wait_stream(side)
+    torch.cuda.synchronize()
+    ms_graph = _time_steps(g.replay, args.steps, args.warmup, stream, barrier)
+
+    # plain form: one launch per polynomial (8 limbs), as a per-polynomial API
+    per_poly = [d[p] for p in range(NTT_INSTANCES)]
+
+    def step_plain():
+        for t in per_poly:
+            he.ntt_fwd(t, N, NTT_LIMBS, 1, tables, stream=stream)
+        for t in per_poly:
+            he.ntt_inv(t, N, NTT_LIMBS, 1, tables, stream=stream)
+
+    ms_plain = _time_steps(step_plain, max(2, args.steps // 5), 1, stream, barrier)
+
+    # the paper's naive radix-2 baseline (one launch per stage)
+    def step_naive():
+        he.ntt_fwd_naive(d, N, NTT_LIMBS, NTT_INSTANCES, tables, stream=stream)
+        he.ntt_inv_naive(d, N, NTT_LIMBS, NTT_INSTANCES, tables, stream=stream)
+
+    ms_naive = _time_steps(step_naive, max(2, args.steps // 5), 1, stream, barrier)
+
+    # MulLinRS on the CKKS evaluation workload
+    data, P = he.chain_primes(MRR_N, MRR_BITS, 60)
+    ctx = he.Context(MRR_N, data, P)
+    L = len(data) - 1
+    rm = Rng(2000 + rank)
+    evk = np.stack([np.stack([rm.uniform_limbs(data + [P], MRR_N) for _ in range(2)]) for _ in range(len(data))])
+    key = he.RelinKey(ctx, evk)
+
+    def cts():
+        return np.stack([np.stack([rm.uniform_limbs(data, MRR_N) for _ in range(2)]) for _ in range(MRR_COUNT)])
+
+    ca = torch.from_numpy(cts().view(np.int64)).to(dev)
+    cb = torch.from_numpy(cts().view(np.int64)).to(dev)
+    out = torch.empty((MRR_COUNT, 2, L, MRR_N), dtype=torch.int64, device=dev)
+    scratch = torch.empty(ctx.mrr_scratch_bytes(L, MRR_COUNT) // 8, dtype=torch.int64, device=dev)
+
+    def mrr_batched():
+        he.mul_relin_rescale(out, ca, cb, MRR_COUNT, key, ctx, L, scratch, stream=stream)
+
+    ms_mrr = max_over_ranks(_time_steps(mrr_batched, args.steps, args.warmup, stream, barrier))
+    s1 = scratch[: ctx.mrr_scratch_bytes(L, 1) // 8]
+
+    def mrr_plain():
+        for c in range(MRR_COUNT):
+            he.mul_relin_rescale(out[c], ca[c], cb[c], 1, key, ctx, L, s1, stream=stream)
+
+    ms_mrr_plain = max_over_ranks(_time_steps(mrr_plain, max(2, args.steps // 5), 1, stream, barrier))
+
+    # end to end through host buffers: H2D, forward, inverse, D2H every step
+    back = torch.empty_like(pinned).pin_memory()
+
+    def step_e2e():
+        d.copy_(pinned, non_blocking=True)
+        he.ntt_fwd(d, N, NTT_LIMBS, NTT_INSTANCES, tables, stream=stream)
+        he.ntt_inv(d, N, NTT_LIMBS, NTT_INSTANCES, tables, stream=stream)
+        back.copy_(d, non_blocking=True)
+
+    ms_e2e = max_over_ranks(_time_steps(step_e2e, max(3, args.steps // 2), 1, stream, barrier))
+    clk = clocks.stop()
+    assert torch.equal(back, pinned), "round trip changed the data"
+
+    # integer roof: register-resident butterflies on every SM
+    sink = torch.empty(sms * 8 * 256, dtype=torch.int64, device=dev)
+    iters = 4096
+
+    def probe():
+        he.butterfly_probe(sink, sms * 8, 256, iters, stream=stream)
+
+    ms_probe = _time_steps(probe, 5, 2, stream, lambda: None)
+    bfly_rate = sms * 8 * 256 * 16 * iters / (ms_probe / 1e3)
+    bfly_per_launch = limbs_total * (N // 2) * NTT_LOG_N
+
+    peaks = _measured_peaks()
+    hbm_peak = peaks.get("hbm_gbs") or 6800.0
+    achieved_gbs = bytes_per_launch / (fwd / 1e3) / 1e9
+    achieved_bfly = bfly_per_launch / (fwd / 1e3)
+    frac_hbm = achieved_gbs / hbm_peak
+    frac_alu = achieved_bfly / bfly_rate
+    bound_alu = frac_alu >= frac_hbm
+    value = world * 2 * limbs_total / (ms / 1e3)
+    e2e_value = world * 2 * limbs_total / (ms_e2e / 1e3)
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u64",
+        "data": "synthetic: seeded uniform residues (SplitMix64), 60/50-bit NTT primes",
+        "config": {
+            "workload": "NTT N=2^15, 1024 instances x 8 RNS limbs (4 x 60-bit, 4 x 50-bit primes), "
+                        "forward + inverse per step, in place",
+            "N": N, "limbs": NTT_LIMBS, "instances": NTT_INSTANCES, "parallelism": f"replicas x{world}",
+            "l2": "inputs larger than L2 (2 GiB per direction)",
+        },
+        "ntt": {
+            "batched_limbs_per_s": value,
+            "graph_limbs_per_s": world * 2 * limbs_total / (ms_graph / 1e3),
+            "plain_limbs_per_s": world * 2 * limbs_total / (ms_plain / 1e3),
+            "naive_limbs_per_s": world * 2 * limbs_total / (ms_naive / 1e3),
+            "fwd_limbs_per_s": world * limbs_total / (fwd / 1e3),
+            "inv_limbs_per_s": world * limbs_total / (inv / 1e3),
+            "fwd_ms": fwd, "inv_ms": inv, "speedup_vs_naive": ms_naive / ms,
+        },
+        "mul_relin_rescale": {
+            "workload": "N=16384, data primes 60+6x50, special 60, 64 ciphertext pairs, level 6 -> 5",
+            "batched_per_s": world * MRR_COUNT / (ms_mrr / 1e3),
+            "plain_per_s": world * MRR_COUNT / (ms_mrr_plain / 1e3),
+            "ms_per_batch": ms_mrr,
+            "transforms_per_op": (L + 1) ** 2 + 5 * (L + 1) + 2,
+        },
+        "roofline": {
+            "kernel": "k_ntt forward, 2^12 words per CTA x cluster of 8",
+            "bound": "alu" if bound_alu else "hbm",
+            "achieved": achieved_bfly / 1e12 if bound_alu else achieved_gbs,
+            "peak": bfly_rate / 1e12 if bound_alu else hbm_peak,
+            "unit": "Tbutterfly/s" if bound_alu else "GB/s",
+            "frac": frac_alu if bound_alu else frac_hbm,
+            "traffic": None,
+            "hbm": {"achieved_gbs": achieved_gbs, "peak_gbs": hbm_peak, "frac": frac_hbm,
+                    "peak_source": "measured copy bandwidth" if peaks.get("hbm_gbs") else "fallback"},
+            "alu": {"achieved_tbfly": achieved_bfly / 1e12, "peak_tbfly": bfly_rate / 1e12, "frac": frac_alu,
+                    "peak_source": "register-resident butterfly probe, same run"},
+            "algorithmic_bytes_per_launch": bytes_per_launch,
+            "butterflies_per_launch": bfly_per_launch,
+        },
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": pinned.numel() * 8,
+                "d2h_bytes_per_step": back.numel() * 8},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def _measured_peaks() -> dict:
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+# ------------------------------------------------------------- CPU oracle
+
+def cpu_baseline(target_seconds: float, limbs: int | None = None) -> dict:
+    """The oracle's forward + inverse NTT at N = 2^15 on a bounded sample of
+    the workload's limbs, on all host cores."""
+    import numpy as np
+
+    import oracle
+    from paper_2109_14704_gb300.synth import Rng
+
+    N = 1 << NTT_LOG_N
+    qs = _ntt_moduli(cpu_oracle=True)
+    cores = os.cpu_count() or 1
+    x = np.stack([Rng(3000).uniform_limbs(qs, N)])
+    t = time.perf_counter()
+    y = oracle.ntt_fwd_many(x, qs, 1)                 # calibrate on one thread
+    oracle.ntt_inv_many(y, qs, 1)
+    per_transform = (time.perf_counter() - t) / (2 * NTT_LIMBS)
+    if limbs is None:
+        polys = max(1, int(target_seconds / (per_transform * 2 * NTT_LIMBS)))
+    else:
+        polys = max(1, limbs // NTT_LIMBS)
+    r = Rng(3001)
+    x = np.stack([r.uniform_limbs(qs, N) for _ in range(polys)])
+    t = time.perf_counter()
+    y = oracle.ntt_fwd_many(x, qs, cores)
+    z = oracle.ntt_inv_many(y, qs, cores)
+    wall = time.perf_counter() - t
+    assert np.array_equal(z, x)
+    transforms = 2 * polys * NTT_LIMBS
+    return {"value": transforms / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{polys} instances x {NTT_LIMBS} limbs at N=2^15, forward + inverse "
+                      f"({transforms} limb transforms, {wall:.1f} s wall, plain __int128 % oracle, "
+                      f"one host thread per (instance, limb) unit)"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    from paper_2109_14704_gb300.synth import Rng
+
+    N = 1 << NTT_LOG_N
+    qs = _ntt_moduli(cpu_oracle=True)
+    cores = os.cpu_count() or 1
+    polys = max(1, cores // NTT_LIMBS) * 2          # a bounded sample per step
+    r = Rng(4000)
+    x = np.stack([r.uniform_limbs(qs, N) for _ in range(polys)])
+
+    def step():
+        y = oracle.ntt_fwd_many(x, qs, cores)
+        oracle.ntt_inv_many(y, qs, cores)
+
+    for _ in range(args.warmup):
+        step()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    wall = (time.perf_counter() - t) / args.steps
+    transforms = 2 * polys * NTT_LIMBS
+    value = transforms / wall
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": "NTT N=2^15, 1024 instances x 8 RNS limbs (4 x 60-bit, 4 x 50-bit primes), "
+                               "forward + inverse per step, in place",
+                   "N": N, "limbs": NTT_LIMBS, "instances": NTT_INSTANCES, "parallelism": "host threads"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{polys} instances x {NTT_LIMBS} limbs per step (of 1024 x 8)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = _args()
+    rank, world, local = _dist()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,232 @@
+/*
+ * he.h -- C ABI of the GB300 CKKS hot-path library (libhe.so).
+ *
+ * The library implements the data-parallel evaluation path of CKKS as
+ * described in "Accelerating Encrypted Computing on Intel GPUs" (arXiv
+ * 2109.14704): the negacyclic NTT and inverse NTT over RNS limbs of 64-bit
+ * words (Sec. II-B, Sec. III-B, Algorithm 1), the NTT-domain dyadic product
+ * (Sec. II-B), and the evaluation routines Mul, Relin and RS (Sec. II-A),
+ * plus batched plans that run many polynomials or ciphertexts in one launch
+ * (Sec. III-B "parallelism of NTT for HE", Sec. III asynchronous pipeline).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Words.    Every coefficient is a uint64_t residue. Moduli are odd primes
+ *           q < 2^60 with q = 1 mod 2N (Sec. III-A-1 bounds them below 60
+ *           bits so that lazy reduction and the fused multiply-add never
+ *           overflow a 64-bit word).
+ * Layout.   Limb-major and contiguous: a polynomial with L limbs is
+ *           poly[l * N + i]; a ciphertext with n limbs and c components is
+ *           ct[(k * n + l) * N + i]. Device buffers must be 16-byte aligned.
+ * Domains.  Ciphertexts and keys are in the NTT domain, in the bit-reversed
+ *           evaluation order of he_ntt_fwd.
+ * Ranges.   Inputs must be canonical (in [0, q)); outputs are always
+ *           canonical. Lazy ranges never cross this interface.
+ * Memory.   Pointers named *_host are host memory; every other data pointer
+ *           is device memory owned by the caller. The library owns only the
+ *           opaque handles (tables, contexts, keys, plans), until *_destroy.
+ *           Scratch buffers are passed in by the caller; he_*_scratch_bytes
+ *           gives their size.
+ * Streams.  Work is enqueued on `stream` (a cudaStream_t; NULL is the legacy
+ *           default stream). Only *_create, *_upload and *_destroy
+ *           synchronise; no other call blocks the host (Sec. III: the host
+ *           synchronises only when results are read back).
+ * Errors.   Every call returns an he_status. Argument checks run on the host
+ *           before anything is enqueued and return HE_EINVAL without side
+ *           effects. A failed CUDA call returns HE_ECUDA; errors raised later
+ *           by enqueued work surface at the caller's next synchronisation.
+ *           he_last_error() gives a message for the calling thread's last
+ *           failure.
+ * Aliasing. Outputs must not overlap inputs unless a call says it works in
+ *           place.
+ */
+#ifndef HE_H
+#define HE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t he_status;
+enum {
+    HE_OK = 0,
+    HE_EINVAL = -1,        /* bad argument (size, modulus, pointer, level) */
+    HE_ENOMEM = -2,        /* device or host allocation failed             */
+    HE_ECUDA = -3,         /* a CUDA runtime call failed                   */
+    HE_EUNSUPPORTED = -4,  /* valid but not built (e.g. N outside 2^10..2^16) */
+    HE_ETIMEOUT = -5       /* a bounded device-side wait gave up           */
+};
+
+typedef struct CUstream_st *he_stream_t;          /* same type as cudaStream_t */
+typedef struct he_ntt_tables he_ntt_tables;       /* twiddles of K primes at one N */
+typedef struct he_context he_context;             /* modulus chain q_0..q_L, P   */
+typedef struct he_relin_key he_relin_key;         /* device copy of evk          */
+typedef struct he_plan he_plan;                   /* a batched, replayable launch */
+
+/* Message of the calling thread's last failed call ("" if none). Copies at
+ * most len - 1 bytes and a terminating NUL into buf. */
+he_status he_last_error(char *buf, size_t len);
+
+/* Library version as 0xMMmmpp. */
+uint32_t he_version(void);
+
+/* ---- parameters ------------------------------------------------------------ */
+
+/* The `count` largest primes q with exactly `bits` bits (2..60) and
+ * q = 1 mod two_n, skipping the `n_exclude` values in exclude_host, written in
+ * descending order to out_host. RNS moduli of Sec. II-B. Returns HE_EINVAL if
+ * fewer than `count` exist. Host only. */
+he_status he_primes_generate(uint32_t bits, uint64_t two_n, uint32_t count,
+                             const uint64_t *exclude_host, uint32_t n_exclude,
+                             uint64_t *out_host);
+
+/* Twiddle tables for `limbs` primes at degree N (a power of two in
+ * [2^10, 2^16]). For each prime q: psi = the smallest primitive 2N-th root of
+ * unity mod q (Sec. II-B names psi; the smallest is this library's choice),
+ * forward powers psi^brv(k) and inverse powers psi^-brv(k), k < N, each with
+ * its Shoup quotient floor(W 2^64 / q) (the W' of Algorithm 1), and N^-1.
+ * Synchronises. Device memory: 32 N bytes per prime. */
+he_status he_ntt_tables_create(uint32_t N, uint32_t limbs, const uint64_t *moduli_host,
+                               he_ntt_tables **out);
+he_status he_ntt_tables_destroy(he_ntt_tables *t);
+
+/* psi chosen for prime `index` of the tables (host read, for checking). */
+he_status he_ntt_tables_psi(const he_ntt_tables *t, uint32_t index, uint64_t *psi_out);
+
+/* ---- transforms and products (Sec. II-B, Sec. III-B) ------------------------- */
+
+/* Forward negacyclic NTT, in place, of `count` polynomials of `limbs` limbs
+ * each, stored back to back (poly[(p * limbs + l) * N + i]); limb l uses prime
+ * l of the tables, which must hold at least `limbs` primes equal to
+ * moduli_host[0..limbs-1] (checked on the host). Natural-order coefficients
+ * become evaluations in bit-reversed order:
+ *     out[i] = sum_j a_j psi^((2 brv(i) + 1) j) mod q.
+ * The psi twist of Sec. II-B is folded into the twiddles. */
+he_status he_ntt_fwd(uint64_t *poly, uint32_t N, uint32_t limbs, uint32_t count,
+                     const uint64_t *moduli_host, const he_ntt_tables *tw, he_stream_t stream);
+
+/* Inverse negacyclic NTT, in place, including the factor N^-1, so that
+ * he_ntt_inv(he_ntt_fwd(a)) = a exactly. Same layout and checks. */
+he_status he_ntt_inv(uint64_t *poly, uint32_t N, uint32_t limbs, uint32_t count,
+                     const uint64_t *moduli_host, const he_ntt_tables *tw, he_stream_t stream);
+
+/* The naive radix-2 transform of Sec. III-B (one launch per stage, every
+ * stage through global memory): the paper's baseline, kept for comparison.
+ * Same contract as he_ntt_fwd / he_ntt_inv. */
+he_status he_ntt_fwd_naive(uint64_t *poly, uint32_t N, uint32_t limbs, uint32_t count,
+                           const uint64_t *moduli_host, const he_ntt_tables *tw,
+                           he_stream_t stream);
+he_status he_ntt_inv_naive(uint64_t *poly, uint32_t N, uint32_t limbs, uint32_t count,
+                           const uint64_t *moduli_host, const he_ntt_tables *tw,
+                           he_stream_t stream);
+
+/* Dyadic product out[l][i] = a[l][i] * b[l][i] mod q_l for `count`
+ * polynomials of `limbs` limbs (Sec. II-B, the elementwise product of the
+ * convolution theorem). out may equal a or b. */
+he_status he_dyadic_mul(uint64_t *out, const uint64_t *a, const uint64_t *b, uint32_t N,
+                        uint32_t limbs, uint32_t count, const uint64_t *moduli_host,
+                        const he_ntt_tables *tw, he_stream_t stream);
+
+/* ---- CKKS evaluation (Sec. II-A) ------------------------------------------- */
+
+/* A modulus chain: n_data data primes q_0..q_L (L = n_data - 1, n_data <= 32)
+ * and one special prime P, all distinct, q < 2^60, q = 1 mod 2N. Builds the
+ * NTT tables of all n_data + 1 primes and the constants of key switching and
+ * rescaling. Synchronises. */
+he_status he_context_create(uint32_t N, uint32_t n_data, const uint64_t *data_moduli_host,
+                            uint64_t special_modulus, he_context **out);
+he_status he_context_destroy(he_context *ctx);
+
+/* Upload a relinearization key. evk_host is [n_data][2][n_data + 1][N] in the
+ * NTT domain: digit j, component k, limbs q_0..q_L then P; it must satisfy
+ * evk[j][0] + evk[j][1] s = e_j + [j = i] (P mod q_i) s^2 on limb q_i (and no
+ * s^2 term on P), i.e. one RNS digit per data prime and one special prime.
+ * The device copy stores each word with its Shoup quotient. Synchronises. */
+he_status he_relin_key_upload(const he_context *ctx, const uint64_t *evk_host,
+                              he_relin_key **out);
+he_status he_relin_key_destroy(he_relin_key *key);
+
+/* Mul (Sec. II-A): out3 = (a0 b0, a0 b1 + a1 b0, a1 b1) mod q_i for the
+ * level-l ciphertexts ct_a and ct_b ([2][l+1][N]); out3 is [3][l+1][N]. The
+ * middle term takes one reduction (the mad_mod of Sec. III-A-1). */
+he_status he_ct_mul(uint64_t *out3, const uint64_t *ct_a, const uint64_t *ct_b,
+                    const he_context *ctx, uint32_t level, he_stream_t stream);
+
+/* Relin (Sec. II-A): ct_out2 = (c0, c1) + round(P^-1 c[2] evk) mod q_l, with
+ * c[2] split into its RNS digits [c[2]]_{q_j} in [0, q_j) and the division by
+ * P rounded half up. ct_in3 is [3][l+1][N], ct_out2 is [2][l+1][N]. */
+size_t he_relin_scratch_bytes(const he_context *ctx, uint32_t level);
+he_status he_relin(uint64_t *ct_out2, const uint64_t *ct_in3, const he_relin_key *key,
+                   const he_context *ctx, uint32_t level, void *scratch, size_t scratch_bytes,
+                   he_stream_t stream);
+
+/* RS (Sec. II-A): ct_out = round(ct_in / q_l) mod q_0..q_{l-1}, rounded half
+ * up; ct_in is [2][l+1][N], ct_out is [2][l][N], level >= 1. */
+size_t he_rescale_scratch_bytes(const he_context *ctx, uint32_t level);
+he_status he_rescale(uint64_t *ct_out, const uint64_t *ct_in, const he_context *ctx,
+                     uint32_t level, void *scratch, size_t scratch_bytes, he_stream_t stream);
+
+/* MulLinRS (Sec. V-C): Mul, Relin and RS of `count` ciphertext pairs in one
+ * fused sequence of launches. ct_a, ct_b are [count][2][l+1][N]; ct_out is
+ * [count][2][l][N]. The two roundings (by P, then by q_l) stay separate, so
+ * the result equals he_rescale(he_relin(he_ct_mul(a, b))). */
+size_t he_mul_relin_rescale_scratch_bytes(const he_context *ctx, uint32_t level, uint32_t count);
+he_status he_mul_relin_rescale(uint64_t *ct_out, const uint64_t *ct_a, const uint64_t *ct_b,
+                               uint32_t count, const he_relin_key *key, const he_context *ctx,
+                               uint32_t level, void *scratch, size_t scratch_bytes,
+                               he_stream_t stream);
+
+/* ---- batched plans (Sec. III-B parallelism over limbs and instances) -------- */
+
+/* One polynomial of a batched NTT: `limbs` limbs of degree N at `data`
+ * (device), limb l using prime (first_prime + l) of `tables`. */
+typedef struct he_poly_desc {
+    uint64_t *data;
+    const he_ntt_tables *tables;
+    uint32_t N;
+    uint32_t limbs;
+    uint32_t first_prime;
+    uint32_t reserved;
+} he_poly_desc;
+
+/* Kernel shape of a plan for one N: local block of 2^log_block words per
+ * CTA (the rest of the transform is split over a cluster of N / 2^log_block
+ * CTAs exchanging through distributed shared memory). 0 = default. */
+typedef struct he_ntt_shape {
+    uint32_t N;
+    uint32_t log_block;
+} he_ntt_shape;
+
+/* A plan that transforms all `count` polynomials (any mix of N and limb
+ * counts) with one launch per direction: a persistent kernel driven by a
+ * device-resident work list. Allocates the work list and synchronises;
+ * execution allocates nothing and can be captured in a CUDA graph. `shapes`
+ * (n_shapes entries, may be NULL) overrides the default kernel shape per N,
+ * e.g. with choices from the autotuner. */
+he_status he_ntt_plan_create(const he_poly_desc *descs_host, uint32_t count,
+                             const he_ntt_shape *shapes_host, uint32_t n_shapes,
+                             he_plan **out);
+he_status he_ntt_plan_fwd(const he_plan *plan, he_stream_t stream);
+he_status he_ntt_plan_inv(const he_plan *plan, he_stream_t stream);
+he_status he_plan_destroy(he_plan *plan);
+
+/* Number of kernel launches one execution of the plan enqueues. */
+uint32_t he_plan_launches(const he_plan *plan);
+
+/* ---- measurement -------------------------------------------------------------- */
+
+/* Integer-throughput probe: blocks x threads threads each run 16 * iters
+ * Harvey butterflies (Algorithm 1, 60-bit prime) entirely in registers and
+ * write one word to sink[blocks * threads] (device). Timing the launch gives
+ * the butterfly rate the integer pipes sustain with no memory traffic, the
+ * compute roof against which the transforms are reported. */
+he_status he_butterfly_probe(uint64_t *sink, uint32_t blocks, uint32_t threads, uint32_t iters,
+                             he_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HE_H */

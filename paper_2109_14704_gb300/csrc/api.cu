@@ -1,0 +1,849 @@
+// api.cu -- host side of libhe.so: the C ABI declared in include/he.h.
+//
+// Parameter generation (primes, psi, twiddles, Shoup and Barrett constants)
+// runs on the host with 128-bit integer arithmetic; everything on the data
+// path runs in the CUDA kernels of kernels.cuh. Argument checks happen before
+// anything is enqueued.
+#define HE_MISC_KERNELS 1
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/he.h"
+#include "kernels.cuh"
+
+using he::u32;
+using he::u64;
+typedef unsigned __int128 u128;
+
+// ------------------------------------------------------------------ errors
+
+static thread_local std::string g_last_error;
+
+static he_status fail(he_status code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+static he_status cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(HE_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define HE_CUDA(call)                                                                              \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);                                        \
+    } while (0)
+
+extern "C" he_status he_last_error(char *buf, size_t len)
+{
+    if (!buf || len == 0) return HE_EINVAL;
+    size_t n = std::min(len - 1, g_last_error.size());
+    memcpy(buf, g_last_error.data(), n);
+    buf[n] = 0;
+    return HE_OK;
+}
+
+extern "C" uint32_t he_version(void) { return 0x000100; }
+
+// --------------------------------------------------------- host arithmetic
+
+static u64 h_mul(u64 a, u64 b, u64 m) { return (u64)((u128)a * b % m); }
+
+static u64 h_pow(u64 a, u64 e, u64 m)
+{
+    u64 r = 1 % m;
+    a %= m;
+    for (; e; e >>= 1) {
+        if (e & 1) r = h_mul(r, a, m);
+        a = h_mul(a, a, m);
+    }
+    return r;
+}
+
+static u64 h_inv(u64 a, u64 p) { return h_pow(a % p, p - 2, p); }  // p prime
+
+static u64 shoup(u64 w, u64 p) { return (u64)(((u128)w << 64) / p); }
+
+static int bit_length(u64 x)
+{
+    int b = 0;
+    while (x) {
+        b++;
+        x >>= 1;
+    }
+    return b;
+}
+
+// Miller-Rabin with the first twelve primes as witnesses: exact for every
+// 64-bit input (Sorenson and Webster, 2015).
+static bool h_is_prime(u64 n)
+{
+    static const u64 W[12] = {2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37};
+    if (n < 2) return false;
+    for (u64 w : W)
+        if (n % w == 0) return n == w;
+    u64 d = n - 1;
+    int r = 0;
+    while (!(d & 1)) {
+        d >>= 1;
+        r++;
+    }
+    for (u64 w : W) {
+        u64 x = h_pow(w, d, n);
+        if (x == 1 || x == n - 1) continue;
+        bool witness = true;
+        for (int i = 1; i < r && witness; i++) {
+            x = h_mul(x, x, n);
+            if (x == n - 1) witness = false;
+        }
+        if (witness) return false;
+    }
+    return true;
+}
+
+// The smallest primitive 2N-th root of unity mod q (q prime, 2N | q - 1).
+// Odd powers of one primitive root c = g^((q-1)/2N), g a non-residue, run
+// over all of them.
+static u64 smallest_psi(u64 q, u32 N)
+{
+    u64 g = 2;
+    while (h_pow(g, (q - 1) / 2, q) != q - 1) g++;
+    const u64 c = h_pow(g, (q - 1) / (2 * (u64)N), q);
+    const u64 c2 = h_mul(c, c, q);
+    u64 best = c;
+    for (u64 k = 1, x = c; k < N; k++) {
+        x = h_mul(x, c2, q);
+        if (x < best) best = x;
+    }
+    return best;
+}
+
+static u32 bit_reverse(u32 x, int bits)
+{
+    u32 r = 0;
+    for (int i = 0; i < bits; i++, x >>= 1) r = (r << 1) | (x & 1);
+    return r;
+}
+
+static int log2_exact(u64 n)
+{
+    if (n == 0 || (n & (n - 1))) return -1;
+    int l = 0;
+    while ((1ull << l) < n) l++;
+    return l;
+}
+
+extern "C" he_status he_primes_generate(uint32_t bits, uint64_t two_n, uint32_t count,
+                                        const uint64_t *exclude_host, uint32_t n_exclude,
+                                        uint64_t *out_host)
+{
+    if (bits < 2 || bits > 60) return fail(HE_EINVAL, "bits must be in [2, 60], got %u", bits);
+    if (two_n == 0) return fail(HE_EINVAL, "two_n must be positive");
+    if (count && !out_host) return fail(HE_EINVAL, "out_host is NULL");
+    if (n_exclude && !exclude_host) return fail(HE_EINVAL, "exclude_host is NULL");
+    const u64 top = (1ull << bits) - 1, low = 1ull << (bits - 1);
+    u64 q = (top - 1) / two_n * two_n + 1;
+    u32 got = 0;
+    while (got < count && q >= low && q > two_n) {
+        bool skip = false;
+        for (u32 i = 0; i < n_exclude; i++) skip |= exclude_host[i] == q;
+        if (!skip && h_is_prime(q)) out_host[got++] = q;
+        q -= two_n;
+    }
+    if (got < count) return fail(HE_EINVAL, "only %u primes of %u bits = 1 mod %llu", got, bits,
+                                 (unsigned long long)two_n);
+    return HE_OK;
+}
+
+// ------------------------------------------------------------------ tables
+
+struct he_ntt_tables {
+    u32 N = 0;
+    int log_n = 0;
+    u32 K = 0;
+    std::vector<u64> moduli, psi;
+    ulonglong2 *d_fwd = nullptr;  // [K][N] (W, W')
+    ulonglong2 *d_inv = nullptr;
+    he::PrimeConst *d_pc = nullptr;
+};
+
+static he_status check_modulus(u64 q, u32 N)
+{
+    if (q < 3 || q >= (1ull << 60)) return fail(HE_EINVAL, "modulus %llu outside [3, 2^60)", (unsigned long long)q);
+    if ((q - 1) % (2ull * N)) return fail(HE_EINVAL, "modulus %llu is not 1 mod 2N (N = %u)", (unsigned long long)q, N);
+    if (!h_is_prime(q)) return fail(HE_EINVAL, "modulus %llu is not prime", (unsigned long long)q);
+    return HE_OK;
+}
+
+static he_status check_degree(u32 N, int *log_n)
+{
+    int l = log2_exact(N);
+    if (l < 0) return fail(HE_EINVAL, "N = %u is not a power of two", N);
+    if (l < 10 || l > 16) return fail(HE_EUNSUPPORTED, "N = %u outside [2^10, 2^16]", N);
+    if (!he::degree_ops(l)) return fail(HE_EUNSUPPORTED, "no kernels built for N = %u", N);
+    *log_n = l;
+    return HE_OK;
+}
+
+static void free_tables(he_ntt_tables *t)
+{
+    if (!t) return;
+    cudaFree(t->d_fwd);
+    cudaFree(t->d_inv);
+    cudaFree(t->d_pc);
+    delete t;
+}
+
+extern "C" he_status he_ntt_tables_create(uint32_t N, uint32_t limbs, const uint64_t *moduli_host,
+                                          he_ntt_tables **out)
+{
+    if (!out) return fail(HE_EINVAL, "out is NULL");
+    *out = nullptr;
+    int log_n;
+    if (he_status s = check_degree(N, &log_n)) return s;
+    if (limbs == 0 || !moduli_host) return fail(HE_EINVAL, "need at least one modulus");
+    for (u32 l = 0; l < limbs; l++)
+        if (he_status s = check_modulus(moduli_host[l], N)) return s;
+
+    he_ntt_tables *t = new he_ntt_tables;
+    t->N = N;
+    t->log_n = log_n;
+    t->K = limbs;
+    t->moduli.assign(moduli_host, moduli_host + limbs);
+    std::vector<ulonglong2> fwd((size_t)limbs * N), inv((size_t)limbs * N);
+    std::vector<he::PrimeConst> pcs(limbs);
+    std::vector<u64> pw(N), pwi(N);
+    for (u32 l = 0; l < limbs; l++) {
+        const u64 q = moduli_host[l];
+        const u64 psi = smallest_psi(q, N), psi_inv = h_inv(psi, q);
+        t->psi.push_back(psi);
+        pw[0] = pwi[0] = 1;
+        for (u32 i = 1; i < N; i++) {
+            pw[i] = h_mul(pw[i - 1], psi, q);
+            pwi[i] = h_mul(pwi[i - 1], psi_inv, q);
+        }
+        for (u32 k = 0; k < N; k++) {
+            const u64 w = pw[bit_reverse(k, log_n)], wi = pwi[bit_reverse(k, log_n)];
+            fwd[(size_t)l * N + k] = make_ulonglong2(w, shoup(w, q));
+            inv[(size_t)l * N + k] = make_ulonglong2(wi, shoup(wi, q));
+        }
+        he::PrimeConst &c = pcs[l];
+        memset(&c, 0, sizeof c);
+        c.p = q;
+        c.two_p = 2 * q;
+        c.bits = (u32)bit_length(q);
+        c.mu = (u64)(((u128)1 << (2 * c.bits + 2)) / q);
+        c.ninv = h_inv(N, q);
+        c.ninv_sh = shoup(c.ninv, q);
+        c.w1ninv = h_mul(inv[(size_t)l * N + 1].x, c.ninv, q);
+        c.w1ninv_sh = shoup(c.w1ninv, q);
+    }
+    cudaError_t e;
+    if ((e = cudaMalloc(&t->d_fwd, fwd.size() * sizeof(ulonglong2))) != cudaSuccess ||
+        (e = cudaMalloc(&t->d_inv, inv.size() * sizeof(ulonglong2))) != cudaSuccess ||
+        (e = cudaMalloc(&t->d_pc, pcs.size() * sizeof(he::PrimeConst))) != cudaSuccess) {
+        free_tables(t);
+        return fail(HE_ENOMEM, "twiddle tables: %s", cudaGetErrorString(e));
+    }
+    if ((e = cudaMemcpy(t->d_fwd, fwd.data(), fwd.size() * sizeof(ulonglong2), cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(t->d_inv, inv.data(), inv.size() * sizeof(ulonglong2), cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(t->d_pc, pcs.data(), pcs.size() * sizeof(he::PrimeConst), cudaMemcpyHostToDevice))) {
+        free_tables(t);
+        return cuda_fail(e, "upload twiddle tables");
+    }
+    *out = t;
+    return HE_OK;
+}
+
+extern "C" he_status he_ntt_tables_destroy(he_ntt_tables *t)
+{
+    if (t) {
+        cudaDeviceSynchronize();
+        free_tables(t);
+    }
+    return HE_OK;
+}
+
+extern "C" he_status he_ntt_tables_psi(const he_ntt_tables *t, uint32_t index, uint64_t *psi_out)
+{
+    if (!t || !psi_out || index >= t->K) return fail(HE_EINVAL, "bad tables, index or output");
+    *psi_out = t->psi[index];
+    return HE_OK;
+}
+
+// ------------------------------------------------------------ transforms
+
+static he_status check_poly_args(const void *poly, uint32_t N, uint32_t limbs, const uint64_t *moduli_host,
+                                 const he_ntt_tables *tw, int *log_n)
+{
+    if (!tw) return fail(HE_EINVAL, "tables are NULL");
+    if (he_status s = check_degree(N, log_n)) return s;
+    if (tw->N != N) return fail(HE_EINVAL, "tables are for N = %u, not %u", tw->N, N);
+    if (limbs > tw->K) return fail(HE_EINVAL, "%u limbs but the tables hold %u primes", limbs, tw->K);
+    if (limbs && !moduli_host) return fail(HE_EINVAL, "moduli_host is NULL");
+    for (u32 l = 0; l < limbs; l++)
+        if (moduli_host[l] != tw->moduli[l])
+            return fail(HE_EINVAL, "modulus %u (%llu) differs from the tables' prime (%llu)", l,
+                        (unsigned long long)moduli_host[l], (unsigned long long)tw->moduli[l]);
+    if (!poly) return fail(HE_EINVAL, "data pointer is NULL");
+    if ((uintptr_t)poly & 15) return fail(HE_EINVAL, "data pointer is not 16-byte aligned");
+    return HE_OK;
+}
+
+static he::NttLaunch uniform_launch(uint64_t *poly, uint32_t limbs, uint32_t count, const he_ntt_tables *tw)
+{
+    he::NttLaunch a = {};
+    a.base = poly;
+    a.limbs = limbs;
+    a.first_prime = 0;
+    a.items = limbs * count;
+    a.tw_fwd = tw->d_fwd;
+    a.tw_inv = tw->d_inv;
+    a.pc = tw->d_pc;
+    a.jobs = nullptr;
+    return a;
+}
+
+static he_status ntt_common(uint64_t *poly, uint32_t N, uint32_t limbs, uint32_t count,
+                            const uint64_t *moduli_host, const he_ntt_tables *tw, he_stream_t stream, bool inv)
+{
+    int log_n;
+    if (he_status s = check_poly_args(poly, N, limbs, moduli_host, tw, &log_n)) return s;
+    if ((u64)limbs * count == 0) return HE_OK;
+    if ((u64)limbs * count * (N / 4096 + 1) > 0x7fffffffull) return fail(HE_EINVAL, "batch too large");
+    const he::DegreeOps *ops = he::degree_ops(log_n);
+    HE_CUDA(ops->ntt(uniform_launch(poly, limbs, count, tw), 0, inv, (cudaStream_t)stream));
+    return HE_OK;
+}
+
+extern "C" he_status he_ntt_fwd(uint64_t *poly, uint32_t N, uint32_t limbs, uint32_t count,
+                                const uint64_t *moduli_host, const he_ntt_tables *tw, he_stream_t stream)
+{
+    return ntt_common(poly, N, limbs, count, moduli_host, tw, stream, false);
+}
+
+extern "C" he_status he_ntt_inv(uint64_t *poly, uint32_t N, uint32_t limbs, uint32_t count,
+                                const uint64_t *moduli_host, const he_ntt_tables *tw, he_stream_t stream)
+{
+    return ntt_common(poly, N, limbs, count, moduli_host, tw, stream, true);
+}
+
+static he_status naive_common(uint64_t *poly, uint32_t N, uint32_t limbs, uint32_t count,
+                              const uint64_t *moduli_host, const he_ntt_tables *tw, he_stream_t stream, bool inv)
+{
+    int log_n;
+    if (he_status s = check_poly_args(poly, N, limbs, moduli_host, tw, &log_n)) return s;
+    if ((u64)limbs * count == 0) return HE_OK;
+    const he::NttLaunch a = uniform_launch(poly, limbs, count, tw);
+    const u64 bfly = (u64)a.items * (N / 2);
+    const u32 threads = 256;
+    const u32 grid = (u32)((bfly + threads - 1) / threads);
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int k = 0; k < log_n; k++) {
+        const u32 S = inv ? (u32)(log_n - 1 - k) : (u32)k;
+        he::k_ntt_naive_stage<<<grid, threads, 0, s>>>(a, (u32)log_n, S, inv);
+    }
+    if (!inv) {
+        const u32 g2 = (u32)(((u64)a.items * N + threads - 1) / threads);
+        he::k_ntt_naive_final<<<g2, threads, 0, s>>>(a, (u32)log_n);
+    }
+    HE_CUDA(cudaGetLastError());
+    return HE_OK;
+}
+
+extern "C" he_status he_ntt_fwd_naive(uint64_t *poly, uint32_t N, uint32_t limbs, uint32_t count,
+                                      const uint64_t *moduli_host, const he_ntt_tables *tw, he_stream_t stream)
+{
+    return naive_common(poly, N, limbs, count, moduli_host, tw, stream, false);
+}
+
+extern "C" he_status he_ntt_inv_naive(uint64_t *poly, uint32_t N, uint32_t limbs, uint32_t count,
+                                      const uint64_t *moduli_host, const he_ntt_tables *tw, he_stream_t stream)
+{
+    return naive_common(poly, N, limbs, count, moduli_host, tw, stream, true);
+}
+
+static int g_num_sms = 0;
+
+static int num_sms()
+{
+    if (!g_num_sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) g_num_sms = 152;
+    }
+    return g_num_sms;
+}
+
+static u32 stream_grid(u64 work_items, u32 threads)
+{
+    const u64 want = (work_items + threads - 1) / threads;
+    const u64 cap = (u64)num_sms() * 8;
+    return (u32)std::max<u64>(1, std::min(want, cap));
+}
+
+extern "C" he_status he_dyadic_mul(uint64_t *out, const uint64_t *a, const uint64_t *b, uint32_t N,
+                                   uint32_t limbs, uint32_t count, const uint64_t *moduli_host,
+                                   const he_ntt_tables *tw, he_stream_t stream)
+{
+    int log_n;
+    if (he_status s = check_poly_args(out, N, limbs, moduli_host, tw, &log_n)) return s;
+    if (!a || !b || ((uintptr_t)a & 15) || ((uintptr_t)b & 15))
+        return fail(HE_EINVAL, "inputs must be non-NULL and 16-byte aligned");
+    const u64 items = (u64)limbs * count;
+    if (!items) return HE_OK;
+    he::k_dyadic<<<stream_grid(items * N / 2, 256), 256, 0, (cudaStream_t)stream>>>(
+        out, a, b, (u32)log_n, (u32)items, limbs, 0, tw->d_pc);
+    HE_CUDA(cudaGetLastError());
+    return HE_OK;
+}
+
+// ----------------------------------------------------------------- context
+
+struct he_context {
+    u32 N = 0;
+    int log_n = 0;
+    u32 n_data = 0;
+    std::vector<u64> data;
+    u64 P = 0;
+    he_ntt_tables *tables = nullptr;   // primes q_0..q_L, P
+    u64 *d_cst = nullptr;
+};
+
+struct he_relin_key {
+    const he_context *ctx = nullptr;
+    ulonglong2 *d_evk = nullptr;
+};
+
+extern "C" he_status he_context_create(uint32_t N, uint32_t n_data, const uint64_t *data_moduli_host,
+                                       uint64_t special_modulus, he_context **out)
+{
+    if (!out) return fail(HE_EINVAL, "out is NULL");
+    *out = nullptr;
+    int log_n;
+    if (he_status s = check_degree(N, &log_n)) return s;
+    if (n_data < 1 || n_data > 32) return fail(HE_EINVAL, "n_data must be in [1, 32], got %u", n_data);
+    if (!data_moduli_host) return fail(HE_EINVAL, "data_moduli_host is NULL");
+    std::vector<u64> all(data_moduli_host, data_moduli_host + n_data);
+    all.push_back(special_modulus);
+    for (size_t i = 0; i < all.size(); i++) {
+        if (he_status s = check_modulus(all[i], N)) return s;
+        // key switching reduces words below 2^60 modulo every prime with one
+        // Barrett step, which needs q >= 2^31
+        if (all[i] < (1ull << 30)) return fail(HE_EINVAL, "modulus %llu has fewer than 31 bits", (unsigned long long)all[i]);
+        for (size_t j = 0; j < i; j++)
+            if (all[j] == all[i]) return fail(HE_EINVAL, "modulus %llu appears twice", (unsigned long long)all[i]);
+    }
+    he_context *c = new he_context;
+    c->N = N;
+    c->log_n = log_n;
+    c->n_data = n_data;
+    c->data.assign(data_moduli_host, data_moduli_host + n_data);
+    c->P = special_modulus;
+    if (he_status s = he_ntt_tables_create(N, n_data + 1, all.data(), &c->tables)) {
+        delete c;
+        return s;
+    }
+    std::vector<u64> cst(3 * (size_t)n_data + 3 * (size_t)n_data * n_data, 0);
+    for (u32 i = 0; i < n_data; i++) {
+        const u64 q = all[i];
+        cst[3 * i + 0] = h_inv(special_modulus % q, q);
+        cst[3 * i + 1] = shoup(cst[3 * i + 0], q);
+        cst[3 * i + 2] = special_modulus % q;
+    }
+    for (u32 l = 1; l < n_data; l++)
+        for (u32 i = 0; i < l; i++) {
+            const u64 q = all[i], ql = all[l];
+            u64 *d = &cst[3 * n_data + 3 * ((size_t)l * n_data + i)];
+            d[0] = h_inv(ql % q, q);
+            d[1] = shoup(d[0], q);
+            d[2] = ql % q;
+        }
+    cudaError_t e = cudaMalloc(&c->d_cst, cst.size() * sizeof(u64));
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_cst, cst.data(), cst.size() * sizeof(u64), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        he_ntt_tables_destroy(c->tables);
+        cudaFree(c->d_cst);
+        delete c;
+        return cuda_fail(e, "context constants");
+    }
+    *out = c;
+    return HE_OK;
+}
+
+extern "C" he_status he_context_destroy(he_context *ctx)
+{
+    if (ctx) {
+        cudaDeviceSynchronize();
+        he_ntt_tables_destroy(ctx->tables);
+        cudaFree(ctx->d_cst);
+        delete ctx;
+    }
+    return HE_OK;
+}
+
+extern "C" he_status he_relin_key_upload(const he_context *ctx, const uint64_t *evk_host, he_relin_key **out)
+{
+    if (!out) return fail(HE_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!ctx || !evk_host) return fail(HE_EINVAL, "context or key is NULL");
+    const u32 nd = ctx->n_data, N = ctx->N;
+    const size_t words = (size_t)nd * 2 * (nd + 1) * N;
+    std::vector<ulonglong2> dev(words);
+    for (u32 j = 0; j < nd; j++)
+        for (u32 k = 0; k < 2; k++)
+            for (u32 t = 0; t <= nd; t++) {
+                const u64 q = ctx->tables->moduli[t];
+                const size_t base = (((size_t)j * 2 + k) * (nd + 1) + t) * N;
+                for (u32 i = 0; i < N; i++) {
+                    const u64 w = evk_host[base + i];
+                    if (w >= q) return fail(HE_EINVAL, "key word %zu is not reduced mod its prime", base + i);
+                    dev[base + i] = make_ulonglong2(w, shoup(w, q));
+                }
+            }
+    he_relin_key *key = new he_relin_key;
+    key->ctx = ctx;
+    cudaError_t e = cudaMalloc(&key->d_evk, words * sizeof(ulonglong2));
+    if (e == cudaSuccess) e = cudaMemcpy(key->d_evk, dev.data(), words * sizeof(ulonglong2), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(key->d_evk);
+        delete key;
+        return fail(e == cudaErrorMemoryAllocation ? HE_ENOMEM : HE_ECUDA, "relin key upload: %s",
+                    cudaGetErrorString(e));
+    }
+    *out = key;
+    return HE_OK;
+}
+
+extern "C" he_status he_relin_key_destroy(he_relin_key *key)
+{
+    if (key) {
+        cudaDeviceSynchronize();
+        cudaFree(key->d_evk);
+        delete key;
+    }
+    return HE_OK;
+}
+
+static he::DevCtx dev_ctx(const he_context *c)
+{
+    he::DevCtx d;
+    d.tw_fwd = c->tables->d_fwd;
+    d.tw_inv = c->tables->d_inv;
+    d.pc = c->tables->d_pc;
+    d.cst = c->d_cst;
+    d.N = c->N;
+    d.n_data = c->n_data;
+    return d;
+}
+
+static he_status check_ptr(const void *p, const char *name)
+{
+    if (!p) return fail(HE_EINVAL, "%s is NULL", name);
+    if ((uintptr_t)p & 15) return fail(HE_EINVAL, "%s is not 16-byte aligned", name);
+    return HE_OK;
+}
+
+static he_status check_level(const he_context *ctx, uint32_t level, bool need_rescale)
+{
+    if (!ctx) return fail(HE_EINVAL, "context is NULL");
+    if (level >= ctx->n_data) return fail(HE_EINVAL, "level %u >= number of data primes %u", level, ctx->n_data);
+    if (need_rescale && level < 1) return fail(HE_EINVAL, "rescale needs level >= 1");
+    return HE_OK;
+}
+
+extern "C" he_status he_ct_mul(uint64_t *out3, const uint64_t *ct_a, const uint64_t *ct_b, const he_context *ctx,
+                               uint32_t level, he_stream_t stream)
+{
+    if (he_status s = check_level(ctx, level, false)) return s;
+    if (he_status s = check_ptr(out3, "out3")) return s;
+    if (he_status s = check_ptr(ct_a, "ct_a")) return s;
+    if (he_status s = check_ptr(ct_b, "ct_b")) return s;
+    const u32 n = level + 1;
+    he::k_tensor<<<stream_grid((u64)n * ctx->N / 2, 256), 256, 0, (cudaStream_t)stream>>>(
+        out3, ct_a, ct_b, (u32)ctx->log_n, n, 1, ctx->tables->d_pc);
+    HE_CUDA(cudaGetLastError());
+    return HE_OK;
+}
+
+// Scratch of key switching and rescale, in words per ciphertext.
+static size_t relin_words(const he_context *c, u32 n) { return (size_t)(3 * n + 2) * c->N; }
+static size_t rescale_words(const he_context *c) { return (size_t)2 * c->N; }
+static size_t mrr_words(const he_context *c, u32 n) { return (size_t)(3 * n + 4) * c->N; }
+
+extern "C" size_t he_relin_scratch_bytes(const he_context *ctx, uint32_t level)
+{
+    return ctx ? relin_words(ctx, level + 1) * 8 : 0;
+}
+
+extern "C" size_t he_rescale_scratch_bytes(const he_context *ctx, uint32_t level)
+{
+    (void)level;
+    return ctx ? rescale_words(ctx) * 8 : 0;
+}
+
+extern "C" size_t he_mul_relin_rescale_scratch_bytes(const he_context *ctx, uint32_t level, uint32_t count)
+{
+    return ctx ? mrr_words(ctx, level + 1) * 8 * count : 0;
+}
+
+static he_status run_eval(const he_context *ctx, he::EvalKernel k, const he::EvalArgs &a, u32 items,
+                          cudaStream_t s)
+{
+    if (!items) return HE_OK;
+    HE_CUDA(he::degree_ops(ctx->log_n)->eval(k, a, items, s));
+    return HE_OK;
+}
+
+extern "C" he_status he_relin(uint64_t *ct_out2, const uint64_t *ct_in3, const he_relin_key *key,
+                              const he_context *ctx, uint32_t level, void *scratch, size_t scratch_bytes,
+                              he_stream_t stream)
+{
+    if (he_status s = check_level(ctx, level, false)) return s;
+    if (!key || key->ctx != ctx) return fail(HE_EINVAL, "relin key is NULL or belongs to another context");
+    if (he_status s = check_ptr(ct_out2, "ct_out2")) return s;
+    if (he_status s = check_ptr(ct_in3, "ct_in3")) return s;
+    if (he_status s = check_ptr(scratch, "scratch")) return s;
+    const u32 n = level + 1;
+    if (scratch_bytes < relin_words(ctx, n) * 8) return fail(HE_EINVAL, "scratch too small");
+    he::EvalArgs a = {};
+    a.ct3 = ct_in3;
+    a.out = ct_out2;
+    a.c2 = (u64 *)scratch;
+    a.accq = a.c2 + (size_t)n * ctx->N;
+    a.plift = a.accq + (size_t)2 * n * ctx->N;
+    a.evk = key->d_evk;
+    a.n = n;
+    a.count = 1;
+    a.ctx = dev_ctx(ctx);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (he_status r = run_eval(ctx, he::EK_KS_DIGITS, a, n, s)) return r;
+    if (he_status r = run_eval(ctx, he::EK_KS_MODUP, a, n + 1, s)) return r;
+    return run_eval(ctx, he::EK_KS_MODDOWN, a, 2 * n, s);
+}
+
+extern "C" he_status he_rescale(uint64_t *ct_out, const uint64_t *ct_in, const he_context *ctx, uint32_t level,
+                                void *scratch, size_t scratch_bytes, he_stream_t stream)
+{
+    if (he_status s = check_level(ctx, level, true)) return s;
+    if (he_status s = check_ptr(ct_out, "ct_out")) return s;
+    if (he_status s = check_ptr(ct_in, "ct_in")) return s;
+    if (he_status s = check_ptr(scratch, "scratch")) return s;
+    if (scratch_bytes < rescale_words(ctx) * 8) return fail(HE_EINVAL, "scratch too small");
+    he::EvalArgs a = {};
+    a.ct2 = ct_in;
+    a.out = ct_out;
+    a.lift2 = (u64 *)scratch;
+    a.n = level + 1;
+    a.count = 1;
+    a.ctx = dev_ctx(ctx);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (he_status r = run_eval(ctx, he::EK_RS_LIFT, a, 2, s)) return r;
+    return run_eval(ctx, he::EK_RS, a, 2 * level, s);
+}
+
+extern "C" he_status he_mul_relin_rescale(uint64_t *ct_out, const uint64_t *ct_a, const uint64_t *ct_b,
+                                          uint32_t count, const he_relin_key *key, const he_context *ctx,
+                                          uint32_t level, void *scratch, size_t scratch_bytes, he_stream_t stream)
+{
+    if (he_status s = check_level(ctx, level, true)) return s;
+    if (!key || key->ctx != ctx) return fail(HE_EINVAL, "relin key is NULL or belongs to another context");
+    if (he_status s = check_ptr(ct_out, "ct_out")) return s;
+    if (he_status s = check_ptr(ct_a, "ct_a")) return s;
+    if (he_status s = check_ptr(ct_b, "ct_b")) return s;
+    if (count == 0) return HE_OK;
+    if (he_status s = check_ptr(scratch, "scratch")) return s;
+    const u32 n = level + 1;
+    if (scratch_bytes < mrr_words(ctx, n) * 8 * count) return fail(HE_EINVAL, "scratch too small");
+    if ((u64)count * 2 * n * (ctx->N / 4096 + 1) > 0x7fffffffull) return fail(HE_EINVAL, "batch too large");
+    he::EvalArgs a = {};
+    a.ct_a = ct_a;
+    a.ct_b = ct_b;
+    a.out = ct_out;
+    a.c2 = (u64 *)scratch;
+    a.accq = a.c2 + (size_t)count * n * ctx->N;
+    a.plift = a.accq + (size_t)count * 2 * n * ctx->N;
+    a.lift2 = a.plift + (size_t)count * 2 * ctx->N;
+    a.evk = key->d_evk;
+    a.n = n;
+    a.count = count;
+    a.ctx = dev_ctx(ctx);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (he_status r = run_eval(ctx, he::EK_KS_DIGITS, a, count * n, s)) return r;
+    if (he_status r = run_eval(ctx, he::EK_KS_MODUP, a, count * (n + 1), s)) return r;
+    if (he_status r = run_eval(ctx, he::EK_MRR_LAST, a, count * 2, s)) return r;
+    return run_eval(ctx, he::EK_MRR_REST, a, count * 2 * level, s);
+}
+
+// ------------------------------------------------------------- measurement
+
+// Register-resident butterfly probe: each thread runs `iters` rounds of 8
+// independent Harvey butterflies (Algorithm 1) on a 60-bit prime with no
+// memory traffic, so the launch measures the integer-pipe ceiling of the
+// transform's arithmetic. One word per thread is written so nothing is
+// optimised away.
+__global__ void k_butterfly_probe(u64 *sink, u64 p, u64 w, u64 w_sh, u32 iters)
+{
+    const u64 two_p = 2 * p;
+    u64 x[16];
+#pragma unroll
+    for (int i = 0; i < 16; i++) x[i] = (threadIdx.x * 977 + blockIdx.x * 131 + i * 7919) % p;
+    for (u32 it = 0; it < iters; it++) {
+#pragma unroll
+        for (int i = 0; i < 8; i++) he::ct_butterfly(x[i], x[i + 8], w, w_sh, p, two_p);
+#pragma unroll
+        for (int i = 0; i < 8; i++) he::ct_butterfly(x[2 * (i & 3) + (i >> 2) * 8], x[2 * (i & 3) + 1 + (i >> 2) * 8],
+                                                     w, w_sh, p, two_p);
+    }
+    u64 acc = 0;
+#pragma unroll
+    for (int i = 0; i < 16; i++) acc ^= x[i];
+    sink[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = acc;
+}
+
+extern "C" he_status he_butterfly_probe(uint64_t *sink, uint32_t blocks, uint32_t threads, uint32_t iters,
+                                        he_stream_t stream)
+{
+    if (he_status s = check_ptr(sink, "sink")) return s;
+    if (!blocks || !threads || threads > 1024 || (threads & 31)) return fail(HE_EINVAL, "bad probe shape");
+    const u64 p = 1152921504606584833ull;   // the largest 60-bit prime = 1 mod 2^16
+    const u64 w = 123456789012345ull % p;
+    k_butterfly_probe<<<blocks, threads, 0, (cudaStream_t)stream>>>(sink, p, w, shoup(w, p), iters);
+    HE_CUDA(cudaGetLastError());
+    return HE_OK;
+}
+
+// ------------------------------------------------------------------- plans
+
+struct he_plan {
+    struct Group {
+        int log_n;
+        int log_b;
+        u32 items;
+        u32 clusters;
+        he::LimbJob *d_jobs;
+    };
+    std::vector<Group> groups;
+};
+
+extern "C" he_status he_plan_destroy(he_plan *plan)
+{
+    if (plan) {
+        cudaDeviceSynchronize();
+        for (auto &g : plan->groups) cudaFree(g.d_jobs);
+        delete plan;
+    }
+    return HE_OK;
+}
+
+extern "C" he_status he_ntt_plan_create(const he_poly_desc *descs_host, uint32_t count,
+                                        const he_ntt_shape *shapes_host, uint32_t n_shapes, he_plan **out)
+{
+    if (!out) return fail(HE_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (count && !descs_host) return fail(HE_EINVAL, "descs_host is NULL");
+    if (n_shapes && !shapes_host) return fail(HE_EINVAL, "shapes_host is NULL");
+    std::map<int, std::vector<he::LimbJob>> by_degree;
+    for (u32 i = 0; i < count; i++) {
+        const he_poly_desc &d = descs_host[i];
+        int log_n;
+        if (!d.tables) return fail(HE_EINVAL, "descriptor %u has no tables", i);
+        if (he_status s = check_degree(d.N, &log_n)) return s;
+        if (d.tables->N != d.N) return fail(HE_EINVAL, "descriptor %u: tables are for N = %u", i, d.tables->N);
+        if ((u64)d.first_prime + d.limbs > d.tables->K)
+            return fail(HE_EINVAL, "descriptor %u: primes %u..%u beyond the tables' %u", i, d.first_prime,
+                        d.first_prime + d.limbs, d.tables->K);
+        if (d.limbs && (!d.data || ((uintptr_t)d.data & 15)))
+            return fail(HE_EINVAL, "descriptor %u: data NULL or not 16-byte aligned", i);
+        for (u32 l = 0; l < d.limbs; l++) {
+            he::LimbJob j;
+            const u32 pr = d.first_prime + l;
+            j.data = d.data + (size_t)l * d.N;
+            j.tw_fwd = d.tables->d_fwd + (size_t)pr * d.N;
+            j.tw_inv = d.tables->d_inv + (size_t)pr * d.N;
+            j.pc = d.tables->d_pc + pr;
+            by_degree[log_n].push_back(j);
+        }
+    }
+    he_plan *plan = new he_plan;
+    for (auto &kv : by_degree) {
+        he_plan::Group g = {};
+        g.log_n = kv.first;
+        const he::DegreeOps *ops = he::degree_ops(g.log_n);
+        g.log_b = ops->default_log_b;
+        for (u32 s = 0; s < n_shapes; s++)
+            if (shapes_host[s].N == (1u << g.log_n) && shapes_host[s].log_block) {
+                if (!ops->has_shape((int)shapes_host[s].log_block)) {
+                    he_plan_destroy(plan);
+                    return fail(HE_EUNSUPPORTED, "no kernel with 2^%u words per CTA for N = 2^%d",
+                                shapes_host[s].log_block, g.log_n);
+                }
+                g.log_b = (int)shapes_host[s].log_block;
+            }
+        g.items = (u32)kv.second.size();
+        const int mc = std::max(ops->max_clusters(g.log_b, false), 1);
+        g.clusters = std::min<u32>(g.items, (u32)mc);
+        cudaError_t e = cudaMalloc(&g.d_jobs, kv.second.size() * sizeof(he::LimbJob));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(g.d_jobs, kv.second.data(), kv.second.size() * sizeof(he::LimbJob), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(g.d_jobs);
+            he_plan_destroy(plan);
+            return cuda_fail(e, "plan job list");
+        }
+        plan->groups.push_back(g);
+    }
+    *out = plan;
+    return HE_OK;
+}
+
+static he_status plan_run(const he_plan *plan, he_stream_t stream, bool inv)
+{
+    if (!plan) return fail(HE_EINVAL, "plan is NULL");
+    for (const auto &g : plan->groups) {
+        he::NttLaunch a = {};
+        a.items = g.items;
+        a.jobs = g.d_jobs;
+        HE_CUDA(he::degree_ops(g.log_n)->ntt_persistent(a, g.log_b, inv, g.clusters, (cudaStream_t)stream));
+    }
+    return HE_OK;
+}
+
+extern "C" he_status he_ntt_plan_fwd(const he_plan *plan, he_stream_t stream) { return plan_run(plan, stream, false); }
+extern "C" he_status he_ntt_plan_inv(const he_plan *plan, he_stream_t stream) { return plan_run(plan, stream, true); }
+
+extern "C" uint32_t he_plan_launches(const he_plan *plan) { return plan ? (uint32_t)plan->groups.size() : 0; }
+
+// ------------------------------------------------------- degree dispatch
+
+namespace he {
+extern const DegreeOps degree_ops_10, degree_ops_11, degree_ops_12, degree_ops_13, degree_ops_14,
+    degree_ops_15, degree_ops_16;
+
+const DegreeOps *degree_ops(int log_n)
+{
+    switch (log_n) {
+    case 10: return &degree_ops_10;
+    case 11: return &degree_ops_11;
+    case 12: return &degree_ops_12;
+    case 13: return &degree_ops_13;
+    case 14: return &degree_ops_14;
+    case 15: return &degree_ops_15;
+    case 16: return &degree_ops_16;
+    default: return nullptr;
+    }
+}
+}  // namespace he

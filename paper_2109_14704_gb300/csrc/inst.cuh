@@ -1,0 +1,188 @@
+// inst.cuh -- per-degree instantiation of the kernels and their launchers.
+// Each inst_n<log N>.cu includes this file and defines HE_LOG_N, so that the
+// degrees compile as separate translation units, in parallel.
+#pragma once
+#include <mutex>
+
+#include "kernels.cuh"
+
+namespace he {
+
+template <class K, class... Args>
+static cudaError_t launch_k(K kernel, u32 grid, u32 block, u32 smem, u32 cluster, cudaStream_t s,
+                            Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid, 1, 1);
+    cfg.blockDim = dim3(block, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    cfg.numAttrs = 0;
+    if (cluster > 1) {
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = cluster;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+    }
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+// Raise the dynamic shared-memory limit of a kernel once per process.
+template <class K>
+static cudaError_t smem_attr(K kernel, u32 bytes, std::once_flag &flag, cudaError_t &err)
+{
+    std::call_once(flag, [&] {
+        err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    });
+    return err;
+}
+
+template <int LOG_B, int LOG_C>
+struct ShapeOps {
+    using Sh = NttShape<LOG_B, LOG_C>;
+
+    template <bool INV>
+    static cudaError_t ntt(const NttLaunch &a, cudaStream_t s)
+    {
+        static std::once_flag f;
+        static cudaError_t e = cudaSuccess;
+        if (cudaError_t r = smem_attr(k_ntt<LOG_B, LOG_C, INV>, Sh::SMEM_BYTES, f, e)) return r;
+        return launch_k(k_ntt<LOG_B, LOG_C, INV>, a.items * Sh::C, Sh::T, Sh::SMEM_BYTES, Sh::C, s, a);
+    }
+
+    template <bool INV>
+    static cudaError_t persistent(const NttLaunch &a, u32 clusters, cudaStream_t s)
+    {
+        static std::once_flag f;
+        static cudaError_t e = cudaSuccess;
+        if (cudaError_t r = smem_attr(k_ntt_persistent<LOG_B, LOG_C, INV>, Sh::SMEM_BYTES, f, e)) return r;
+        return launch_k(k_ntt_persistent<LOG_B, LOG_C, INV>, clusters * Sh::C, Sh::T, Sh::SMEM_BYTES, Sh::C,
+                        s, a);
+    }
+
+    template <bool INV>
+    static int max_clusters()
+    {
+        static std::once_flag f;
+        static cudaError_t e = cudaSuccess;
+        if (smem_attr(k_ntt_persistent<LOG_B, LOG_C, INV>, Sh::SMEM_BYTES, f, e) != cudaSuccess) return 0;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(Sh::C * 1024, 1, 1);
+        cfg.blockDim = dim3(Sh::T, 1, 1);
+        cfg.dynamicSmemBytes = Sh::SMEM_BYTES;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = Sh::C;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, k_ntt_persistent<LOG_B, LOG_C, INV>, &cfg) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        return n;
+    }
+
+    static cudaError_t eval(EvalKernel k, const EvalArgs &a, u32 items, cudaStream_t s)
+    {
+        const u32 grid = items * Sh::C;
+        const u32 sm1 = Sh::SMEM_BYTES;
+        const u32 sm3 = Sh::SMEM_BYTES * 3;    // modup: transform + two accumulators
+        switch (k) {
+#define HE_EVAL_CASE(ID, KERNEL, SMEM)                                                   \
+    case ID: {                                                                           \
+        static std::once_flag f;                                                         \
+        static cudaError_t e = cudaSuccess;                                              \
+        if (cudaError_t r = smem_attr(KERNEL<LOG_B, LOG_C>, SMEM, f, e)) return r;       \
+        return launch_k(KERNEL<LOG_B, LOG_C>, grid, Sh::T, SMEM, Sh::C, s, a);           \
+    }
+            HE_EVAL_CASE(EK_KS_DIGITS, k_ks_digits, sm1)
+            HE_EVAL_CASE(EK_KS_MODUP, k_ks_modup, sm3)
+            HE_EVAL_CASE(EK_KS_MODDOWN, k_ks_moddown, sm1)
+            HE_EVAL_CASE(EK_RS_LIFT, k_rs_lift, sm1)
+            HE_EVAL_CASE(EK_RS, k_rs, sm1)
+            HE_EVAL_CASE(EK_MRR_LAST, k_mrr_last, sm1)
+            HE_EVAL_CASE(EK_MRR_REST, k_mrr_rest, sm1)
+#undef HE_EVAL_CASE
+        default:
+            return cudaErrorInvalidValue;
+        }
+    }
+};
+
+}  // namespace he
+
+// Shapes built per degree: words per CTA 2^LOG_B with at most 8 CTAs per
+// cluster. The first listed is the default (and the one the evaluation
+// kernels use).
+#define HE_SHAPE_FN(LOG_N_, LB)                                                                    \
+    if (log_b == LB) return fn(::he::ShapeOps<LB, LOG_N_ - LB>{});
+
+namespace he {
+
+template <int LOG_N>
+struct DegreeImpl;
+
+#define HE_DEGREE(LOG_N_, DEF, ...)                                                                \
+    template <>                                                                                    \
+    struct DegreeImpl<LOG_N_> {                                                                    \
+        static constexpr int def = DEF;                                                            \
+        template <class F>                                                                         \
+        static auto with_shape(int log_b, F fn) -> decltype(fn(ShapeOps<DEF, LOG_N_ - DEF>{}))     \
+        {                                                                                          \
+            if (log_b == 0) log_b = DEF;                                                           \
+            __VA_ARGS__                                                                            \
+            return decltype(fn(ShapeOps<DEF, LOG_N_ - DEF>{}))();                                  \
+        }                                                                                          \
+    };
+
+}  // namespace he
+
+#define HE_DEFINE_DEGREE_OPS(LOG_N_)                                                               \
+    namespace he {                                                                                 \
+    static cudaError_t ntt_##LOG_N_(const NttLaunch &a, int log_b, bool inv, cudaStream_t s)        \
+    {                                                                                              \
+        using D = DegreeImpl<LOG_N_>;                                                              \
+        bool found = false;                                                                        \
+        cudaError_t r = D::with_shape(log_b, [&](auto ops) {                                       \
+            found = true;                                                                          \
+            return inv ? decltype(ops)::template ntt<true>(a, s) : decltype(ops)::template ntt<false>(a, s); \
+        });                                                                                        \
+        return found ? r : cudaErrorInvalidValue;                                                  \
+    }                                                                                              \
+    static cudaError_t ntt_p_##LOG_N_(const NttLaunch &a, int log_b, bool inv, u32 cl, cudaStream_t s) \
+    {                                                                                              \
+        using D = DegreeImpl<LOG_N_>;                                                              \
+        bool found = false;                                                                        \
+        cudaError_t r = D::with_shape(log_b, [&](auto ops) {                                       \
+            found = true;                                                                          \
+            return inv ? decltype(ops)::template persistent<true>(a, cl, s)                       \
+                       : decltype(ops)::template persistent<false>(a, cl, s);                     \
+        });                                                                                        \
+        return found ? r : cudaErrorInvalidValue;                                                  \
+    }                                                                                              \
+    static int maxcl_##LOG_N_(int log_b, bool inv)                                                 \
+    {                                                                                              \
+        using D = DegreeImpl<LOG_N_>;                                                              \
+        return D::with_shape(log_b, [&](auto ops) {                                                \
+            return inv ? decltype(ops)::template max_clusters<true>()                              \
+                       : decltype(ops)::template max_clusters<false>();                           \
+        });                                                                                        \
+    }                                                                                              \
+    static cudaError_t eval_##LOG_N_(EvalKernel k, const EvalArgs &a, u32 items, cudaStream_t s)   \
+    {                                                                                              \
+        return ShapeOps<DegreeImpl<LOG_N_>::def, LOG_N_ - DegreeImpl<LOG_N_>::def>::eval(k, a, items, s); \
+    }                                                                                              \
+    static bool has_##LOG_N_(int log_b)                                                            \
+    {                                                                                              \
+        return DegreeImpl<LOG_N_>::with_shape(log_b, [&](auto) { return true; });                 \
+    }                                                                                              \
+    extern const DegreeOps degree_ops_##LOG_N_ = {LOG_N_, DegreeImpl<LOG_N_>::def, ntt_##LOG_N_,     \
+                                                  ntt_p_##LOG_N_, maxcl_##LOG_N_, eval_##LOG_N_,   \
+                                                  has_##LOG_N_};                                   \
+    }

@@ -1,0 +1,464 @@
+// kernels.cuh -- the CUDA kernels of the library, as templates over the NTT
+// shape (words per CTA, CTAs per cluster). inst_n*.cu instantiate them per
+// polynomial degree; launch.h describes the host-side launchers.
+#pragma once
+#include <stdint.h>
+
+#include "launch.h"
+#include "ntt_core.cuh"
+
+namespace he {
+
+// ============================================================ plain NTT ====
+
+template <int LOG_B, int LOG_C, bool INV>
+__global__ void __launch_bounds__(NttShape<LOG_B, LOG_C>::T) k_ntt(NttLaunch a)
+{
+    using Sh = NttShape<LOG_B, LOG_C>;
+    extern __shared__ __align__(16) u64 smem[];
+    const u32 m = (LOG_C > 0) ? cluster_ctarank() : 0u;
+    const u32 item = blockIdx.x >> LOG_C;
+    u64 *data;
+    const ulonglong2 *tw;
+    const PrimeConst *pcp;
+    if (a.jobs) {
+        const LimbJob j = a.jobs[item];
+        data = j.data;
+        tw = INV ? j.tw_inv : j.tw_fwd;
+        pcp = j.pc;
+    } else {
+        data = a.base + (size_t)item * Sh::N;
+        const u32 pr = a.first_prime + item % a.limbs;
+        tw = (INV ? a.tw_inv : a.tw_fwd) + (size_t)pr * Sh::N;
+        pcp = a.pc + pr;
+    }
+    const PrimeConst pc = *pcp;
+    u64 x[16];
+    auto ld = [&](u32 P) -> u64 { return data[P]; };
+    auto st = [&](u32 P, u64 v) { data[P] = v; };
+    if constexpr (!INV)
+        ntt_fwd_block<Sh>(smem, m, tw, pc.p, pc.two_p, ld, st, x);
+    else
+        ntt_inv_block<Sh, false>(smem, m, tw, pc, ld, st, x);
+}
+
+// Persistent form for plans: a fixed grid of clusters walks the job list.
+template <int LOG_B, int LOG_C, bool INV>
+__global__ void __launch_bounds__(NttShape<LOG_B, LOG_C>::T) k_ntt_persistent(NttLaunch a)
+{
+    using Sh = NttShape<LOG_B, LOG_C>;
+    extern __shared__ __align__(16) u64 smem[];
+    const u32 m = (LOG_C > 0) ? cluster_ctarank() : 0u;
+    const u32 clusters = gridDim.x >> LOG_C;
+    bool first = true;
+    for (u32 item = blockIdx.x >> LOG_C; item < a.items; item += clusters) {
+        if (!first) ntt_barrier<Sh>();
+        first = false;
+        const LimbJob j = a.jobs[item];
+        u64 *data = j.data;
+        const PrimeConst pc = *j.pc;
+        u64 x[16];
+        auto ld = [&](u32 P) -> u64 { return data[P]; };
+        auto st = [&](u32 P, u64 v) { data[P] = v; };
+        if constexpr (!INV)
+            ntt_fwd_block<Sh>(smem, m, j.tw_fwd, pc.p, pc.two_p, ld, st, x);
+        else
+            ntt_inv_block<Sh, false>(smem, m, j.tw_inv, pc, ld, st, x);
+    }
+}
+
+#ifdef HE_MISC_KERNELS  // defined by the one translation unit that owns them
+// ======================================================== naive radix-2 ====
+// The baseline of Sec. III-B: one launch per stage, each thread one
+// butterfly, data exchanged through global memory, and a final pass that
+// reduces [0, 4p) to [0, p) (forward) -- 2 N log N + 2 N global accesses.
+
+__global__ void k_ntt_naive_stage(NttLaunch a, u32 log_n, u32 S, bool inv)
+{
+    const u32 N = 1u << log_n;
+    const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t total = (size_t)a.items * (N / 2);
+    if (gid >= total) return;
+    const u32 item = (u32)(gid / (N / 2));
+    const u32 b = (u32)(gid % (N / 2));
+    u64 *data = a.base + (size_t)item * N;
+    const u32 pr = a.first_prime + item % a.limbs;
+    const PrimeConst pc = a.pc[pr];
+    const u32 t = N >> (S + 1);
+    const u32 g = b / t;
+    const u32 j = 2 * g * t + (b % t);
+    u64 x = data[j], y = data[j + t];
+    if (!inv) {
+        const ulonglong2 w = a.tw_fwd[(size_t)pr * N + (1u << S) + g];
+        ct_butterfly(x, y, w.x, w.y, pc.p, pc.two_p);
+    } else if (S == 0) {
+        gs_last(x, y, pc);
+    } else {
+        const ulonglong2 w = a.tw_inv[(size_t)pr * N + (1u << S) + g];
+        gs_butterfly(x, y, w.x, w.y, pc.p, pc.two_p);
+    }
+    data[j] = x;
+    data[j + t] = y;
+}
+
+__global__ void k_ntt_naive_final(NttLaunch a, u32 log_n)
+{
+    const u32 N = 1u << log_n;
+    const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (size_t)a.items * N) return;
+    const u32 item = (u32)(gid >> log_n);
+    const PrimeConst &pc = a.pc[a.first_prime + item % a.limbs];
+    u64 v = a.base[gid];
+    a.base[gid] = reduce_once(reduce_once(v, pc.two_p), pc.p);
+}
+
+// =========================================================== dyadic ========
+
+// out = a * b mod q for `items` limbs of N words; 2 words per thread.
+__global__ void k_dyadic(u64 *out, const u64 *a, const u64 *b, u32 log_n, u32 items, u32 limbs,
+                         u32 first_prime, const PrimeConst *pcs)
+{
+    const size_t total2 = ((size_t)items << log_n) >> 1;
+    for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < total2;
+         g += (size_t)gridDim.x * blockDim.x) {
+        const size_t e = g * 2;
+        const u32 item = (u32)(e >> log_n);
+        const PrimeConst pc = pcs[first_prime + item % limbs];
+        const ulonglong2 va = *reinterpret_cast<const ulonglong2 *>(a + e);
+        const ulonglong2 vb = *reinterpret_cast<const ulonglong2 *>(b + e);
+        ulonglong2 r;
+        r.x = mul_mod(va.x, vb.x, pc);
+        r.y = mul_mod(va.y, vb.y, pc);
+        *reinterpret_cast<ulonglong2 *>(out + e) = r;
+    }
+}
+
+// ============================================================ Mul ==========
+
+// out3[c] = (a0 b0, a0 b1 + a1 b0, a1 b1) per limb (Sec. II-A), count pairs.
+__global__ void k_tensor(u64 *out3, const u64 *ct_a, const u64 *ct_b, u32 log_n, u32 n, u32 count,
+                         const PrimeConst *pcs)
+{
+    const size_t per = (size_t)n << log_n;           // words per component
+    const size_t total2 = (size_t)count * per / 2;
+    for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < total2;
+         g += (size_t)gridDim.x * blockDim.x) {
+        const size_t e = g * 2;
+        const size_t c = e / per;
+        const size_t off = e - c * per;
+        const u32 limb = (u32)(off >> log_n);
+        const PrimeConst pc = pcs[limb];
+        const u64 *A = ct_a + c * 2 * per + off;
+        const u64 *Bp = ct_b + c * 2 * per + off;
+        const ulonglong2 a0 = *reinterpret_cast<const ulonglong2 *>(A);
+        const ulonglong2 a1 = *reinterpret_cast<const ulonglong2 *>(A + per);
+        const ulonglong2 b0 = *reinterpret_cast<const ulonglong2 *>(Bp);
+        const ulonglong2 b1 = *reinterpret_cast<const ulonglong2 *>(Bp + per);
+        u64 *O = out3 + c * 3 * per + off;
+        ulonglong2 d0, d1, d2;
+        d0.x = mul_mod(a0.x, b0.x, pc);
+        d0.y = mul_mod(a0.y, b0.y, pc);
+        d1.x = mad2_mod(a0.x, b1.x, a1.x, b0.x, pc);
+        d1.y = mad2_mod(a0.y, b1.y, a1.y, b0.y, pc);
+        d2.x = mul_mod(a1.x, b1.x, pc);
+        d2.y = mul_mod(a1.y, b1.y, pc);
+        *reinterpret_cast<ulonglong2 *>(O) = d0;
+        *reinterpret_cast<ulonglong2 *>(O + per) = d1;
+        *reinterpret_cast<ulonglong2 *>(O + 2 * per) = d2;
+    }
+}
+
+#endif  // HE_MISC_KERNELS
+
+// ============================================== key switching and rescale ==
+//
+// Relin (Sec. II-A) with RNS digits and one special prime P, as four kernels
+// over all ciphertexts of a batch:
+//   k_ks_digits   INTT_{q_j}(c[2]_j) -> coefficient digits c2_j     (n INTT)
+//   k_ks_modup    for each target t in {q_0..q_l, P}:
+//                 acc_k[t] = sum_j NTT_t(c2_j mod t) * evk[j][k][t]  (n^2 NTT)
+//                 (for t = q_j the NTT-domain c[2]_j is used as is); on P the
+//                 accumulators are brought back by INTT_P and kept as the
+//                 coefficient-domain residues y_k = [x_k]_P          (2 INTT)
+//   k_ks_moddown  out_k[i] = d_k[i] + (acc_k[q_i] - NTT(r_k mod q_i)) P^-1,
+//                 r_k the centred lift of y_k                        (2n NTT)
+// RS (Sec. II-A): k_rs_lift brings c_k[q_l] to the coefficient domain
+// (2 INTT), k_rs combines (c_k[q_i] - NTT(r mod q_i)) q_l^-1 (2(n-1) NTT).
+// MulLinRS fuses Mul into the loads and the mod-down of limb q_l with RS's
+// INTT (k_mrr_last), and mod-down with RS for the other limbs (k_mrr_rest).
+
+// Centred residue of y in [0, m) (|r| <= (m-1)/2) reduced mod q:
+// y mod q, or y mod q - m mod q when y > (m-1)/2. Needs y < 2 q^2.
+__device__ __forceinline__ u64 centred_mod(u64 y, u64 half_m, u64 m_mod_q, const PrimeConst &pc)
+{
+    u64 r = barrett_reduce(0, y, pc.p, pc.mu, pc.bits);
+    return y > half_m ? sub_mod(r, m_mod_q, pc.p) : r;
+}
+
+// d_k[i] at position P for component k (0 or 1): from the tensor of the two
+// input ciphertexts (fused Mul) or from a 3-component input.
+struct DSource {
+    const u64 *ct_a, *ct_b, *ct3;  // per-ciphertext bases
+    size_t per;                    // n * N words per component
+    __device__ __forceinline__ u64 d(int k, u32 limb, u32 log_n, u32 P, const PrimeConst &pc) const
+    {
+        const size_t off = ((size_t)limb << log_n) + P;
+        if (ct3) return ct3[k * per + off];
+        if (k == 0) return mul_mod(ct_a[off], ct_b[off], pc);
+        if (k == 1) return mad2_mod(ct_a[off], ct_b[per + off], ct_a[per + off], ct_b[off], pc);
+        return mul_mod(ct_a[per + off], ct_b[per + off], pc);
+    }
+};
+
+__device__ __forceinline__ DSource dsource(const EvalArgs &a, u32 c)
+{
+    DSource s;
+    s.per = (size_t)a.n * a.ctx.N;
+    s.ct3 = a.ct3 ? a.ct3 + (size_t)c * 3 * s.per : nullptr;
+    s.ct_a = a.ct_a ? a.ct_a + (size_t)c * 2 * s.per : nullptr;
+    s.ct_b = a.ct_b ? a.ct_b + (size_t)c * 2 * s.per : nullptr;
+    return s;
+}
+
+template <int LOG_B, int LOG_C>
+__global__ void __launch_bounds__(NttShape<LOG_B, LOG_C>::T, 2) k_ks_digits(EvalArgs a)
+{
+    using Sh = NttShape<LOG_B, LOG_C>;
+    extern __shared__ __align__(16) u64 smem[];
+    const u32 m = (LOG_C > 0) ? cluster_ctarank() : 0u;
+    const u32 item = blockIdx.x >> LOG_C;
+    const u32 c = item / a.n, j = item % a.n;
+    const PrimeConst pc = a.ctx.pc[j];
+    const DSource ds = dsource(a, c);
+    u64 *out = a.c2 + ((size_t)c * a.n + j) * Sh::N;
+    u64 x[16];
+    auto ld = [&](u32 P) -> u64 { return ds.d(2, j, Sh::LOG_N, P, pc); };
+    auto st = [&](u32 P, u64 v) { out[P] = v; };
+    ntt_inv_block<Sh, false>(smem, m, a.ctx.tw_inv + (size_t)j * Sh::N, pc, ld, st, x);
+}
+
+template <class Sh>
+__device__ __forceinline__ u32 last_pos(u32 m, u32 tid, int e)
+{
+    using RL = typename RoundOf<Sh, Sh::NROUND - 1>::type;
+    return m * Sh::B + round_pos<RL>(tid, e >> RL::R, e & ((1 << RL::R) - 1));
+}
+
+template <int LOG_B, int LOG_C>
+__global__ void __launch_bounds__(NttShape<LOG_B, LOG_C>::T, 2) k_ks_modup(EvalArgs a)
+{
+    using Sh = NttShape<LOG_B, LOG_C>;
+    extern __shared__ __align__(16) u64 smem[];
+    u64 *acc = smem + Sh::B;                   // [2][16][T], own positions only
+    const u32 tid = threadIdx.x;
+    const u32 m = (LOG_C > 0) ? cluster_ctarank() : 0u;
+    const u32 item = blockIdx.x >> LOG_C;
+    const u32 n = a.n;
+    const u32 c = item / (n + 1), t = item % (n + 1);
+    const u32 tp = (t == n) ? a.ctx.n_data : t; // prime index of the target
+    const PrimeConst pc = a.ctx.pc[tp];
+    const DSource ds = dsource(a, c);
+    const ulonglong2 *twf = a.ctx.tw_fwd + (size_t)tp * Sh::N;
+    u64 x[16];
+    for (u32 j = 0; j < n; j++) {
+        if (t == j) {
+#pragma unroll
+            for (int e = 0; e < 16; e++) x[e] = ds.d(2, j, Sh::LOG_N, last_pos<Sh>(m, tid, e), pc);
+        } else {
+            if (j > 0) ntt_barrier<Sh>();
+            const u64 *src = a.c2 + ((size_t)c * n + j) * Sh::N;
+            auto ld = [&](u32 P) -> u64 { return barrett_reduce(0, src[P], pc.p, pc.mu, pc.bits); };
+            auto st = [&](u32, u64) {};
+            ntt_fwd_block<Sh>(smem, m, twf, pc.p, pc.two_p, ld, st, x);
+        }
+#pragma unroll
+        for (int k = 0; k < 2; k++) {
+            const ulonglong2 *key = a.evk + (((size_t)j * 2 + k) * (a.ctx.n_data + 1) + tp) * Sh::N;
+#pragma unroll
+            for (int e = 0; e < 16; e++) {
+                const ulonglong2 w = __ldg(key + last_pos<Sh>(m, tid, e));
+                const u64 prod = mul_shoup(x[e], w.x, w.y, pc.p);
+                u64 &slot = acc[(k * 16 + e) * Sh::T + tid];
+                slot = (j == 0) ? prod : add_mod(slot, prod, pc.p);
+            }
+        }
+    }
+    if (t < n) {
+#pragma unroll
+        for (int k = 0; k < 2; k++) {
+            u64 *dst = a.accq + (((size_t)c * 2 + k) * n + t) * Sh::N;
+#pragma unroll
+            for (int e = 0; e < 16; e++) dst[last_pos<Sh>(m, tid, e)] = acc[(k * 16 + e) * Sh::T + tid];
+        }
+    } else {
+        // special prime: y_k = INTT_P(acc_k), kept in the coefficient domain
+#pragma unroll
+        for (int k = 0; k < 2; k++) {
+            ntt_barrier<Sh>();
+#pragma unroll
+            for (int e = 0; e < 16; e++) x[e] = acc[(k * 16 + e) * Sh::T + tid];
+            u64 *dst = a.plift + ((size_t)c * 2 + k) * Sh::N;
+            auto st = [&](u32 P, u64 v) { dst[P] = v; };
+            auto ld = [&](u32) -> u64 { return 0; };
+            ntt_inv_block<Sh, true>(smem, m, a.ctx.tw_inv + (size_t)tp * Sh::N, pc, ld, st, x);
+        }
+    }
+}
+
+// Relin mod-down (no rescale): out[c][k][i] = d_k[i] + (acc - NTT(r)) P^-1.
+template <int LOG_B, int LOG_C>
+__global__ void __launch_bounds__(NttShape<LOG_B, LOG_C>::T, 2) k_ks_moddown(EvalArgs a)
+{
+    using Sh = NttShape<LOG_B, LOG_C>;
+    extern __shared__ __align__(16) u64 smem[];
+    const u32 tid = threadIdx.x;
+    const u32 m = (LOG_C > 0) ? cluster_ctarank() : 0u;
+    const u32 item = blockIdx.x >> LOG_C;
+    const u32 n = a.n;
+    const u32 c = item / (2 * n), k = (item / n) % 2, i = item % n;
+    const PrimeConst pc = a.ctx.pc[i];
+    const PrimeConst pP = a.ctx.pc[a.ctx.n_data];
+    const u64 *cst = a.ctx.cst + 3 * i;         // P^-1, Shoup, P mod q_i
+    const u64 half_P = (pP.p - 1) / 2;
+    const DSource ds = dsource(a, c);
+    const u64 *y = a.plift + ((size_t)c * 2 + k) * Sh::N;
+    u64 x[16];
+    auto ld = [&](u32 P) -> u64 { return centred_mod(y[P], half_P, cst[2], pc); };
+    auto st = [&](u32, u64) {};
+    ntt_fwd_block<Sh>(smem, m, a.ctx.tw_fwd + (size_t)i * Sh::N, pc.p, pc.two_p, ld, st, x);
+    const u64 *accp = a.accq + (((size_t)c * 2 + k) * n + i) * Sh::N;
+    u64 *out = a.out + (((size_t)c * 2 + k) * n + i) * Sh::N;
+#pragma unroll
+    for (int e = 0; e < 16; e++) {
+        const u32 P = last_pos<Sh>(m, tid, e);
+        const u64 v = mul_shoup(sub_mod(accp[P], x[e], pc.p), cst[0], cst[1], pc.p);
+        out[P] = add_mod(ds.d(k, i, Sh::LOG_N, P, pc), v, pc.p);
+    }
+}
+
+// RS, first half: y_k = INTT_{q_l}(c_k[q_l]) -> lift2 (coefficient domain).
+template <int LOG_B, int LOG_C>
+__global__ void __launch_bounds__(NttShape<LOG_B, LOG_C>::T, 2) k_rs_lift(EvalArgs a)
+{
+    using Sh = NttShape<LOG_B, LOG_C>;
+    extern __shared__ __align__(16) u64 smem[];
+    const u32 m = (LOG_C > 0) ? cluster_ctarank() : 0u;
+    const u32 item = blockIdx.x >> LOG_C;
+    const u32 n = a.n, l = n - 1;
+    const u32 c = item / 2, k = item % 2;
+    const PrimeConst pc = a.ctx.pc[l];
+    const u64 *src = a.ct2 + (((size_t)c * 2 + k) * n + l) * Sh::N;
+    u64 *dst = a.lift2 + ((size_t)c * 2 + k) * Sh::N;
+    u64 x[16];
+    auto ld = [&](u32 P) -> u64 { return src[P]; };
+    auto st = [&](u32 P, u64 v) { dst[P] = v; };
+    ntt_inv_block<Sh, false>(smem, m, a.ctx.tw_inv + (size_t)l * Sh::N, pc, ld, st, x);
+}
+
+// RS, second half: out[c][k][i] = (c_k[q_i] - NTT(r mod q_i)) q_l^-1, i < l.
+template <int LOG_B, int LOG_C>
+__global__ void __launch_bounds__(NttShape<LOG_B, LOG_C>::T, 2) k_rs(EvalArgs a)
+{
+    using Sh = NttShape<LOG_B, LOG_C>;
+    extern __shared__ __align__(16) u64 smem[];
+    const u32 tid = threadIdx.x;
+    const u32 m = (LOG_C > 0) ? cluster_ctarank() : 0u;
+    const u32 item = blockIdx.x >> LOG_C;
+    const u32 n = a.n, l = n - 1;
+    const u32 c = item / (2 * l), k = (item / l) % 2, i = item % l;
+    const PrimeConst pc = a.ctx.pc[i];
+    const u64 *cst = a.ctx.cst + 3 * a.ctx.n_data + 3 * ((size_t)l * a.ctx.n_data + i);
+    const u64 half_l = (a.ctx.pc[l].p - 1) / 2;
+    const u64 *y = a.lift2 + ((size_t)c * 2 + k) * Sh::N;
+    u64 x[16];
+    auto ld = [&](u32 P) -> u64 { return centred_mod(y[P], half_l, cst[2], pc); };
+    auto st = [&](u32, u64) {};
+    ntt_fwd_block<Sh>(smem, m, a.ctx.tw_fwd + (size_t)i * Sh::N, pc.p, pc.two_p, ld, st, x);
+    const u64 *src = a.ct2 + (((size_t)c * 2 + k) * n + i) * Sh::N;
+    u64 *out = a.out + (((size_t)c * 2 + k) * l + i) * Sh::N;
+#pragma unroll
+    for (int e = 0; e < 16; e++) {
+        const u32 P = last_pos<Sh>(m, tid, e);
+        out[P] = mul_shoup(sub_mod(src[P], x[e], pc.p), cst[0], cst[1], pc.p);
+    }
+}
+
+// MulLinRS, limb q_l: relin output c_k[q_l] = d_k[l] + (acc - NTT(r)) P^-1,
+// then straight into INTT_{q_l} (values stay in registers) -> lift2.
+template <int LOG_B, int LOG_C>
+__global__ void __launch_bounds__(NttShape<LOG_B, LOG_C>::T, 2) k_mrr_last(EvalArgs a)
+{
+    using Sh = NttShape<LOG_B, LOG_C>;
+    extern __shared__ __align__(16) u64 smem[];
+    const u32 tid = threadIdx.x;
+    const u32 m = (LOG_C > 0) ? cluster_ctarank() : 0u;
+    const u32 item = blockIdx.x >> LOG_C;
+    const u32 n = a.n, l = n - 1;
+    const u32 c = item / 2, k = item % 2;
+    const PrimeConst pc = a.ctx.pc[l];
+    const PrimeConst pP = a.ctx.pc[a.ctx.n_data];
+    const u64 *cst = a.ctx.cst + 3 * l;
+    const u64 half_P = (pP.p - 1) / 2;
+    const DSource ds = dsource(a, c);
+    const u64 *y = a.plift + ((size_t)c * 2 + k) * Sh::N;
+    u64 x[16];
+    auto ld = [&](u32 P) -> u64 { return centred_mod(y[P], half_P, cst[2], pc); };
+    auto nost = [&](u32, u64) {};
+    ntt_fwd_block<Sh>(smem, m, a.ctx.tw_fwd + (size_t)l * Sh::N, pc.p, pc.two_p, ld, nost, x);
+    const u64 *accp = a.accq + (((size_t)c * 2 + k) * n + l) * Sh::N;
+#pragma unroll
+    for (int e = 0; e < 16; e++) {
+        const u32 P = last_pos<Sh>(m, tid, e);
+        const u64 v = mul_shoup(sub_mod(accp[P], x[e], pc.p), cst[0], cst[1], pc.p);
+        x[e] = add_mod(ds.d(k, l, Sh::LOG_N, P, pc), v, pc.p);
+    }
+    u64 *dst = a.lift2 + ((size_t)c * 2 + k) * Sh::N;
+    auto st = [&](u32 P, u64 v) { dst[P] = v; };
+    auto nold = [&](u32) -> u64 { return 0; };
+    ntt_inv_block<Sh, true>(smem, m, a.ctx.tw_inv + (size_t)l * Sh::N, pc, nold, st, x);
+}
+
+// MulLinRS, limbs i < l: mod-down by P then rescale by q_l, two NTTs.
+template <int LOG_B, int LOG_C>
+__global__ void __launch_bounds__(NttShape<LOG_B, LOG_C>::T, 2) k_mrr_rest(EvalArgs a)
+{
+    using Sh = NttShape<LOG_B, LOG_C>;
+    extern __shared__ __align__(16) u64 smem[];
+    const u32 tid = threadIdx.x;
+    const u32 m = (LOG_C > 0) ? cluster_ctarank() : 0u;
+    const u32 item = blockIdx.x >> LOG_C;
+    const u32 n = a.n, l = n - 1;
+    const u32 c = item / (2 * l), k = (item / l) % 2, i = item % l;
+    const PrimeConst pc = a.ctx.pc[i];
+    const PrimeConst pP = a.ctx.pc[a.ctx.n_data];
+    const u64 *cP = a.ctx.cst + 3 * i;
+    const u64 *cl = a.ctx.cst + 3 * a.ctx.n_data + 3 * ((size_t)l * a.ctx.n_data + i);
+    const u64 half_P = (pP.p - 1) / 2;
+    const u64 half_l = (a.ctx.pc[l].p - 1) / 2;
+    const DSource ds = dsource(a, c);
+    const ulonglong2 *twf = a.ctx.tw_fwd + (size_t)i * Sh::N;
+    const u64 *y = a.plift + ((size_t)c * 2 + k) * Sh::N;
+    u64 x[16], z[16];
+    auto nost = [&](u32, u64) {};
+    auto ld1 = [&](u32 P) -> u64 { return centred_mod(y[P], half_P, cP[2], pc); };
+    ntt_fwd_block<Sh>(smem, m, twf, pc.p, pc.two_p, ld1, nost, x);
+    const u64 *accp = a.accq + (((size_t)c * 2 + k) * n + i) * Sh::N;
+#pragma unroll
+    for (int e = 0; e < 16; e++) {
+        const u32 P = last_pos<Sh>(m, tid, e);
+        const u64 v = mul_shoup(sub_mod(accp[P], x[e], pc.p), cP[0], cP[1], pc.p);
+        z[e] = add_mod(ds.d(k, i, Sh::LOG_N, P, pc), v, pc.p);
+    }
+    ntt_barrier<Sh>();
+    const u64 *y2 = a.lift2 + ((size_t)c * 2 + k) * Sh::N;
+    auto ld2 = [&](u32 P) -> u64 { return centred_mod(y2[P], half_l, cl[2], pc); };
+    ntt_fwd_block<Sh>(smem, m, twf, pc.p, pc.two_p, ld2, nost, x);
+    u64 *out = a.out + (((size_t)c * 2 + k) * l + i) * Sh::N;
+#pragma unroll
+    for (int e = 0; e < 16; e++) {
+        const u32 P = last_pos<Sh>(m, tid, e);
+        out[P] = mul_shoup(sub_mod(z[e], x[e], pc.p), cl[0], cl[1], pc.p);
+    }
+}
+
+}  // namespace he

@@ -1,0 +1,94 @@
+// launch.h -- argument blocks of the kernels and the per-degree launcher
+// table (host and device visible). Internal to the library.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "modarith.cuh"
+
+namespace he {
+
+// One limb of a batched transform (plans): its data, twiddles and constants.
+struct LimbJob {
+    u64 *data;
+    const ulonglong2 *tw_fwd;
+    const ulonglong2 *tw_inv;
+    const PrimeConst *pc;
+};
+
+// A uniform batch (items = count * limbs limbs of one degree, limb l of each
+// polynomial using prime first_prime + l of one table set), or a job list.
+struct NttLaunch {
+    u64 *base;
+    u32 limbs;
+    u32 first_prime;
+    u32 items;
+    u32 pad;
+    const ulonglong2 *tw_fwd;   // [prime][N]
+    const ulonglong2 *tw_inv;
+    const PrimeConst *pc;       // [prime]
+    const LimbJob *jobs;        // non-null: per-item jobs instead of base/limbs
+};
+
+// Device view of a modulus chain (q_0..q_{n_data-1}, then P at n_data).
+struct DevCtx {
+    const ulonglong2 *tw_fwd;   // [n_data + 1][N]
+    const ulonglong2 *tw_inv;
+    const PrimeConst *pc;       // [n_data + 1]
+    // cst[3 i + {0,1,2}] = P^-1 mod q_i, its Shoup quotient, P mod q_i;
+    // cst[3 n_data + 3 (l n_data + i) + {0,1,2}] = q_l^-1 mod q_i, Shoup,
+    // q_l mod q_i (rescale from level l, i < l).
+    const u64 *cst;
+    u32 N;
+    u32 n_data;
+};
+
+struct EvalArgs {
+    const u64 *ct_a, *ct_b;     // [count][2][n][N] (fused Mul) or null
+    const u64 *ct3;             // [count][3][n][N] or null
+    const u64 *ct2;             // [count][2][n][N] rescale input
+    u64 *out;
+    u64 *c2;                    // scratch [count][n][N]
+    u64 *accq;                  // scratch [count][2][n][N]
+    u64 *plift;                 // scratch [count][2][N]
+    u64 *lift2;                 // scratch [count][2][N]
+    const ulonglong2 *evk;      // [n_data][2][n_data + 1][N] (value, Shoup)
+    u32 n;                      // limbs at the current level
+    u32 count;
+    DevCtx ctx;
+};
+
+enum EvalKernel {
+    EK_KS_DIGITS = 0,
+    EK_KS_MODUP,
+    EK_KS_MODDOWN,
+    EK_RS_LIFT,
+    EK_RS,
+    EK_MRR_LAST,
+    EK_MRR_REST,
+    EK_COUNT
+};
+
+// Launchers of one polynomial degree N = 2^log_n. Shapes are given by
+// log_b (words per CTA = 2^log_b, cluster of N / 2^log_b CTAs); 0 picks the
+// default shape of the degree.
+struct DegreeOps {
+    int log_n;
+    int default_log_b;
+    // Plain transform of a uniform batch or a job list, one cluster per limb.
+    cudaError_t (*ntt)(const NttLaunch &a, int log_b, bool inverse, cudaStream_t s);
+    // Persistent transform over a job list with `grid_clusters` clusters.
+    cudaError_t (*ntt_persistent)(const NttLaunch &a, int log_b, bool inverse, u32 grid_clusters,
+                                  cudaStream_t s);
+    // Largest number of co-resident clusters of the persistent kernel.
+    int (*max_clusters)(int log_b, bool inverse);
+    // Evaluation kernels over `items` clusters.
+    cudaError_t (*eval)(EvalKernel k, const EvalArgs &a, u32 items, cudaStream_t s);
+    // Is the shape log_b built for this degree?
+    bool (*has_shape)(int log_b);
+};
+
+const DegreeOps *degree_ops(int log_n);
+
+}  // namespace he

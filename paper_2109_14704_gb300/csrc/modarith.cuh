@@ -1,0 +1,115 @@
+// modarith.cuh -- 64-bit modular arithmetic on the integer pipes (sm_103a).
+//
+// Moduli are primes p < 2^60 (Sec. III-A-1). Products are built from
+// __umul64hi and the low 64-bit product; no 128-bit type is used on the device.
+//
+//  * Shoup multiplication by a constant W with precomputed W' = floor(W 2^64/p)
+//    (the W' of Algorithm 1): for any Y < 2^64, T = W Y - floor(W' Y / 2^64) p
+//    lies in [0, 2p).
+//  * Harvey's lazy forward butterfly (Algorithm 1): X, Y in [0, 4p) ->
+//    X' = X + W Y, Y' = X - W Y (mod p), both in [0, 4p).
+//  * The matching Gentleman-Sande inverse butterfly on [0, 2p).
+//  * Barrett reduction of a 128-bit z < 2 p^2 (Barrett 1986; the mad_mod of
+//    Sec. III-A-1 feeds it a0 b1 + a1 b0 and reduces once).
+#pragma once
+#include <stdint.h>
+
+namespace he {
+
+typedef uint64_t u64;
+typedef uint32_t u32;
+
+// Constants of one prime, resident in device memory.
+struct PrimeConst {
+    u64 p;
+    u64 two_p;
+    u64 mu;          // floor(2^(2b+2) / p), b = bit length of p
+    u64 ninv;        // N^-1 mod p
+    u64 ninv_sh;     // its Shoup quotient
+    u64 w1ninv;      // psi^-brv(1) * N^-1 mod p (last inverse stage)
+    u64 w1ninv_sh;
+    u32 bits;        // b
+    u32 pad;
+};
+
+__device__ __forceinline__ u64 reduce_once(u64 x, u64 m) { return x >= m ? x - m : x; }
+
+__device__ __forceinline__ u64 add_mod(u64 a, u64 b, u64 p) { return reduce_once(a + b, p); }
+
+__device__ __forceinline__ u64 sub_mod(u64 a, u64 b, u64 p) { return a >= b ? a - b : a + p - b; }
+
+// W * Y mod p in [0, 2p) for any Y < 2^64 (Shoup).
+__device__ __forceinline__ u64 mul_shoup_lazy(u64 y, u64 w, u64 w_sh, u64 p)
+{
+    return w * y - __umul64hi(w_sh, y) * p;
+}
+
+__device__ __forceinline__ u64 mul_shoup(u64 y, u64 w, u64 w_sh, u64 p)
+{
+    return reduce_once(mul_shoup_lazy(y, w, w_sh, p), p);
+}
+
+// Algorithm 1: x, y in [0, 4p) -> x + W y, x - W y (mod p), both in [0, 4p).
+__device__ __forceinline__ void ct_butterfly(u64 &x, u64 &y, u64 w, u64 w_sh, u64 p, u64 two_p)
+{
+    u64 X = reduce_once(x, two_p);
+    u64 T = mul_shoup_lazy(y, w, w_sh, p);
+    x = X + T;
+    y = X - T + two_p;
+}
+
+// Inverse (Gentleman-Sande) butterfly on [0, 2p):
+// x, y -> x + y, (x - y) W^-1 (mod p), both in [0, 2p).
+__device__ __forceinline__ void gs_butterfly(u64 &x, u64 &y, u64 w, u64 w_sh, u64 p, u64 two_p)
+{
+    u64 X = reduce_once(x + y, two_p);
+    u64 T = x - y + two_p;
+    y = mul_shoup_lazy(T, w, w_sh, p);
+    x = X;
+}
+
+// 128-bit product as (hi, lo).
+__device__ __forceinline__ void mul_wide(u64 a, u64 b, u64 &hi, u64 &lo)
+{
+    lo = a * b;
+    hi = __umul64hi(a, b);
+}
+
+// Barrett reduction of z = (hi, lo) < 2 p^2 with p of b bits (3 <= b <= 60),
+// mu = floor(2^(2b+2) / p). With q1 = floor(z / 2^(b-2)) and
+// q3 = floor(q1 mu / 2^(b+4)): z/p - q3 < 2^(b-2)/p + q1/2^(b+4) + 1 < 2,
+// so z - q3 p lies in [0, 2p) and one conditional subtraction finishes.
+// q1 < 2^(b+3) and mu < 2^(b+3) fit one word each.
+__device__ __forceinline__ u64 barrett_reduce(u64 hi, u64 lo, u64 p, u64 mu, u32 b)
+{
+    const u32 s1 = b - 2;                        // 1 .. 58
+    u64 q1 = (hi << (64 - s1)) | (lo >> s1);
+    u64 phi, plo;
+    mul_wide(q1, mu, phi, plo);
+    const u32 s2 = b + 4;                        // 7 .. 64
+    u64 q3 = (phi << (64 - s2)) | ((plo >> 1) >> (s2 - 1));
+    if (s2 == 64) q3 = phi;
+    u64 r = lo - q3 * p;
+    return reduce_once(r, p);
+}
+
+__device__ __forceinline__ u64 mul_mod(u64 a, u64 b, const PrimeConst &c)
+{
+    u64 hi, lo;
+    mul_wide(a, b, hi, lo);
+    return barrett_reduce(hi, lo, c.p, c.mu, c.bits);
+}
+
+// mad_mod of Sec. III-A-1: a0 b1 + a1 b0 mod p with a single reduction
+// (the 128-bit sum is below 2 p^2).
+__device__ __forceinline__ u64 mad2_mod(u64 a0, u64 b1, u64 a1, u64 b0, const PrimeConst &c)
+{
+    u64 h0, l0, h1, l1;
+    mul_wide(a0, b1, h0, l0);
+    mul_wide(a1, b0, h1, l1);
+    u64 lo = l0 + l1;
+    u64 hi = h0 + h1 + (lo < l0 ? 1 : 0);
+    return barrett_reduce(hi, lo, c.p, c.mu, c.bits);
+}
+
+}  // namespace he

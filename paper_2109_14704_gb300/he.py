@@ -1,0 +1,358 @@
+"""Python binding of libhe.so: the same entry points as include/he.h, with
+argument marshalling only (tensor data pointers, the current CUDA stream,
+host arrays). Every step of the computation runs in the library's CUDA
+kernels; there is no CPU fallback. If the library cannot be built or loaded,
+every call raises.
+
+Device buffers are torch tensors of dtype int64 or uint64 holding the 64-bit
+words (the bits are used as is), contiguous and 16-byte aligned.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+_vp = ctypes.c_void_p
+
+HE_OK, HE_EINVAL, HE_ENOMEM, HE_ECUDA, HE_EUNSUPPORTED, HE_ETIMEOUT = 0, -1, -2, -3, -4, -5
+_NAMES = {-1: "HE_EINVAL", -2: "HE_ENOMEM", -3: "HE_ECUDA", -4: "HE_EUNSUPPORTED", -5: "HE_ETIMEOUT"}
+
+
+class HeError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class PolyDesc(ctypes.Structure):
+    _fields_ = [("data", _vp), ("tables", _vp), ("N", ctypes.c_uint32), ("limbs", ctypes.c_uint32),
+                ("first_prime", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+class NttShape(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_uint32), ("log_block", ctypes.c_uint32)]
+
+
+_SIGS = {
+    "he_last_error": (ctypes.c_int32, [ctypes.c_char_p, ctypes.c_size_t]),
+    "he_version": (ctypes.c_uint32, []),
+    "he_primes_generate": (ctypes.c_int32, [ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32, _u64p,
+                                            ctypes.c_uint32, _u64p]),
+    "he_ntt_tables_create": (ctypes.c_int32, [ctypes.c_uint32, ctypes.c_uint32, _u64p, ctypes.POINTER(_vp)]),
+    "he_ntt_tables_destroy": (ctypes.c_int32, [_vp]),
+    "he_ntt_tables_psi": (ctypes.c_int32, [_vp, ctypes.c_uint32, _u64p]),
+    "he_ntt_fwd": (ctypes.c_int32, [_vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, _u64p, _vp, _vp]),
+    "he_ntt_inv": (ctypes.c_int32, [_vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, _u64p, _vp, _vp]),
+    "he_ntt_fwd_naive": (ctypes.c_int32, [_vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, _u64p, _vp,
+                                          _vp]),
+    "he_ntt_inv_naive": (ctypes.c_int32, [_vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, _u64p, _vp,
+                                          _vp]),
+    "he_dyadic_mul": (ctypes.c_int32, [_vp, _vp, _vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, _u64p,
+                                       _vp, _vp]),
+    "he_context_create": (ctypes.c_int32, [ctypes.c_uint32, ctypes.c_uint32, _u64p, ctypes.c_uint64,
+                                           ctypes.POINTER(_vp)]),
+    "he_context_destroy": (ctypes.c_int32, [_vp]),
+    "he_relin_key_upload": (ctypes.c_int32, [_vp, _u64p, ctypes.POINTER(_vp)]),
+    "he_relin_key_destroy": (ctypes.c_int32, [_vp]),
+    "he_ct_mul": (ctypes.c_int32, [_vp, _vp, _vp, _vp, ctypes.c_uint32, _vp]),
+    "he_relin_scratch_bytes": (ctypes.c_size_t, [_vp, ctypes.c_uint32]),
+    "he_relin": (ctypes.c_int32, [_vp, _vp, _vp, _vp, ctypes.c_uint32, _vp, ctypes.c_size_t, _vp]),
+    "he_rescale_scratch_bytes": (ctypes.c_size_t, [_vp, ctypes.c_uint32]),
+    "he_rescale": (ctypes.c_int32, [_vp, _vp, _vp, ctypes.c_uint32, _vp, ctypes.c_size_t, _vp]),
+    "he_mul_relin_rescale_scratch_bytes": (ctypes.c_size_t, [_vp, ctypes.c_uint32, ctypes.c_uint32]),
+    "he_mul_relin_rescale": (ctypes.c_int32, [_vp, _vp, _vp, ctypes.c_uint32, _vp, _vp, ctypes.c_uint32, _vp,
+                                              ctypes.c_size_t, _vp]),
+    "he_ntt_plan_create": (ctypes.c_int32, [ctypes.POINTER(PolyDesc), ctypes.c_uint32, ctypes.POINTER(NttShape),
+                                            ctypes.c_uint32, ctypes.POINTER(_vp)]),
+    "he_ntt_plan_fwd": (ctypes.c_int32, [_vp, _vp]),
+    "he_ntt_plan_inv": (ctypes.c_int32, [_vp, _vp]),
+    "he_plan_destroy": (ctypes.c_int32, [_vp]),
+    "he_plan_launches": (ctypes.c_uint32, [_vp]),
+    "he_butterfly_probe": (ctypes.c_int32, [_vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, _vp]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_needed: bool = True):
+    """Load libhe.so (building it first if its sources are newer)."""
+    global _lib
+    if _lib is None:
+        if build_if_needed:
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(f"CUDA library missing: {_build.LIB} (run __graft_entry__.build())")
+        lib = ctypes.CDLL(_build.LIB)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def declared_symbols() -> list[str]:
+    return sorted(_SIGS)
+
+
+def last_error() -> str:
+    buf = ctypes.create_string_buffer(512)
+    load().he_last_error(buf, 512)
+    return buf.value.decode()
+
+
+def _check(status: int):
+    if status != HE_OK:
+        raise HeError(status, last_error())
+
+
+def _ptr(x):
+    """Device pointer of a torch tensor (or an int address, or None)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if not x.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not x.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    if x.element_size() != 8:
+        raise ValueError("expected 64-bit words (int64 or uint64)")
+    return x.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _host_u64(values) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(values, dtype=np.uint64))
+
+
+def _hp(a: np.ndarray):
+    return a.ctypes.data_as(_u64p)
+
+
+def version() -> int:
+    return int(load().he_version())
+
+
+def primes_generate(bits: int, two_n: int, count: int, exclude=()) -> list[int]:
+    ex = _host_u64(list(exclude) or [0])
+    out = np.zeros(max(count, 1), dtype=np.uint64)
+    _check(load().he_primes_generate(bits, two_n, count, _hp(ex), len(exclude), _hp(out)))
+    return [int(v) for v in out[:count]]
+
+
+def chain_primes(N: int, data_bits, special_bits: int, two_n: int | None = None):
+    """Data primes of the given bit sizes then one special prime, each the
+    largest unused prime of its size that is 1 mod 2N (or mod two_n)."""
+    two_n = two_n or 2 * N
+    used: list[int] = []
+    for b in data_bits:
+        used += primes_generate(b, two_n, 1, exclude=used)
+    P = primes_generate(special_bits, two_n, 1, exclude=used)[0]
+    return used, P
+
+
+class NttTables:
+    """he_ntt_tables: device-resident twiddles of `moduli` at degree N."""
+
+    def __init__(self, N: int, moduli):
+        self.N = int(N)
+        self.moduli = [int(q) for q in moduli]
+        self._m = _host_u64(self.moduli)
+        h = _vp()
+        _check(load().he_ntt_tables_create(self.N, len(self.moduli), _hp(self._m), ctypes.byref(h)))
+        self.handle = h
+
+    def psi(self, index: int) -> int:
+        out = np.zeros(1, dtype=np.uint64)
+        _check(load().he_ntt_tables_psi(self.handle, index, _hp(out)))
+        return int(out[0])
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().he_ntt_tables_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _moduli_arg(tables: NttTables, limbs: int, moduli):
+    m = _host_u64(tables.moduli[:limbs] if moduli is None else list(moduli)[:limbs])
+    return m
+
+
+def ntt_fwd(poly, N, limbs, count, tables: NttTables, moduli=None, stream=None):
+    m = _moduli_arg(tables, limbs, moduli)
+    _check(load().he_ntt_fwd(_ptr(poly), N, limbs, count, _hp(m), tables.handle, _stream(stream)))
+
+
+def ntt_inv(poly, N, limbs, count, tables: NttTables, moduli=None, stream=None):
+    m = _moduli_arg(tables, limbs, moduli)
+    _check(load().he_ntt_inv(_ptr(poly), N, limbs, count, _hp(m), tables.handle, _stream(stream)))
+
+
+def ntt_fwd_naive(poly, N, limbs, count, tables: NttTables, moduli=None, stream=None):
+    m = _moduli_arg(tables, limbs, moduli)
+    _check(load().he_ntt_fwd_naive(_ptr(poly), N, limbs, count, _hp(m), tables.handle, _stream(stream)))
+
+
+def ntt_inv_naive(poly, N, limbs, count, tables: NttTables, moduli=None, stream=None):
+    m = _moduli_arg(tables, limbs, moduli)
+    _check(load().he_ntt_inv_naive(_ptr(poly), N, limbs, count, _hp(m), tables.handle, _stream(stream)))
+
+
+def dyadic_mul(out, a, b, N, limbs, count, tables: NttTables, moduli=None, stream=None):
+    m = _moduli_arg(tables, limbs, moduli)
+    _check(load().he_dyadic_mul(_ptr(out), _ptr(a), _ptr(b), N, limbs, count, _hp(m), tables.handle,
+                                _stream(stream)))
+
+
+class Context:
+    """he_context: modulus chain q_0..q_L and special prime P at degree N."""
+
+    def __init__(self, N: int, data_moduli, special_modulus: int):
+        self.N = int(N)
+        self.data_moduli = [int(q) for q in data_moduli]
+        self.P = int(special_modulus)
+        m = _host_u64(self.data_moduli)
+        h = _vp()
+        _check(load().he_context_create(self.N, len(self.data_moduli), _hp(m), self.P, ctypes.byref(h)))
+        self.handle = h
+
+    @property
+    def n_data(self) -> int:
+        return len(self.data_moduli)
+
+    def relin_scratch_bytes(self, level: int) -> int:
+        return int(load().he_relin_scratch_bytes(self.handle, level))
+
+    def rescale_scratch_bytes(self, level: int) -> int:
+        return int(load().he_rescale_scratch_bytes(self.handle, level))
+
+    def mrr_scratch_bytes(self, level: int, count: int) -> int:
+        return int(load().he_mul_relin_rescale_scratch_bytes(self.handle, level, count))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().he_context_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class RelinKey:
+    """he_relin_key: evk [n_data][2][n_data+1][N] (host array) uploaded."""
+
+    def __init__(self, ctx: Context, evk_host: np.ndarray):
+        evk = _host_u64(evk_host)
+        nd = ctx.n_data
+        if evk.shape != (nd, 2, nd + 1, ctx.N):
+            raise ValueError(f"evk must have shape {(nd, 2, nd + 1, ctx.N)}, got {evk.shape}")
+        h = _vp()
+        _check(load().he_relin_key_upload(ctx.handle, _hp(evk), ctypes.byref(h)))
+        self.handle = h
+        self.ctx = ctx
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().he_relin_key_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ct_mul(out3, ct_a, ct_b, ctx: Context, level: int, stream=None):
+    _check(load().he_ct_mul(_ptr(out3), _ptr(ct_a), _ptr(ct_b), ctx.handle, level, _stream(stream)))
+
+
+def relin(ct_out2, ct_in3, key: RelinKey, ctx: Context, level: int, scratch, stream=None):
+    _check(load().he_relin(_ptr(ct_out2), _ptr(ct_in3), key.handle, ctx.handle, level, _ptr(scratch),
+                           scratch.numel() * 8, _stream(stream)))
+
+
+def rescale(ct_out, ct_in, ctx: Context, level: int, scratch, stream=None):
+    _check(load().he_rescale(_ptr(ct_out), _ptr(ct_in), ctx.handle, level, _ptr(scratch), scratch.numel() * 8,
+                             _stream(stream)))
+
+
+def mul_relin_rescale(ct_out, ct_a, ct_b, count: int, key: RelinKey, ctx: Context, level: int, scratch,
+                      stream=None):
+    _check(load().he_mul_relin_rescale(_ptr(ct_out), _ptr(ct_a), _ptr(ct_b), count, key.handle, ctx.handle, level,
+                                       _ptr(scratch), scratch.numel() * 8, _stream(stream)))
+
+
+class NttPlan:
+    """he_plan over a list of (tensor, tables, N, limbs, first_prime)."""
+
+    def __init__(self, polys, shapes=None):
+        arr = (PolyDesc * max(len(polys), 1))()
+        self._keep = []
+        for i, (data, tables, N, limbs, first) in enumerate(polys):
+            arr[i].data = _ptr(data)
+            arr[i].tables = tables.handle.value
+            arr[i].N = N
+            arr[i].limbs = limbs
+            arr[i].first_prime = first
+            self._keep.append((data, tables))
+        shapes = shapes or {}
+        sh = (NttShape * max(len(shapes), 1))()
+        for i, (N, lb) in enumerate(shapes.items()):
+            sh[i].N, sh[i].log_block = N, lb
+        h = _vp()
+        _check(load().he_ntt_plan_create(arr, len(polys), sh, len(shapes), ctypes.byref(h)))
+        self.handle = h
+
+    def fwd(self, stream=None):
+        _check(load().he_ntt_plan_fwd(self.handle, _stream(stream)))
+
+    def inv(self, stream=None):
+        _check(load().he_ntt_plan_inv(self.handle, _stream(stream)))
+
+    @property
+    def launches(self) -> int:
+        return int(load().he_plan_launches(self.handle))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().he_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def butterfly_probe(sink, blocks: int, threads: int, iters: int, stream=None):
+    """Launch the register-resident butterfly probe (16 * iters butterflies
+    per thread)."""
+    _check(load().he_butterfly_probe(_ptr(sink), blocks, threads, iters, _stream(stream)))

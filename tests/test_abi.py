@@ -1,0 +1,100 @@
+"""The C ABI without a GPU: libhe.so loads, exports every entry point that
+include/he.h declares, generates the same RNS primes as the oracle, and
+rejects bad arguments on the host before touching the device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+import sympy
+
+import oracle
+from paper_2109_14704_gb300 import he
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "he.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(he_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = he.load()
+    declared = _declared()
+    assert len(declared) >= 20
+    missing = [s for s in declared if not hasattr(lib, s)]
+    assert not missing, missing
+    # the binding covers the whole ABI too
+    assert set(declared) == set(he.declared_symbols())
+
+
+def test_version():
+    assert he.version() == 0x000100
+
+
+@pytest.mark.parametrize("bits,two_n", [(60, 2 ** 13), (60, 2 ** 16), (50, 2 ** 15), (40, 2 ** 14), (31, 2 ** 11)])
+def test_primes_match_oracle(bits, two_n):
+    assert he.primes_generate(bits, two_n, 5) == oracle.find_primes(bits, two_n, 5)
+
+
+def test_chain_primes_match_oracle():
+    for N, bits in [(16384, [60] + [50] * 6), (8192, [60, 40, 40]), (32768, [60] + [50] * 15)]:
+        assert he.chain_primes(N, bits, 60) == oracle.chain_primes(N, bits, 60)
+
+
+
+def test_invalid_arguments_rejected_on_host():
+    lib = he.load()
+    h = ctypes.c_void_p()
+    q = np.array(he.primes_generate(60, 2 * 4096, 1), dtype=np.uint64)
+    qp = q.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+    # N not a power of two, N out of range
+    assert lib.he_ntt_tables_create(3000, 1, qp, ctypes.byref(h)) == he.HE_EINVAL
+    assert lib.he_ntt_tables_create(1 << 17, 1, qp, ctypes.byref(h)) == he.HE_EUNSUPPORTED
+    assert lib.he_ntt_tables_create(512, 1, qp, ctypes.byref(h)) == he.HE_EUNSUPPORTED
+    # modulus not 1 mod 2N, not prime, too large
+    composite = next(8192 * k + 1 for k in range(3, 100) if not sympy.isprime(8192 * k + 1))
+    for bad in (int(q[0]) + 2, (1 << 60) + 1, composite):
+        b = np.array([bad], dtype=np.uint64)
+        assert lib.he_ntt_tables_create(4096, 1, b.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                        ctypes.byref(h)) == he.HE_EINVAL
+    assert "modulus" in he.last_error()
+    # null output handle, no moduli
+    assert lib.he_ntt_tables_create(4096, 1, qp, None) == he.HE_EINVAL
+    assert lib.he_ntt_tables_create(4096, 0, qp, ctypes.byref(h)) == he.HE_EINVAL
+    # null tables on a transform
+    assert lib.he_ntt_fwd(None, 4096, 1, 1, qp, None, None) == he.HE_EINVAL
+    # contexts: too many primes, duplicates, small primes
+    assert lib.he_context_create(4096, 0, qp, int(q[0]), ctypes.byref(h)) == he.HE_EINVAL
+    assert lib.he_context_create(4096, 1, qp, int(q[0]), ctypes.byref(h)) == he.HE_EINVAL
+    assert "twice" in he.last_error()
+    small = np.array(he.primes_generate(20, 2 * 4096, 1), dtype=np.uint64)
+    assert lib.he_context_create(4096, 1, small.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), int(q[0]),
+                                 ctypes.byref(h)) == he.HE_EINVAL
+    # prime search out of range
+    out = np.zeros(4, dtype=np.uint64)
+    assert lib.he_primes_generate(61, 8192, 1, None, 0, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))) == \
+        he.HE_EINVAL
+    assert lib.he_primes_generate(10, 1 << 12, 4, None, 0, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))) == \
+        he.HE_EINVAL
+    # plans with missing tables
+    d = (he.PolyDesc * 1)()
+    d[0].N, d[0].limbs = 4096, 1
+    assert lib.he_ntt_plan_create(d, 1, None, 0, ctypes.byref(h)) == he.HE_EINVAL
+
+
+def test_error_message_buffer():
+    lib = he.load()
+    buf = ctypes.create_string_buffer(8)
+    assert lib.he_ntt_tables_create(3000, 1, None, None) == he.HE_EINVAL
+    assert lib.he_last_error(buf, 8) == 0 and len(buf.value) == 7
+    assert lib.he_last_error(None, 0) == he.HE_EINVAL
+
+
+def test_error_type():
+    with pytest.raises(he.HeError) as e:
+        he.primes_generate(61, 8192, 1)
+    assert e.value.status == he.HE_EINVAL
