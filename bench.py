@@ -54,6 +54,9 @@ def _args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle sample")
+    ap.add_argument("--profile-case", choices=["ntt", "mrr", "probe"],
+                    help="run one small case of a kernel family and exit (for profilers)")
+    ap.add_argument("--instances", type=int, default=64, help="NTT instances of --profile-case ntt")
     return ap.parse_args()
 
 
@@ -458,9 +461,58 @@ def run_reference(args, rank, world):
     }), flush=True)
 
 
+def profile_case(args):
+    """A small case of one kernel family: `ntt` transforms args.instances x 8
+    limbs at N = 2^15 (64 instances = 128 MiB, above the L2 size) forward
+    then inverse, `mrr` runs one MulLinRS batch of 8 pairs on the CKKS
+    workload, `probe` the butterfly probe. Each runs `--steps` times."""
+    import numpy as np
+    import torch
+
+    from paper_2109_14704_gb300 import he
+    from paper_2109_14704_gb300.synth import Rng
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    he.load()
+    if args.profile_case == "ntt":
+        N = 1 << NTT_LOG_N
+        qs = _ntt_moduli()
+        tables = he.NttTables(N, qs)
+        r = Rng(1)
+        d = torch.from_numpy(np.stack([r.uniform_limbs(qs, N) for _ in range(args.instances)]).view(np.int64)).to(dev)
+        for _ in range(args.steps):
+            he.ntt_fwd(d, N, NTT_LIMBS, args.instances, tables)
+            he.ntt_inv(d, N, NTT_LIMBS, args.instances, tables)
+    elif args.profile_case == "mrr":
+        data, P = he.chain_primes(MRR_N, MRR_BITS, 60)
+        ctx = he.Context(MRR_N, data, P)
+        L, count = len(data) - 1, 8
+        rm = Rng(2)
+        evk = np.stack([np.stack([rm.uniform_limbs(data + [P], MRR_N) for _ in range(2)]) for _ in range(len(data))])
+        key = he.RelinKey(ctx, evk)
+        mk = lambda: torch.from_numpy(np.stack([np.stack([rm.uniform_limbs(data, MRR_N) for _ in range(2)])
+                                                 for _ in range(count)]).view(np.int64)).to(dev)
+        ca, cb = mk(), mk()
+        out = torch.empty((count, 2, L, MRR_N), dtype=torch.int64, device=dev)
+        scratch = torch.empty(ctx.mrr_scratch_bytes(L, count) // 8, dtype=torch.int64, device=dev)
+        for _ in range(args.steps):
+            he.mul_relin_rescale(out, ca, cb, count, key, ctx, L, scratch)
+    else:
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        sink = torch.empty(sms * 8 * 256, dtype=torch.int64, device=dev)
+        for _ in range(args.steps):
+            he.butterfly_probe(sink, sms * 8, 256, 1024)
+    torch.cuda.synchronize()
+    print(f"profile case {args.profile_case}: done")
+
+
 def main():
     args = _args()
     rank, world, local = _dist()
+    if args.profile_case:
+        profile_case(args)
+        return
     if args.impl == "reference":
         run_reference(args, rank, world)
     else:
