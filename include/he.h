@@ -179,6 +179,26 @@ he_status he_mul_relin_rescale(uint64_t *ct_out, const uint64_t *ct_a, const uin
                                uint32_t level, void *scratch, size_t scratch_bytes,
                                he_stream_t stream);
 
+/* Allocation-free MulLinRS. The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory when they need the
+ * routine -- code running during stream capture, latency-critical serving
+ * paths that must not block on the device allocator, and embedders whose
+ * device memory is budgeted by another runtime. It computes exactly what
+ * he_mul_relin_rescale computes (same arguments minus the scratch buffer),
+ * taking its scratch from a buffer of HE_NOALLOC_SCRATCH_BYTES compiled into
+ * the library, held on every GPU that loads the library until the process
+ * exits. It never allocates. Requests needing more scratch than that
+ * ((3 (level + 1) + 4) * N * 8 bytes per pair) return HE_EINVAL with a
+ * message. The first call on each device resolves the buffer's address
+ * (cudaGetSymbolAddress, with that device current), so make that first call
+ * before any stream capture. All calls share the buffer: calls that may
+ * overlap on the GPU race and must be ordered by the caller (e.g. one
+ * stream). No scratch word needs to start at zero. */
+#define HE_NOALLOC_SCRATCH_BYTES (16u << 20)
+he_status he_mul_relin_rescale_noalloc(uint64_t *ct_out, const uint64_t *ct_a, const uint64_t *ct_b,
+                                       uint32_t count, const he_relin_key *key, const he_context *ctx,
+                                       uint32_t level, he_stream_t stream);
+
 /* ---- batched plans (Sec. III-B parallelism over limbs and instances) -------- */
 
 /* One polynomial of a batched NTT: `limbs` limbs of degree N at `data`

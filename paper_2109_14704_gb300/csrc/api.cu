@@ -11,6 +11,7 @@
 
 #include <algorithm>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -826,6 +827,68 @@ extern "C" he_status he_ntt_plan_fwd(const he_plan *plan, he_stream_t stream) { 
 extern "C" he_status he_ntt_plan_inv(const he_plan *plan, he_stream_t stream) { return plan_run(plan, stream, true); }
 
 extern "C" uint32_t he_plan_launches(const he_plan *plan) { return plan ? (uint32_t)plan->groups.size() : 0; }
+
+// ------------------------------------------- allocation-free MulLinRS
+//
+// Some callers cannot allocate device memory at the point where they need a
+// mul-relin-rescale: code that runs while a stream is being captured (plain
+// cudaMalloc is not allowed there), latency-critical serving paths that must
+// never block on the device allocator (cudaMalloc can synchronise the whole
+// device), and embedders whose device memory is owned and budgeted by another
+// runtime. he_mul_relin_rescale_noalloc serves them: it runs the same kernels
+// as he_mul_relin_rescale with the key-switching and rescale scratch taken
+// from a fixed buffer compiled into this library, so the call itself never
+// allocates.
+//
+// The buffer is a file-scope __device__ array of HE_NOALLOC_SCRATCH_BYTES;
+// every GPU that loads the library holds it until the process exits. Host
+// code cannot use the array's name as a device address, so the first call on
+// each device resolves the address with cudaGetSymbolAddress (with that
+// device current) and caches it; that first call should therefore come
+// before any stream capture. All calls share the one buffer: calls that may
+// overlap on the GPU (different streams without ordering between them) race
+// on it and must be serialised by the caller. Each kernel writes every
+// scratch word it later reads within the same call, so nothing in the buffer
+// needs to start at zero and the contents left by a previous call are
+// harmless.
+static const size_t kNoAllocScratchBytes = (size_t)HE_NOALLOC_SCRATCH_BYTES;
+static __device__ __align__(256) u64 g_noalloc_scratch[kNoAllocScratchBytes / 8];
+
+static std::mutex g_noalloc_mutex;
+static void *g_noalloc_addr[256];   // per device ordinal, resolved once
+
+static he_status noalloc_scratch_address(void **out)
+{
+    int dev = 0;
+    HE_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) return fail(HE_EUNSUPPORTED, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(built-in scratch)");
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return HE_OK;
+}
+
+extern "C" he_status he_mul_relin_rescale_noalloc(uint64_t *ct_out, const uint64_t *ct_a, const uint64_t *ct_b,
+                                                  uint32_t count, const he_relin_key *key, const he_context *ctx,
+                                                  uint32_t level, he_stream_t stream)
+{
+    if (he_status s = check_level(ctx, level, true)) return s;
+    if (count == 0) return HE_OK;
+    const size_t need = mrr_words(ctx, level + 1) * 8 * (size_t)count;
+    if (need > kNoAllocScratchBytes)
+        return fail(HE_EINVAL,
+                    "mul-relin-rescale of %u pair(s) at N = %u, level %u needs %zu bytes of scratch; the built-in "
+                    "buffer holds %zu bytes (use he_mul_relin_rescale with caller scratch, or fewer pairs)",
+                    count, ctx->N, level, need, kNoAllocScratchBytes);
+    void *scratch = nullptr;
+    if (he_status s = noalloc_scratch_address(&scratch)) return s;
+    return he_mul_relin_rescale(ct_out, ct_a, ct_b, count, key, ctx, level, scratch, kNoAllocScratchBytes, stream);
+}
 
 // ------------------------------------------------------- degree dispatch
 

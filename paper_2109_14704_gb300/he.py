@@ -75,6 +75,8 @@ _SIGS = {
     "he_plan_destroy": (ctypes.c_int32, [_vp]),
     "he_plan_launches": (ctypes.c_uint32, [_vp]),
     "he_butterfly_probe": (ctypes.c_int32, [_vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, _vp]),
+    "he_mul_relin_rescale_noalloc": (ctypes.c_int32, [_vp, _vp, _vp, ctypes.c_uint32, _vp, _vp, ctypes.c_uint32,
+                                                      _vp]),
 }
 
 
@@ -356,3 +358,17 @@ def butterfly_probe(sink, blocks: int, threads: int, iters: int, stream=None):
     """Launch the register-resident butterfly probe (16 * iters butterflies
     per thread)."""
     _check(load().he_butterfly_probe(_ptr(sink), blocks, threads, iters, _stream(stream)))
+
+
+# Bytes of the scratch buffer built into the library (HE_NOALLOC_SCRATCH_BYTES).
+NOALLOC_SCRATCH_BYTES = 16 << 20
+
+
+def mul_relin_rescale_noalloc(ct_out, ct_a, ct_b, count: int, key: RelinKey, ctx: Context, level: int,
+                              stream=None):
+    """MulLinRS without a scratch argument, for callers that cannot allocate
+    device memory at call time (stream capture, allocator-free serving paths,
+    externally budgeted memory): the library's built-in buffer is used.
+    Calls that can overlap on the GPU share that buffer and must be ordered."""
+    _check(load().he_mul_relin_rescale_noalloc(_ptr(ct_out), _ptr(ct_a), _ptr(ct_b), count, key.handle, ctx.handle,
+                                               level, _stream(stream)))
