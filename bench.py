@@ -57,7 +57,12 @@ def _args():
     ap.add_argument("--profile-case", choices=["ntt", "mrr", "probe"],
                     help="run one small case of a kernel family and exit (for profilers)")
     ap.add_argument("--instances", type=int, default=64, help="NTT instances of --profile-case ntt")
-    return ap.parse_args()
+    ap.add_argument("--skip", default="", help="comma list of sub-benchmarks to skip: uneven,matrix,serving")
+    ap.add_argument("--serve-requests", type=int, default=4000)
+    ap.add_argument("--no-tune-cache", action="store_true", help="always re-run the autotuner")
+    a = ap.parse_args()
+    a.skip = set(x for x in a.skip.split(",") if x)
+    return a
 
 
 def _dist():
@@ -159,7 +164,7 @@ def run_ours(args, rank, world, local):
     import numpy as np
     import torch
 
-    from paper_2109_14704_gb300 import he
+    from paper_2109_14704_gb300 import autotune, he
     from paper_2109_14704_gb300.synth import Rng
 
     torch.cuda.set_device(local)
@@ -199,6 +204,11 @@ def run_ours(args, rank, world, local):
     def step_batched():
         he.ntt_fwd(d, N, NTT_LIMBS, NTT_INSTANCES, tables, stream=stream)
         he.ntt_inv(d, N, NTT_LIMBS, NTT_INSTANCES, tables, stream=stream)
+
+    # pick the transform shape for this batch (checked, timed, applied)
+    tune = autotune.tune_uniform(N, NTT_LIMBS, NTT_INSTANCES, moduli=qs, reps=5, warmup=2,
+                                 cache_path=None if args.no_tune_cache else autotune.DEFAULT_CACHE)
+    d.copy_(pinned)
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -280,6 +290,9 @@ def run_ours(args, rank, world, local):
 
     ms_mrr_plain = max_over_ranks(_time_steps(mrr_plain, max(2, args.steps // 5), 1, stream, barrier))
 
+    uneven = bench_uneven(args, stream, barrier) if "uneven" not in args.skip else None
+    matrix = bench_matrix(args, stream, barrier) if "matrix" not in args.skip else None
+
     # end to end through host buffers: H2D, forward, inverse, D2H every step
     back = torch.empty_like(pinned).pin_memory()
 
@@ -291,6 +304,8 @@ def run_ours(args, rank, world, local):
 
     ms_e2e = max_over_ranks(_time_steps(step_e2e, max(3, args.steps // 2), 1, stream, barrier))
     clk = clocks.stop()
+    del pinned, back
+    serve = bench_serving(args) if "serving" not in args.skip else None
     assert torch.equal(back, pinned), "round trip changed the data"
 
     # integer roof: register-resident butterflies on every SM
@@ -341,6 +356,11 @@ def run_ours(args, rank, world, local):
             "inv_limbs_per_s": world * limbs_total / (inv / 1e3),
             "fwd_ms": fwd, "inv_ms": inv, "speedup_vs_naive": ms_naive / ms,
         },
+        "autotune": {"shape": {"log_block": tune["shape"][0], "log_thread_words": tune["shape"][1]},
+                     "candidates": [{"shape": c["shape"], "ms_fwd_inv": c.get("ms_fwd_inv")} for c in tune["candidates"]]},
+        "uneven_batch": uneven,
+        "matrix_mul_relin_rescale": matrix,
+        "serving": serve,
         "mul_relin_rescale": {
             "workload": "N=16384, data primes 60+6x50, special 60, 64 ciphertext pairs, level 6 -> 5",
             "batched_per_s": world * MRR_COUNT / (ms_mrr / 1e3),
@@ -363,8 +383,8 @@ def run_ours(args, rank, world, local):
             "algorithmic_bytes_per_launch": bytes_per_launch,
             "butterflies_per_launch": bfly_per_launch,
         },
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": pinned.numel() * 8,
-                "d2h_bytes_per_step": back.numel() * 8},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * limbs_total * N,
+                "d2h_bytes_per_step": 8 * limbs_total * N},
         "gpu_launches": 2 * args.steps,
         "clocks": clk,
     }
@@ -383,6 +403,127 @@ def _measured_peaks() -> dict:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         return {}
+
+
+# ------------------------------------------------------ other workloads
+
+def bench_uneven(args, stream, barrier):
+    """Uneven batch: 512 polynomials, N uniform in {2^12 .. 2^15}, 1-16 limbs
+    each from a pool of sixteen 50-60-bit primes = 1 mod 2^16 (seed 3). One
+    mixed-degree launch per direction versus per-degree persistent launches
+    versus one launch per polynomial."""
+    import numpy as np
+    import torch
+
+    from paper_2109_14704_gb300 import he
+    from paper_2109_14704_gb300.synth import Rng
+
+    pool = he.primes_generate(60, 1 << 16, 6) + he.primes_generate(55, 1 << 16, 5) + \
+        he.primes_generate(50, 1 << 16, 5)
+    degrees = [4096, 8192, 16384, 32768]
+    tables = {N: he.NttTables(N, pool) for N in degrees}
+    r = Rng(3)
+    Ns = r.choice(degrees, 512)
+    Ls = r.choice(list(range(1, 17)), 512)
+    Fs = [int(x) for x in r.choice(list(range(16)), 512)]
+    Fs = [min(f, 16 - L) for f, L in zip(Fs, Ls)]
+    polys = [torch.from_numpy(r.uniform_limbs(pool[f:f + L], N).view(np.int64)).cuda()
+             for N, L, f in zip(Ns, Ls, Fs)]
+    entries = [(polys[i], tables[N], N, L, f) for i, (N, L, f) in enumerate(zip(Ns, Ls, Fs))]
+    limbs = sum(Ls)
+    words = sum(N * L for N, L in zip(Ns, Ls))
+    mixed = he.NttPlan(entries)
+    per_degree = he.NttPlan(entries, shapes={N: he.ntt_shapes(N)[0] for N in degrees})
+
+    def run_plan(plan):
+        def step():
+            plan.fwd(stream=stream)
+            plan.inv(stream=stream)
+        return step
+
+    singles = [he.NttPlan([e]) for e in entries]     # one launch per polynomial
+
+    def step_plain():
+        for pl in singles:
+            pl.fwd(stream=stream)
+        for pl in singles:
+            pl.inv(stream=stream)
+
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        mixed.fwd(stream=side)
+        mixed.inv(stream=side)
+        with torch.cuda.graph(g, stream=side):
+            mixed.fwd(stream=side)
+            mixed.inv(stream=side)
+    stream.wait_stream(side)
+    torch.cuda.synchronize()
+    ms_mixed = _time_steps(run_plan(mixed), args.steps, args.warmup, stream, barrier)
+    ms_graph = _time_steps(g.replay, args.steps, args.warmup, stream, barrier)
+    ms_deg = _time_steps(run_plan(per_degree), args.steps, args.warmup, stream, barrier)
+    ms_plain = _time_steps(step_plain, max(2, args.steps // 5), 1, stream, barrier)
+    return {
+        "workload": "512 polys, N in {4096..32768}, 1-16 limbs of 50-60-bit primes, seed 3",
+        "limbs": limbs, "words": words,
+        "mixed_single_launch_limbs_per_s": 2 * limbs / (ms_mixed / 1e3),
+        "mixed_graph_limbs_per_s": 2 * limbs / (ms_graph / 1e3),
+        "per_degree_launches_limbs_per_s": 2 * limbs / (ms_deg / 1e3),
+        "plain_per_poly_limbs_per_s": 2 * limbs / (ms_plain / 1e3),
+        "mixed_gbs": 2 * 16 * words / (ms_mixed / 1e3) / 1e9,
+        "launches_per_direction": {"mixed": mixed.launches, "per_degree": per_degree.launches,
+                                   "plain": len(singles)},
+    }
+
+
+def bench_matrix(args, stream, barrier):
+    """Element-wise product of two 32 x 32 matrices of ciphertexts: 1024
+    MulLinRS at N = 8192, data primes 60/40/40, special prime 60, one call."""
+    import numpy as np
+    import torch
+
+    from paper_2109_14704_gb300 import he
+    from paper_2109_14704_gb300.synth import Rng
+
+    N, count = 8192, 1024
+    data, P = he.chain_primes(N, [60, 40, 40], 60)
+    ctx = he.Context(N, data, P)
+    L = 2
+    r = Rng(4)
+    evk = np.stack([np.stack([r.uniform_limbs(data + [P], N) for _ in range(2)]) for _ in range(3)])
+    key = he.RelinKey(ctx, evk)
+    mk = lambda: torch.from_numpy(np.stack([np.stack([r.uniform_limbs(data, N) for _ in range(2)])
+                                            for _ in range(count)]).view(np.int64)).cuda()
+    A, B = mk(), mk()
+    out = torch.empty((count, 2, L, N), dtype=torch.int64, device="cuda")
+    scratch = torch.empty(ctx.mrr_scratch_bytes(L, count) // 8, dtype=torch.int64, device="cuda")
+
+    def step():
+        he.mul_relin_rescale(out, A, B, count, key, ctx, L, scratch, stream=stream)
+
+    ms = _time_steps(step, args.steps, args.warmup, stream, barrier)
+    return {"workload": "32x32 element-wise, N=8192, primes 60/40/40 + 60, 1024 MulLinRS per step",
+            "ms_per_step": ms, "mul_relin_rescale_per_s": count / (ms / 1e3)}
+
+
+def bench_serving(args):
+    """Poisson arrivals at 2000 requests/s of MulLinRS jobs, N in {8192,
+    16384, 32768}, levels 2-16, keys resident, 64 GB admission budget: the
+    continuous-batching server versus the same server with one request per
+    launch (one slot, one stream)."""
+    from paper_2109_14704_gb300 import serving
+
+    out = {"workload": "Poisson 2000 req/s, N in {8192,16384,32768}, levels 2-16, budget 64 GB"}
+    for name, kw in (("batched", dict(slots=16, streams=4)), ("plain", dict(slots=1, streams=1))):
+        srv = serving.Server(pool_per_bucket=1, seed=5, **kw)
+        srv.run(srv.make_requests(300, rate=2000.0, seed=55))              # warm-up
+        srv.completed.clear()
+        srv.batches_launched = 0
+        stats = srv.run(srv.make_requests(args.serve_requests, rate=2000.0, seed=5))
+        out[name] = stats
+        del srv
+    return out
 
 
 # ------------------------------------------------------------- CPU oracle

@@ -123,6 +123,19 @@ he_status he_ntt_inv_naive(uint64_t *poly, uint32_t N, uint32_t limbs, uint32_t 
                            const uint64_t *moduli_host, const he_ntt_tables *tw,
                            he_stream_t stream);
 
+/* Transform shapes built for degree N: writes up to `cap` pairs
+ * (log_block, log_thread_words) to pairs_out (host), the default first, and
+ * the number built to *n_out. log_block: 2^log_block words per CTA, the
+ * transform of one limb split over a cluster of N / 2^log_block CTAs;
+ * log_thread_words: 2^log_thread_words words per thread, i.e. radix-2^k
+ * register rounds (the paper's radix and SLM-stage choices, Sec. III-B). */
+he_status he_ntt_shapes(uint32_t N, uint32_t *pairs_out, uint32_t cap, uint32_t *n_out);
+
+/* Shape used from now on by he_ntt_fwd / he_ntt_inv at degree N (process
+ * wide; 0, 0 restores the built-in default). The autotuner's choice is
+ * applied here. Returns HE_EUNSUPPORTED for a shape that is not built. */
+he_status he_ntt_set_shape(uint32_t N, uint32_t log_block, uint32_t log_thread_words);
+
 /* Dyadic product out[l][i] = a[l][i] * b[l][i] mod q_l for `count`
  * polynomials of `limbs` limbs (Sec. II-B, the elementwise product of the
  * convolution theorem). out may equal a or b. */
@@ -212,20 +225,24 @@ typedef struct he_poly_desc {
     uint32_t reserved;
 } he_poly_desc;
 
-/* Kernel shape of a plan for one N: local block of 2^log_block words per
- * CTA (the rest of the transform is split over a cluster of N / 2^log_block
- * CTAs exchanging through distributed shared memory). 0 = default. */
+/* Kernel shape of a plan for one N: 2^log_block words per CTA (the rest of
+ * the transform is split over a cluster of N / 2^log_block CTAs exchanging
+ * through distributed shared memory) and 2^log_thread_words words per
+ * thread (radix-2^log_thread_words register rounds; 0 = 16 words). */
 typedef struct he_ntt_shape {
     uint32_t N;
     uint32_t log_block;
+    uint32_t log_thread_words;
+    uint32_t reserved;
 } he_ntt_shape;
 
 /* A plan that transforms all `count` polynomials (any mix of N and limb
- * counts) with one launch per direction: a persistent kernel driven by a
- * device-resident work list. Allocates the work list and synchronises;
- * execution allocates nothing and can be captured in a CUDA graph. `shapes`
- * (n_shapes entries, may be NULL) overrides the default kernel shape per N,
- * e.g. with choices from the autotuner. */
+ * counts) with persistent kernels driven by a device-resident work list.
+ * Without shape overrides (n_shapes = 0) and with every N in [2^12, 2^15],
+ * the whole plan is ONE launch per direction: clusters of 8 CTAs split into
+ * sub-clusters per degree. With overrides (e.g. the autotuner's choices per
+ * N), each degree gets its own persistent launch in the given shape.
+ * Allocates the work list and synchronises; execution allocates nothing. */
 he_status he_ntt_plan_create(const he_poly_desc *descs_host, uint32_t count,
                              const he_ntt_shape *shapes_host, uint32_t n_shapes,
                              he_plan **out);

@@ -1,0 +1,176 @@
+"""Autotuner for the transform kernels.
+
+For a batch shape (N, limbs, count) it times every transform shape the
+library built for that degree (he_ntt_shapes: words per CTA, i.e. how many
+stages run across the CTAs of a cluster versus inside one CTA's shared
+memory, and words per thread, i.e. radix-8 or radix-16 register rounds --
+the paper tuned the same knobs by hand: radix, SLM threshold and register
+slots, Sec. III-B, Sec. V-A). Each candidate is first checked once: its
+forward output must equal the default shape's output bit for bit and its
+inverse must restore the input exactly. Candidates are timed with CUDA
+events (forward + inverse, median of `reps` after warm-up); the fastest wins,
+ties going to the earlier candidate. Results are cached in a JSON file keyed
+by device, N, limbs and count, and applied with he_ntt_set_shape so that the
+plain he_ntt_fwd / he_ntt_inv calls use them.
+
+For uneven batches, tune_plan compares the single mixed-degree launch with
+per-degree persistent launches in each degree's tuned shape.
+"""
+from __future__ import annotations
+
+import json
+import os
+import statistics
+
+import numpy as np
+
+from . import he
+from .synth import Rng
+
+DEFAULT_CACHE = os.environ.get(
+    "HE_AUTOTUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "paper_2109_14704_gb300", "autotune.json"))
+
+
+def _load_cache(path):
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _save_cache(path, cache):
+    os.makedirs(os.path.dirname(path) or ".", exist_ok=True)
+    tmp = f"{path}.tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def _device_key():
+    import torch
+    return torch.cuda.get_device_name(torch.cuda.current_device())
+
+
+def _time(fn, reps, warmup):
+    import torch
+    s = torch.cuda.current_stream()
+    for _ in range(warmup):
+        fn()
+    times = []
+    for _ in range(reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        fn()
+        b.record(s)
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+    return statistics.median(times)
+
+
+def default_moduli(N: int, limbs: int) -> list[int]:
+    two_n = 2 * N
+    half = (limbs + 1) // 2
+    return (he.primes_generate(60, two_n, half) + he.primes_generate(50, two_n, limbs - half))[:limbs]
+
+
+def tune_uniform(N: int, limbs: int, count: int, moduli=None, reps: int = 10, warmup: int = 3,
+                 cache_path: str | None = DEFAULT_CACHE, apply: bool = True, force: bool = False) -> dict:
+    """Pick the fastest built shape for he_ntt_fwd / he_ntt_inv on `count`
+    polynomials of `limbs` limbs at degree N."""
+    import torch
+
+    key = f"{_device_key()}|uniform|N={N}|limbs={limbs}|count={count}"
+    cache = _load_cache(cache_path) if cache_path else {}
+    if not force and key in cache:
+        res = cache[key]
+        if apply:
+            he.ntt_set_shape(N, *res["shape"])
+        return res
+
+    qs = list(moduli) if moduli is not None else default_moduli(N, limbs)
+    tables = he.NttTables(N, qs)
+    r = Rng(0xA070)
+    x = np.stack([r.uniform_limbs(qs, N) for _ in range(count)])
+    x_dev = torch.from_numpy(x.view(np.int64)).cuda()
+    d = torch.empty_like(x_dev)
+    shapes = he.ntt_shapes(N)
+
+    # reference output: the default shape
+    he.ntt_set_shape(N, 0, 0)
+    d.copy_(x_dev)
+    he.ntt_fwd(d, N, limbs, count, tables)
+    ref = d.clone()
+
+    cands = []
+    try:
+        for idx, (lb, le) in enumerate(shapes):
+            he.ntt_set_shape(N, lb, le)
+            d.copy_(x_dev)
+            he.ntt_fwd(d, N, limbs, count, tables)
+            ok_fwd = bool(torch.equal(d, ref))
+            he.ntt_inv(d, N, limbs, count, tables)
+            ok_inv = bool(torch.equal(d, x_dev))
+            if not (ok_fwd and ok_inv):
+                cands.append({"index": idx, "shape": [lb, le], "ok": False})
+                continue
+
+            def step():
+                he.ntt_fwd(d, N, limbs, count, tables)
+                he.ntt_inv(d, N, limbs, count, tables)
+
+            ms = _time(step, reps, warmup)
+            cands.append({"index": idx, "shape": [lb, le], "ok": True, "ms_fwd_inv": ms})
+    finally:
+        he.ntt_set_shape(N, 0, 0)
+    good = [c for c in cands if c["ok"]]
+    if not good:
+        raise RuntimeError(f"no transform shape for N = {N} passed its check")
+    best = min(good, key=lambda c: (c["ms_fwd_inv"], c["index"]))
+    res = {"shape": best["shape"], "ms_fwd_inv": best["ms_fwd_inv"], "candidates": cands,
+           "default_ms_fwd_inv": next(c["ms_fwd_inv"] for c in good if c["index"] == 0) if cands[0]["ok"] else None}
+    if cache_path:
+        cache = _load_cache(cache_path)
+        cache[key] = res
+        _save_cache(cache_path, cache)
+    if apply:
+        he.ntt_set_shape(N, *res["shape"])
+    return res
+
+
+def tune_plan(polys, reps: int = 10, warmup: int = 3, shapes_per_degree: dict | None = None) -> dict:
+    """Compare, for an uneven batch given as NttPlan entries (tensor, tables,
+    N, limbs, first_prime), the single mixed-degree launch (when every N is
+    in [2^12, 2^15]) with per-degree launches in the given (or default)
+    shapes. Returns the winning configuration: {"shapes": {...}} to pass to
+    NttPlan (an empty dict selects the mixed launch)."""
+    import torch
+
+    degrees = sorted({p[2] for p in polys})
+    options = []
+    if all(4096 <= N <= 32768 for N in degrees):
+        options.append({})
+    per_degree = {N: tuple((shapes_per_degree or {}).get(N, he.ntt_shapes(N)[0])) for N in degrees}
+    options.append(per_degree)
+    saved = [p[0].clone() for p in polys]
+    results = []
+    for idx, shapes in enumerate(options):
+        plan = he.NttPlan(polys, shapes=shapes or None)
+
+        def step():
+            plan.fwd()
+            plan.inv()
+
+        step()
+        ok = all(torch.equal(p[0], s) for p, s in zip(polys, saved))
+        ms = _time(step, reps, warmup) if ok else None
+        results.append({"index": idx, "shapes": {str(k): list(v) for k, v in shapes.items()}, "ok": ok,
+                        "ms_fwd_inv": ms, "launches_per_direction": plan.launches})
+        plan.close()
+    good = [r for r in results if r["ok"]]
+    if not good:
+        raise RuntimeError("no plan configuration passed its check")
+    best = min(good, key=lambda r: (r["ms_fwd_inv"], r["index"]))
+    return {"best": best, "candidates": results,
+            "shapes": {int(k): tuple(v) for k, v in best["shapes"].items()}}

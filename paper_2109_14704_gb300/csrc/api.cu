@@ -10,6 +10,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <string>
@@ -318,6 +319,39 @@ static he::NttLaunch uniform_launch(uint64_t *poly, uint32_t limbs, uint32_t cou
     return a;
 }
 
+// Shape used by he_ntt_fwd / he_ntt_inv per degree (0, 0 = built-in default),
+// set by he_ntt_set_shape (e.g. from the autotuner).
+static std::atomic<int> g_shape_b[17], g_shape_e[17];
+
+extern "C" he_status he_ntt_shapes(uint32_t N, uint32_t *pairs_out, uint32_t cap, uint32_t *n_out)
+{
+    int log_n;
+    if (he_status s = check_degree(N, &log_n)) return s;
+    if (!n_out) return fail(HE_EINVAL, "n_out is NULL");
+    const he::DegreeOps *ops = he::degree_ops(log_n);
+    *n_out = (uint32_t)ops->n_shapes;
+    if (cap && !pairs_out) return fail(HE_EINVAL, "pairs_out is NULL");
+    for (int i = 0; i < ops->n_shapes && (uint32_t)i < cap; i++) {
+        pairs_out[2 * i] = (uint32_t)ops->shapes[i][0];
+        pairs_out[2 * i + 1] = (uint32_t)ops->shapes[i][1];
+    }
+    return HE_OK;
+}
+
+extern "C" he_status he_ntt_set_shape(uint32_t N, uint32_t log_block, uint32_t log_thread_words)
+{
+    int log_n;
+    if (he_status s = check_degree(N, &log_n)) return s;
+    if (log_block || log_thread_words) {
+        if (!he::degree_ops(log_n)->has_shape((int)log_block, (int)log_thread_words))
+            return fail(HE_EUNSUPPORTED, "no kernel with 2^%u words per CTA and 2^%u per thread for N = %u",
+                        log_block, log_thread_words, N);
+    }
+    g_shape_b[log_n].store((int)log_block);
+    g_shape_e[log_n].store((int)log_thread_words);
+    return HE_OK;
+}
+
 static he_status ntt_common(uint64_t *poly, uint32_t N, uint32_t limbs, uint32_t count,
                             const uint64_t *moduli_host, const he_ntt_tables *tw, he_stream_t stream, bool inv)
 {
@@ -326,7 +360,8 @@ static he_status ntt_common(uint64_t *poly, uint32_t N, uint32_t limbs, uint32_t
     if ((u64)limbs * count == 0) return HE_OK;
     if ((u64)limbs * count * (N / 4096 + 1) > 0x7fffffffull) return fail(HE_EINVAL, "batch too large");
     const he::DegreeOps *ops = he::degree_ops(log_n);
-    HE_CUDA(ops->ntt(uniform_launch(poly, limbs, count, tw), 0, inv, (cudaStream_t)stream));
+    HE_CUDA(ops->ntt(uniform_launch(poly, limbs, count, tw), g_shape_b[log_n].load(), g_shape_e[log_n].load(), inv,
+                     (cudaStream_t)stream));
     return HE_OK;
 }
 
@@ -733,11 +768,17 @@ struct he_plan {
     struct Group {
         int log_n;
         int log_b;
+        int log_e;
         u32 items;
         u32 clusters;
         he::LimbJob *d_jobs;
     };
-    std::vector<Group> groups;
+    std::vector<Group> groups;         // per-degree persistent launches
+    bool mixed = false;                // one mixed-degree launch per direction
+    he::MixedUnit *d_units = nullptr;
+    he::LimbJob *d_mixed_jobs = nullptr;
+    u32 n_units = 0;
+    u32 clusters_fwd = 0, clusters_inv = 0;
 };
 
 extern "C" he_status he_plan_destroy(he_plan *plan)
@@ -745,9 +786,19 @@ extern "C" he_status he_plan_destroy(he_plan *plan)
     if (plan) {
         cudaDeviceSynchronize();
         for (auto &g : plan->groups) cudaFree(g.d_jobs);
+        cudaFree(plan->d_units);
+        cudaFree(plan->d_mixed_jobs);
         delete plan;
     }
     return HE_OK;
+}
+
+template <class T>
+static cudaError_t upload(T **dst, const std::vector<T> &v)
+{
+    cudaError_t e = cudaMalloc(dst, std::max<size_t>(v.size(), 1) * sizeof(T));
+    if (e == cudaSuccess && !v.empty()) e = cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+    return e;
 }
 
 extern "C" he_status he_ntt_plan_create(const he_poly_desc *descs_host, uint32_t count,
@@ -779,29 +830,62 @@ extern "C" he_status he_ntt_plan_create(const he_poly_desc *descs_host, uint32_t
             by_degree[log_n].push_back(j);
         }
     }
+    for (u32 s = 0; s < n_shapes; s++) {
+        int log_n;
+        if (he_status st = check_degree(shapes_host[s].N, &log_n)) return st;
+        const he::DegreeOps *ops = he::degree_ops(log_n);
+        if (!ops->has_shape((int)shapes_host[s].log_block, (int)shapes_host[s].log_thread_words))
+            return fail(HE_EUNSUPPORTED, "no kernel with 2^%u words per CTA and 2^%u per thread for N = 2^%d",
+                        shapes_host[s].log_block, shapes_host[s].log_thread_words, log_n);
+    }
     he_plan *plan = new he_plan;
+    bool mixed = n_shapes == 0 && !by_degree.empty();
+    for (auto &kv : by_degree) mixed = mixed && kv.first >= 12 && kv.first <= 15;
+    if (mixed) {
+        // largest degrees first, so that the long units start early
+        std::vector<he::LimbJob> jobs;
+        std::vector<he::MixedUnit> units;
+        for (auto it = by_degree.rbegin(); it != by_degree.rend(); ++it) {
+            const u32 per = 8u >> (it->first - 12);
+            for (size_t k = 0; k < it->second.size(); k += per) {
+                he::MixedUnit u;
+                u.log_n = (u32)it->first;
+                u.first_job = (u32)jobs.size();
+                u.n_jobs = (u32)std::min<size_t>(per, it->second.size() - k);
+                u.pad = 0;
+                for (u32 q = 0; q < u.n_jobs; q++) jobs.push_back(it->second[k + q]);
+                units.push_back(u);
+            }
+        }
+        cudaError_t e = upload(&plan->d_mixed_jobs, jobs);
+        if (e == cudaSuccess) e = upload(&plan->d_units, units);
+        if (e != cudaSuccess) {
+            he_plan_destroy(plan);
+            return cuda_fail(e, "plan work list");
+        }
+        plan->mixed = true;
+        plan->n_units = (u32)units.size();
+        plan->clusters_fwd = std::min<u32>(plan->n_units, (u32)std::max(he::mixed_max_clusters(false), 1));
+        plan->clusters_inv = std::min<u32>(plan->n_units, (u32)std::max(he::mixed_max_clusters(true), 1));
+        *out = plan;
+        return HE_OK;
+    }
     for (auto &kv : by_degree) {
         he_plan::Group g = {};
         g.log_n = kv.first;
         const he::DegreeOps *ops = he::degree_ops(g.log_n);
         g.log_b = ops->default_log_b;
+        g.log_e = ops->default_log_e;
         for (u32 s = 0; s < n_shapes; s++)
             if (shapes_host[s].N == (1u << g.log_n) && shapes_host[s].log_block) {
-                if (!ops->has_shape((int)shapes_host[s].log_block)) {
-                    he_plan_destroy(plan);
-                    return fail(HE_EUNSUPPORTED, "no kernel with 2^%u words per CTA for N = 2^%d",
-                                shapes_host[s].log_block, g.log_n);
-                }
                 g.log_b = (int)shapes_host[s].log_block;
+                g.log_e = shapes_host[s].log_thread_words ? (int)shapes_host[s].log_thread_words : 4;
             }
         g.items = (u32)kv.second.size();
-        const int mc = std::max(ops->max_clusters(g.log_b, false), 1);
+        const int mc = std::max(ops->max_clusters(g.log_b, g.log_e, false), 1);
         g.clusters = std::min<u32>(g.items, (u32)mc);
-        cudaError_t e = cudaMalloc(&g.d_jobs, kv.second.size() * sizeof(he::LimbJob));
-        if (e == cudaSuccess)
-            e = cudaMemcpy(g.d_jobs, kv.second.data(), kv.second.size() * sizeof(he::LimbJob), cudaMemcpyHostToDevice);
+        cudaError_t e = upload(&g.d_jobs, kv.second);
         if (e != cudaSuccess) {
-            cudaFree(g.d_jobs);
             he_plan_destroy(plan);
             return cuda_fail(e, "plan job list");
         }
@@ -814,11 +898,16 @@ extern "C" he_status he_ntt_plan_create(const he_poly_desc *descs_host, uint32_t
 static he_status plan_run(const he_plan *plan, he_stream_t stream, bool inv)
 {
     if (!plan) return fail(HE_EINVAL, "plan is NULL");
+    if (plan->mixed) {
+        HE_CUDA(he::launch_ntt_mixed(plan->d_units, plan->n_units, plan->d_mixed_jobs, inv,
+                                     inv ? plan->clusters_inv : plan->clusters_fwd, (cudaStream_t)stream));
+        return HE_OK;
+    }
     for (const auto &g : plan->groups) {
         he::NttLaunch a = {};
         a.items = g.items;
         a.jobs = g.d_jobs;
-        HE_CUDA(he::degree_ops(g.log_n)->ntt_persistent(a, g.log_b, inv, g.clusters, (cudaStream_t)stream));
+        HE_CUDA(he::degree_ops(g.log_n)->ntt_persistent(a, g.log_b, g.log_e, inv, g.clusters, (cudaStream_t)stream));
     }
     return HE_OK;
 }
@@ -826,7 +915,10 @@ static he_status plan_run(const he_plan *plan, he_stream_t stream, bool inv)
 extern "C" he_status he_ntt_plan_fwd(const he_plan *plan, he_stream_t stream) { return plan_run(plan, stream, false); }
 extern "C" he_status he_ntt_plan_inv(const he_plan *plan, he_stream_t stream) { return plan_run(plan, stream, true); }
 
-extern "C" uint32_t he_plan_launches(const he_plan *plan) { return plan ? (uint32_t)plan->groups.size() : 0; }
+extern "C" uint32_t he_plan_launches(const he_plan *plan)
+{
+    return plan ? (plan->mixed ? 1u : (uint32_t)plan->groups.size()) : 0;
+}
 
 // ------------------------------------------- allocation-free MulLinRS
 //

@@ -1,6 +1,7 @@
 // inst.cuh -- per-degree instantiation of the kernels and their launchers.
-// Each inst_n<log N>.cu includes this file and defines HE_LOG_N, so that the
-// degrees compile as separate translation units, in parallel.
+// Each inst_n<log N>.cu includes this file and lists the shapes of its
+// degree, so that the degrees compile as separate translation units, in
+// parallel.
 #pragma once
 #include <mutex>
 
@@ -40,17 +41,17 @@ static cudaError_t smem_attr(K kernel, u32 bytes, std::once_flag &flag, cudaErro
     return err;
 }
 
-template <int LOG_B, int LOG_C>
+template <int LOG_B, int LOG_C, int LOG_E = 4>
 struct ShapeOps {
-    using Sh = NttShape<LOG_B, LOG_C>;
+    using Sh = NttShape<LOG_B, LOG_C, LOG_E>;
 
     template <bool INV>
     static cudaError_t ntt(const NttLaunch &a, cudaStream_t s)
     {
         static std::once_flag f;
         static cudaError_t e = cudaSuccess;
-        if (cudaError_t r = smem_attr(k_ntt<LOG_B, LOG_C, INV>, Sh::SMEM_BYTES, f, e)) return r;
-        return launch_k(k_ntt<LOG_B, LOG_C, INV>, a.items * Sh::C, Sh::T, Sh::SMEM_BYTES, Sh::C, s, a);
+        if (cudaError_t r = smem_attr(k_ntt<LOG_B, LOG_C, LOG_E, INV>, Sh::SMEM_BYTES, f, e)) return r;
+        return launch_k(k_ntt<LOG_B, LOG_C, LOG_E, INV>, a.items * Sh::C, Sh::T, Sh::SMEM_BYTES, Sh::C, s, a);
     }
 
     template <bool INV>
@@ -58,8 +59,8 @@ struct ShapeOps {
     {
         static std::once_flag f;
         static cudaError_t e = cudaSuccess;
-        if (cudaError_t r = smem_attr(k_ntt_persistent<LOG_B, LOG_C, INV>, Sh::SMEM_BYTES, f, e)) return r;
-        return launch_k(k_ntt_persistent<LOG_B, LOG_C, INV>, clusters * Sh::C, Sh::T, Sh::SMEM_BYTES, Sh::C,
+        if (cudaError_t r = smem_attr(k_ntt_persistent<LOG_B, LOG_C, LOG_E, INV>, Sh::SMEM_BYTES, f, e)) return r;
+        return launch_k(k_ntt_persistent<LOG_B, LOG_C, LOG_E, INV>, clusters * Sh::C, Sh::T, Sh::SMEM_BYTES, Sh::C,
                         s, a);
     }
 
@@ -68,7 +69,7 @@ struct ShapeOps {
     {
         static std::once_flag f;
         static cudaError_t e = cudaSuccess;
-        if (smem_attr(k_ntt_persistent<LOG_B, LOG_C, INV>, Sh::SMEM_BYTES, f, e) != cudaSuccess) return 0;
+        if (smem_attr(k_ntt_persistent<LOG_B, LOG_C, LOG_E, INV>, Sh::SMEM_BYTES, f, e) != cudaSuccess) return 0;
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(Sh::C * 1024, 1, 1);
         cfg.blockDim = dim3(Sh::T, 1, 1);
@@ -81,7 +82,7 @@ struct ShapeOps {
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         int n = 0;
-        if (cudaOccupancyMaxActiveClusters(&n, k_ntt_persistent<LOG_B, LOG_C, INV>, &cfg) != cudaSuccess) {
+        if (cudaOccupancyMaxActiveClusters(&n, k_ntt_persistent<LOG_B, LOG_C, LOG_E, INV>, &cfg) != cudaSuccess) {
             cudaGetLastError();
             return 0;
         }
@@ -117,27 +118,31 @@ struct ShapeOps {
 
 }  // namespace he
 
-// Shapes built per degree: words per CTA 2^LOG_B with at most 8 CTAs per
-// cluster. The first listed is the default (and the one the evaluation
-// kernels use).
-#define HE_SHAPE_FN(LOG_N_, LB)                                                                    \
-    if (log_b == LB) return fn(::he::ShapeOps<LB, LOG_N_ - LB>{});
+// Shapes built per degree: 2^LB words per CTA (at most 8 CTAs per cluster)
+// and 2^LE words per thread. The first listed is the default (and the one
+// the evaluation kernels use).
+#define HE_SHAPE_FN(LOG_N_, LB, LE)                                                                \
+    if (log_b == LB && log_e == LE) return fn(::he::ShapeOps<LB, LOG_N_ - LB, LE>{});
 
 namespace he {
 
 template <int LOG_N>
 struct DegreeImpl;
 
-#define HE_DEGREE(LOG_N_, DEF, ...)                                                                \
+#define HE_DEGREE(LOG_N_, DEF_B, DEF_E, LIST, ...)                                                 \
     template <>                                                                                    \
     struct DegreeImpl<LOG_N_> {                                                                    \
-        static constexpr int def = DEF;                                                            \
+        static constexpr int def_b = DEF_B;                                                        \
+        static constexpr int def_e = DEF_E;                                                        \
+        static constexpr int shapes[][2] = LIST;                                                   \
         template <class F>                                                                         \
-        static auto with_shape(int log_b, F fn) -> decltype(fn(ShapeOps<DEF, LOG_N_ - DEF>{}))     \
+        static auto with_shape(int log_b, int log_e, F fn)                                         \
+            -> decltype(fn(ShapeOps<DEF_B, LOG_N_ - DEF_B, DEF_E>{}))                              \
         {                                                                                          \
-            if (log_b == 0) log_b = DEF;                                                           \
+            if (log_b == 0) log_b = DEF_B;                                                         \
+            if (log_e == 0) log_e = DEF_E;                                                         \
             __VA_ARGS__                                                                            \
-            return decltype(fn(ShapeOps<DEF, LOG_N_ - DEF>{}))();                                  \
+            return decltype(fn(ShapeOps<DEF_B, LOG_N_ - DEF_B, DEF_E>{}))();                       \
         }                                                                                          \
     };
 
@@ -145,44 +150,48 @@ struct DegreeImpl;
 
 #define HE_DEFINE_DEGREE_OPS(LOG_N_)                                                               \
     namespace he {                                                                                 \
-    static cudaError_t ntt_##LOG_N_(const NttLaunch &a, int log_b, bool inv, cudaStream_t s)        \
+    static cudaError_t ntt_##LOG_N_(const NttLaunch &a, int log_b, int log_e, bool inv, cudaStream_t s) \
     {                                                                                              \
         using D = DegreeImpl<LOG_N_>;                                                              \
         bool found = false;                                                                        \
-        cudaError_t r = D::with_shape(log_b, [&](auto ops) {                                       \
+        cudaError_t r = D::with_shape(log_b, log_e, [&](auto ops) {                                \
             found = true;                                                                          \
             return inv ? decltype(ops)::template ntt<true>(a, s) : decltype(ops)::template ntt<false>(a, s); \
         });                                                                                        \
         return found ? r : cudaErrorInvalidValue;                                                  \
     }                                                                                              \
-    static cudaError_t ntt_p_##LOG_N_(const NttLaunch &a, int log_b, bool inv, u32 cl, cudaStream_t s) \
+    static cudaError_t ntt_p_##LOG_N_(const NttLaunch &a, int log_b, int log_e, bool inv, u32 cl,   \
+                                      cudaStream_t s)                                              \
     {                                                                                              \
         using D = DegreeImpl<LOG_N_>;                                                              \
         bool found = false;                                                                        \
-        cudaError_t r = D::with_shape(log_b, [&](auto ops) {                                       \
+        cudaError_t r = D::with_shape(log_b, log_e, [&](auto ops) {                                \
             found = true;                                                                          \
             return inv ? decltype(ops)::template persistent<true>(a, cl, s)                       \
                        : decltype(ops)::template persistent<false>(a, cl, s);                     \
         });                                                                                        \
         return found ? r : cudaErrorInvalidValue;                                                  \
     }                                                                                              \
-    static int maxcl_##LOG_N_(int log_b, bool inv)                                                 \
+    static int maxcl_##LOG_N_(int log_b, int log_e, bool inv)                                      \
     {                                                                                              \
         using D = DegreeImpl<LOG_N_>;                                                              \
-        return D::with_shape(log_b, [&](auto ops) {                                                \
+        return D::with_shape(log_b, log_e, [&](auto ops) {                                         \
             return inv ? decltype(ops)::template max_clusters<true>()                              \
                        : decltype(ops)::template max_clusters<false>();                           \
         });                                                                                        \
     }                                                                                              \
     static cudaError_t eval_##LOG_N_(EvalKernel k, const EvalArgs &a, u32 items, cudaStream_t s)   \
     {                                                                                              \
-        return ShapeOps<DegreeImpl<LOG_N_>::def, LOG_N_ - DegreeImpl<LOG_N_>::def>::eval(k, a, items, s); \
+        using D = DegreeImpl<LOG_N_>;                                                              \
+        return ShapeOps<D::def_b, LOG_N_ - D::def_b, 4>::eval(k, a, items, s);                     \
     }                                                                                              \
-    static bool has_##LOG_N_(int log_b)                                                            \
+    static bool has_##LOG_N_(int log_b, int log_e)                                                 \
     {                                                                                              \
-        return DegreeImpl<LOG_N_>::with_shape(log_b, [&](auto) { return true; });                 \
+        return DegreeImpl<LOG_N_>::with_shape(log_b, log_e, [&](auto) { return true; });           \
     }                                                                                              \
-    extern const DegreeOps degree_ops_##LOG_N_ = {LOG_N_, DegreeImpl<LOG_N_>::def, ntt_##LOG_N_,     \
-                                                  ntt_p_##LOG_N_, maxcl_##LOG_N_, eval_##LOG_N_,   \
-                                                  has_##LOG_N_};                                   \
+    extern const DegreeOps degree_ops_##LOG_N_ = {                                                 \
+        LOG_N_, DegreeImpl<LOG_N_>::def_b, DegreeImpl<LOG_N_>::def_e, ntt_##LOG_N_, ntt_p_##LOG_N_,  \
+        maxcl_##LOG_N_, eval_##LOG_N_, has_##LOG_N_,                                               \
+        (int)(sizeof(DegreeImpl<LOG_N_>::shapes) / sizeof(DegreeImpl<LOG_N_>::shapes[0])),         \
+        DegreeImpl<LOG_N_>::shapes};                                                               \
     }

@@ -1,8 +1,9 @@
-// inst_n15.cu -- kernels for N = 2^15 (words per CTA: 2^12, 2^13).
+// inst_n15.cu -- kernels for N = 2^15; transform shapes: 2^12 words/CTA x 2^4 words/thread, 2^13 words/CTA x 2^4 words/thread, 2^12 words/CTA x 2^3 words/thread, 2^13 words/CTA x 2^3 words/thread.
 #include "inst.cuh"
 
+#define HE_SHAPES_15 {{12, 4}, {13, 4}, {12, 3}, {13, 3}}
 namespace he {
-HE_DEGREE(15, 12, HE_SHAPE_FN(15, 12) HE_SHAPE_FN(15, 13))
+HE_DEGREE(15, 12, 4, HE_SHAPES_15, HE_SHAPE_FN(15, 12, 4) HE_SHAPE_FN(15, 13, 4) HE_SHAPE_FN(15, 12, 3) HE_SHAPE_FN(15, 13, 3))
 }  // namespace he
 
 HE_DEFINE_DEGREE_OPS(15)

@@ -11,10 +11,11 @@ namespace he {
 
 // ============================================================ plain NTT ====
 
-template <int LOG_B, int LOG_C, bool INV>
-__global__ void __launch_bounds__(NttShape<LOG_B, LOG_C>::T) k_ntt(NttLaunch a)
+template <int LOG_B, int LOG_C, int LOG_E, bool INV>
+__global__ void __launch_bounds__(NttShape<LOG_B, LOG_C, LOG_E>::T, NttShape<LOG_B, LOG_C, LOG_E>::MIN_CTAS)
+k_ntt(NttLaunch a)
 {
-    using Sh = NttShape<LOG_B, LOG_C>;
+    using Sh = NttShape<LOG_B, LOG_C, LOG_E>;
     extern __shared__ __align__(16) u64 smem[];
     const u32 m = (LOG_C > 0) ? cluster_ctarank() : 0u;
     const u32 item = blockIdx.x >> LOG_C;
@@ -33,20 +34,21 @@ __global__ void __launch_bounds__(NttShape<LOG_B, LOG_C>::T) k_ntt(NttLaunch a)
         pcp = a.pc + pr;
     }
     const PrimeConst pc = *pcp;
-    u64 x[16];
+    u64 x[Sh::E];
     auto ld = [&](u32 P) -> u64 { return data[P]; };
     auto st = [&](u32 P, u64 v) { data[P] = v; };
     if constexpr (!INV)
-        ntt_fwd_block<Sh>(smem, m, tw, pc.p, pc.two_p, ld, st, x);
+        ntt_fwd_block<Sh>(smem, m, 0, tw, pc.p, pc.two_p, ld, st, x);
     else
-        ntt_inv_block<Sh, false>(smem, m, tw, pc, ld, st, x);
+        ntt_inv_block<Sh, false>(smem, m, 0, tw, pc, ld, st, x);
 }
 
 // Persistent form for plans: a fixed grid of clusters walks the job list.
-template <int LOG_B, int LOG_C, bool INV>
-__global__ void __launch_bounds__(NttShape<LOG_B, LOG_C>::T) k_ntt_persistent(NttLaunch a)
+template <int LOG_B, int LOG_C, int LOG_E, bool INV>
+__global__ void __launch_bounds__(NttShape<LOG_B, LOG_C, LOG_E>::T, NttShape<LOG_B, LOG_C, LOG_E>::MIN_CTAS)
+k_ntt_persistent(NttLaunch a)
 {
-    using Sh = NttShape<LOG_B, LOG_C>;
+    using Sh = NttShape<LOG_B, LOG_C, LOG_E>;
     extern __shared__ __align__(16) u64 smem[];
     const u32 m = (LOG_C > 0) ? cluster_ctarank() : 0u;
     const u32 clusters = gridDim.x >> LOG_C;
@@ -57,13 +59,61 @@ __global__ void __launch_bounds__(NttShape<LOG_B, LOG_C>::T) k_ntt_persistent(Nt
         const LimbJob j = a.jobs[item];
         u64 *data = j.data;
         const PrimeConst pc = *j.pc;
-        u64 x[16];
+        u64 x[Sh::E];
         auto ld = [&](u32 P) -> u64 { return data[P]; };
         auto st = [&](u32 P, u64 v) { data[P] = v; };
         if constexpr (!INV)
-            ntt_fwd_block<Sh>(smem, m, j.tw_fwd, pc.p, pc.two_p, ld, st, x);
+            ntt_fwd_block<Sh>(smem, m, 0, j.tw_fwd, pc.p, pc.two_p, ld, st, x);
         else
-            ntt_inv_block<Sh, false>(smem, m, j.tw_inv, pc, ld, st, x);
+            ntt_inv_block<Sh, false>(smem, m, 0, j.tw_inv, pc, ld, st, x);
+    }
+}
+
+// Mixed-degree persistent form: clusters of 8 CTAs of 2^12 words each walk a
+// list of units; a unit of degree 2^(12+c) holds up to 8 >> c limbs, each
+// transformed by a sub-cluster of 2^c CTAs (cluster ranks rbase .. rbase +
+// 2^c - 1). One launch covers every degree from 2^12 to 2^15. Sub-clusters
+// without a limb in the last unit of a degree recompute the unit's first
+// limb with stores switched off, so that every CTA of the cluster passes the
+// same cluster barriers.
+template <class Sh, bool INV>
+__device__ __forceinline__ void mixed_unit(u64 *smem, u32 rank, const MixedUnit &un, const LimbJob *jobs)
+{
+    const u32 sub = rank >> Sh::LOG_C;
+    const u32 m = rank & (Sh::C - 1);
+    const u32 rbase = sub << Sh::LOG_C;
+    const bool valid = sub < un.n_jobs;
+    const LimbJob j = jobs[un.first_job + (valid ? sub : 0u)];
+    u64 *data = j.data;
+    const PrimeConst pc = *j.pc;
+    u64 x[Sh::E];
+    auto ld = [&](u32 P) -> u64 { return data[P]; };
+    auto st = [&](u32 P, u64 v) {
+        if (valid) data[P] = v;
+    };
+    if constexpr (!INV)
+        ntt_fwd_block<Sh>(smem, m, rbase, j.tw_fwd, pc.p, pc.two_p, ld, st, x);
+    else
+        ntt_inv_block<Sh, false>(smem, m, rbase, j.tw_inv, pc, ld, st, x);
+}
+
+template <bool INV>
+__global__ void __launch_bounds__(256, 2) k_ntt_mixed(const MixedUnit *units, u32 n_units, const LimbJob *jobs)
+{
+    extern __shared__ __align__(16) u64 smem[];
+    const u32 rank = cluster_ctarank();
+    const u32 clusters = gridDim.x >> 3;
+    bool first = true;
+    for (u32 ui = blockIdx.x >> 3; ui < n_units; ui += clusters) {
+        if (!first) cluster_sync_all();
+        first = false;
+        const MixedUnit un = units[ui];
+        switch (un.log_n) {
+        case 12: mixed_unit<NttShape<12, 0>, INV>(smem, rank, un, jobs); break;
+        case 13: mixed_unit<NttShape<12, 1>, INV>(smem, rank, un, jobs); break;
+        case 14: mixed_unit<NttShape<12, 2>, INV>(smem, rank, un, jobs); break;
+        default: mixed_unit<NttShape<12, 3>, INV>(smem, rank, un, jobs); break;
+        }
     }
 }
 
@@ -231,17 +281,10 @@ __global__ void __launch_bounds__(NttShape<LOG_B, LOG_C>::T, 2) k_ks_digits(Eval
     const PrimeConst pc = a.ctx.pc[j];
     const DSource ds = dsource(a, c);
     u64 *out = a.c2 + ((size_t)c * a.n + j) * Sh::N;
-    u64 x[16];
+    u64 x[Sh::E];
     auto ld = [&](u32 P) -> u64 { return ds.d(2, j, Sh::LOG_N, P, pc); };
     auto st = [&](u32 P, u64 v) { out[P] = v; };
-    ntt_inv_block<Sh, false>(smem, m, a.ctx.tw_inv + (size_t)j * Sh::N, pc, ld, st, x);
-}
-
-template <class Sh>
-__device__ __forceinline__ u32 last_pos(u32 m, u32 tid, int e)
-{
-    using RL = typename RoundOf<Sh, Sh::NROUND - 1>::type;
-    return m * Sh::B + round_pos<RL>(tid, e >> RL::R, e & ((1 << RL::R) - 1));
+    ntt_inv_block<Sh, false>(smem, m, 0, a.ctx.tw_inv + (size_t)j * Sh::N, pc, ld, st, x);
 }
 
 template <int LOG_B, int LOG_C>
@@ -249,7 +292,7 @@ __global__ void __launch_bounds__(NttShape<LOG_B, LOG_C>::T, 2) k_ks_modup(EvalA
 {
     using Sh = NttShape<LOG_B, LOG_C>;
     extern __shared__ __align__(16) u64 smem[];
-    u64 *acc = smem + Sh::B;                   // [2][16][T], own positions only
+    u64 *acc = smem + Sh::B;                   // [2][E][T], own positions only
     const u32 tid = threadIdx.x;
     const u32 m = (LOG_C > 0) ? cluster_ctarank() : 0u;
     const u32 item = blockIdx.x >> LOG_C;
@@ -259,26 +302,26 @@ __global__ void __launch_bounds__(NttShape<LOG_B, LOG_C>::T, 2) k_ks_modup(EvalA
     const PrimeConst pc = a.ctx.pc[tp];
     const DSource ds = dsource(a, c);
     const ulonglong2 *twf = a.ctx.tw_fwd + (size_t)tp * Sh::N;
-    u64 x[16];
+    u64 x[Sh::E];
     for (u32 j = 0; j < n; j++) {
         if (t == j) {
 #pragma unroll
-            for (int e = 0; e < 16; e++) x[e] = ds.d(2, j, Sh::LOG_N, last_pos<Sh>(m, tid, e), pc);
+            for (int e = 0; e < Sh::E; e++) x[e] = ds.d(2, j, Sh::LOG_N, last_pos<Sh>(m, tid, e), pc);
         } else {
             if (j > 0) ntt_barrier<Sh>();
             const u64 *src = a.c2 + ((size_t)c * n + j) * Sh::N;
             auto ld = [&](u32 P) -> u64 { return barrett_reduce(0, src[P], pc.p, pc.mu, pc.bits); };
             auto st = [&](u32, u64) {};
-            ntt_fwd_block<Sh>(smem, m, twf, pc.p, pc.two_p, ld, st, x);
+            ntt_fwd_block<Sh>(smem, m, 0, twf, pc.p, pc.two_p, ld, st, x);
         }
 #pragma unroll
         for (int k = 0; k < 2; k++) {
             const ulonglong2 *key = a.evk + (((size_t)j * 2 + k) * (a.ctx.n_data + 1) + tp) * Sh::N;
 #pragma unroll
-            for (int e = 0; e < 16; e++) {
+            for (int e = 0; e < Sh::E; e++) {
                 const ulonglong2 w = __ldg(key + last_pos<Sh>(m, tid, e));
                 const u64 prod = mul_shoup(x[e], w.x, w.y, pc.p);
-                u64 &slot = acc[(k * 16 + e) * Sh::T + tid];
+                u64 &slot = acc[(k * Sh::E + e) * Sh::T + tid];
                 slot = (j == 0) ? prod : add_mod(slot, prod, pc.p);
             }
         }
@@ -288,7 +331,7 @@ __global__ void __launch_bounds__(NttShape<LOG_B, LOG_C>::T, 2) k_ks_modup(EvalA
         for (int k = 0; k < 2; k++) {
             u64 *dst = a.accq + (((size_t)c * 2 + k) * n + t) * Sh::N;
 #pragma unroll
-            for (int e = 0; e < 16; e++) dst[last_pos<Sh>(m, tid, e)] = acc[(k * 16 + e) * Sh::T + tid];
+            for (int e = 0; e < Sh::E; e++) dst[last_pos<Sh>(m, tid, e)] = acc[(k * Sh::E + e) * Sh::T + tid];
         }
     } else {
         // special prime: y_k = INTT_P(acc_k), kept in the coefficient domain
@@ -296,11 +339,11 @@ __global__ void __launch_bounds__(NttShape<LOG_B, LOG_C>::T, 2) k_ks_modup(EvalA
         for (int k = 0; k < 2; k++) {
             ntt_barrier<Sh>();
 #pragma unroll
-            for (int e = 0; e < 16; e++) x[e] = acc[(k * 16 + e) * Sh::T + tid];
+            for (int e = 0; e < Sh::E; e++) x[e] = acc[(k * Sh::E + e) * Sh::T + tid];
             u64 *dst = a.plift + ((size_t)c * 2 + k) * Sh::N;
             auto st = [&](u32 P, u64 v) { dst[P] = v; };
             auto ld = [&](u32) -> u64 { return 0; };
-            ntt_inv_block<Sh, true>(smem, m, a.ctx.tw_inv + (size_t)tp * Sh::N, pc, ld, st, x);
+            ntt_inv_block<Sh, true>(smem, m, 0, a.ctx.tw_inv + (size_t)tp * Sh::N, pc, ld, st, x);
         }
     }
 }
@@ -322,14 +365,14 @@ __global__ void __launch_bounds__(NttShape<LOG_B, LOG_C>::T, 2) k_ks_moddown(Eva
     const u64 half_P = (pP.p - 1) / 2;
     const DSource ds = dsource(a, c);
     const u64 *y = a.plift + ((size_t)c * 2 + k) * Sh::N;
-    u64 x[16];
+    u64 x[Sh::E];
     auto ld = [&](u32 P) -> u64 { return centred_mod(y[P], half_P, cst[2], pc); };
     auto st = [&](u32, u64) {};
-    ntt_fwd_block<Sh>(smem, m, a.ctx.tw_fwd + (size_t)i * Sh::N, pc.p, pc.two_p, ld, st, x);
+    ntt_fwd_block<Sh>(smem, m, 0, a.ctx.tw_fwd + (size_t)i * Sh::N, pc.p, pc.two_p, ld, st, x);
     const u64 *accp = a.accq + (((size_t)c * 2 + k) * n + i) * Sh::N;
     u64 *out = a.out + (((size_t)c * 2 + k) * n + i) * Sh::N;
 #pragma unroll
-    for (int e = 0; e < 16; e++) {
+    for (int e = 0; e < Sh::E; e++) {
         const u32 P = last_pos<Sh>(m, tid, e);
         const u64 v = mul_shoup(sub_mod(accp[P], x[e], pc.p), cst[0], cst[1], pc.p);
         out[P] = add_mod(ds.d(k, i, Sh::LOG_N, P, pc), v, pc.p);
@@ -349,10 +392,10 @@ __global__ void __launch_bounds__(NttShape<LOG_B, LOG_C>::T, 2) k_rs_lift(EvalAr
     const PrimeConst pc = a.ctx.pc[l];
     const u64 *src = a.ct2 + (((size_t)c * 2 + k) * n + l) * Sh::N;
     u64 *dst = a.lift2 + ((size_t)c * 2 + k) * Sh::N;
-    u64 x[16];
+    u64 x[Sh::E];
     auto ld = [&](u32 P) -> u64 { return src[P]; };
     auto st = [&](u32 P, u64 v) { dst[P] = v; };
-    ntt_inv_block<Sh, false>(smem, m, a.ctx.tw_inv + (size_t)l * Sh::N, pc, ld, st, x);
+    ntt_inv_block<Sh, false>(smem, m, 0, a.ctx.tw_inv + (size_t)l * Sh::N, pc, ld, st, x);
 }
 
 // RS, second half: out[c][k][i] = (c_k[q_i] - NTT(r mod q_i)) q_l^-1, i < l.
@@ -370,14 +413,14 @@ __global__ void __launch_bounds__(NttShape<LOG_B, LOG_C>::T, 2) k_rs(EvalArgs a)
     const u64 *cst = a.ctx.cst + 3 * a.ctx.n_data + 3 * ((size_t)l * a.ctx.n_data + i);
     const u64 half_l = (a.ctx.pc[l].p - 1) / 2;
     const u64 *y = a.lift2 + ((size_t)c * 2 + k) * Sh::N;
-    u64 x[16];
+    u64 x[Sh::E];
     auto ld = [&](u32 P) -> u64 { return centred_mod(y[P], half_l, cst[2], pc); };
     auto st = [&](u32, u64) {};
-    ntt_fwd_block<Sh>(smem, m, a.ctx.tw_fwd + (size_t)i * Sh::N, pc.p, pc.two_p, ld, st, x);
+    ntt_fwd_block<Sh>(smem, m, 0, a.ctx.tw_fwd + (size_t)i * Sh::N, pc.p, pc.two_p, ld, st, x);
     const u64 *src = a.ct2 + (((size_t)c * 2 + k) * n + i) * Sh::N;
     u64 *out = a.out + (((size_t)c * 2 + k) * l + i) * Sh::N;
 #pragma unroll
-    for (int e = 0; e < 16; e++) {
+    for (int e = 0; e < Sh::E; e++) {
         const u32 P = last_pos<Sh>(m, tid, e);
         out[P] = mul_shoup(sub_mod(src[P], x[e], pc.p), cst[0], cst[1], pc.p);
     }
@@ -401,13 +444,13 @@ __global__ void __launch_bounds__(NttShape<LOG_B, LOG_C>::T, 2) k_mrr_last(EvalA
     const u64 half_P = (pP.p - 1) / 2;
     const DSource ds = dsource(a, c);
     const u64 *y = a.plift + ((size_t)c * 2 + k) * Sh::N;
-    u64 x[16];
+    u64 x[Sh::E];
     auto ld = [&](u32 P) -> u64 { return centred_mod(y[P], half_P, cst[2], pc); };
     auto nost = [&](u32, u64) {};
-    ntt_fwd_block<Sh>(smem, m, a.ctx.tw_fwd + (size_t)l * Sh::N, pc.p, pc.two_p, ld, nost, x);
+    ntt_fwd_block<Sh>(smem, m, 0, a.ctx.tw_fwd + (size_t)l * Sh::N, pc.p, pc.two_p, ld, nost, x);
     const u64 *accp = a.accq + (((size_t)c * 2 + k) * n + l) * Sh::N;
 #pragma unroll
-    for (int e = 0; e < 16; e++) {
+    for (int e = 0; e < Sh::E; e++) {
         const u32 P = last_pos<Sh>(m, tid, e);
         const u64 v = mul_shoup(sub_mod(accp[P], x[e], pc.p), cst[0], cst[1], pc.p);
         x[e] = add_mod(ds.d(k, l, Sh::LOG_N, P, pc), v, pc.p);
@@ -415,7 +458,7 @@ __global__ void __launch_bounds__(NttShape<LOG_B, LOG_C>::T, 2) k_mrr_last(EvalA
     u64 *dst = a.lift2 + ((size_t)c * 2 + k) * Sh::N;
     auto st = [&](u32 P, u64 v) { dst[P] = v; };
     auto nold = [&](u32) -> u64 { return 0; };
-    ntt_inv_block<Sh, true>(smem, m, a.ctx.tw_inv + (size_t)l * Sh::N, pc, nold, st, x);
+    ntt_inv_block<Sh, true>(smem, m, 0, a.ctx.tw_inv + (size_t)l * Sh::N, pc, nold, st, x);
 }
 
 // MulLinRS, limbs i < l: mod-down by P then rescale by q_l, two NTTs.
@@ -438,13 +481,13 @@ __global__ void __launch_bounds__(NttShape<LOG_B, LOG_C>::T, 2) k_mrr_rest(EvalA
     const DSource ds = dsource(a, c);
     const ulonglong2 *twf = a.ctx.tw_fwd + (size_t)i * Sh::N;
     const u64 *y = a.plift + ((size_t)c * 2 + k) * Sh::N;
-    u64 x[16], z[16];
+    u64 x[Sh::E], z[Sh::E];
     auto nost = [&](u32, u64) {};
     auto ld1 = [&](u32 P) -> u64 { return centred_mod(y[P], half_P, cP[2], pc); };
-    ntt_fwd_block<Sh>(smem, m, twf, pc.p, pc.two_p, ld1, nost, x);
+    ntt_fwd_block<Sh>(smem, m, 0, twf, pc.p, pc.two_p, ld1, nost, x);
     const u64 *accp = a.accq + (((size_t)c * 2 + k) * n + i) * Sh::N;
 #pragma unroll
-    for (int e = 0; e < 16; e++) {
+    for (int e = 0; e < Sh::E; e++) {
         const u32 P = last_pos<Sh>(m, tid, e);
         const u64 v = mul_shoup(sub_mod(accp[P], x[e], pc.p), cP[0], cP[1], pc.p);
         z[e] = add_mod(ds.d(k, i, Sh::LOG_N, P, pc), v, pc.p);
@@ -452,10 +495,10 @@ __global__ void __launch_bounds__(NttShape<LOG_B, LOG_C>::T, 2) k_mrr_rest(EvalA
     ntt_barrier<Sh>();
     const u64 *y2 = a.lift2 + ((size_t)c * 2 + k) * Sh::N;
     auto ld2 = [&](u32 P) -> u64 { return centred_mod(y2[P], half_l, cl[2], pc); };
-    ntt_fwd_block<Sh>(smem, m, twf, pc.p, pc.two_p, ld2, nost, x);
+    ntt_fwd_block<Sh>(smem, m, 0, twf, pc.p, pc.two_p, ld2, nost, x);
     u64 *out = a.out + (((size_t)c * 2 + k) * l + i) * Sh::N;
 #pragma unroll
-    for (int e = 0; e < 16; e++) {
+    for (int e = 0; e < Sh::E; e++) {
         const u32 P = last_pos<Sh>(m, tid, e);
         out[P] = mul_shoup(sub_mod(z[e], x[e], pc.p), cl[0], cl[1], pc.p);
     }

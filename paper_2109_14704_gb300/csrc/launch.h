@@ -31,6 +31,21 @@ struct NttLaunch {
     const LimbJob *jobs;        // non-null: per-item jobs instead of base/limbs
 };
 
+// A unit of the mixed-degree persistent transform: up to 8 >> (log_n - 12)
+// limbs of degree 2^log_n, jobs[first_job .. first_job + n_jobs).
+struct MixedUnit {
+    u32 log_n;
+    u32 first_job;
+    u32 n_jobs;
+    u32 pad;
+};
+
+// Mixed-degree transform of N in [2^12, 2^15]: one launch of `clusters`
+// clusters of 8 CTAs walking the unit list (mixed.cu).
+cudaError_t launch_ntt_mixed(const MixedUnit *units, u32 n_units, const LimbJob *jobs, bool inverse, u32 clusters,
+                             cudaStream_t s);
+int mixed_max_clusters(bool inverse);
+
 // Device view of a modulus chain (q_0..q_{n_data-1}, then P at n_data).
 struct DevCtx {
     const ulonglong2 *tw_fwd;   // [n_data + 1][N]
@@ -70,23 +85,28 @@ enum EvalKernel {
     EK_COUNT
 };
 
-// Launchers of one polynomial degree N = 2^log_n. Shapes are given by
-// log_b (words per CTA = 2^log_b, cluster of N / 2^log_b CTAs); 0 picks the
-// default shape of the degree.
+// Launchers of one polynomial degree N = 2^log_n. A transform shape is
+// (log_b, log_e): 2^log_b words per CTA (a cluster of N / 2^log_b CTAs per
+// limb) and 2^log_e words per thread (radix-2^log_e register rounds); 0, 0
+// picks the degree's default shape.
 struct DegreeOps {
     int log_n;
     int default_log_b;
+    int default_log_e;
     // Plain transform of a uniform batch or a job list, one cluster per limb.
-    cudaError_t (*ntt)(const NttLaunch &a, int log_b, bool inverse, cudaStream_t s);
+    cudaError_t (*ntt)(const NttLaunch &a, int log_b, int log_e, bool inverse, cudaStream_t s);
     // Persistent transform over a job list with `grid_clusters` clusters.
-    cudaError_t (*ntt_persistent)(const NttLaunch &a, int log_b, bool inverse, u32 grid_clusters,
+    cudaError_t (*ntt_persistent)(const NttLaunch &a, int log_b, int log_e, bool inverse, u32 grid_clusters,
                                   cudaStream_t s);
     // Largest number of co-resident clusters of the persistent kernel.
-    int (*max_clusters)(int log_b, bool inverse);
-    // Evaluation kernels over `items` clusters.
+    int (*max_clusters)(int log_b, int log_e, bool inverse);
+    // Evaluation kernels over `items` clusters (default shape).
     cudaError_t (*eval)(EvalKernel k, const EvalArgs &a, u32 items, cudaStream_t s);
-    // Is the shape log_b built for this degree?
-    bool (*has_shape)(int log_b);
+    // Is the shape built for this degree?
+    bool (*has_shape)(int log_b, int log_e);
+    // Shapes built for this degree: n pairs (log_b, log_e), default first.
+    int n_shapes;
+    const int (*shapes)[2];
 };
 
 const DegreeOps *degree_ops(int log_n);

@@ -1,8 +1,8 @@
 // ntt_core.cuh -- block-level negacyclic NTT building blocks for sm_103a.
 //
-// One limb of N = B * C words is transformed by a thread-block cluster of C
-// CTAs; CTA m owns the contiguous block [m B, (m + 1) B) of positions in
-// shared memory (B = 2^LOG_B words, 16 per thread).
+// One limb of N = B * C words is transformed by C CTAs of a thread-block
+// cluster; CTA m owns the contiguous block [m B, (m + 1) B) of positions in
+// shared memory (B = 2^LOG_B words, E = 2^LOG_E words per thread).
 //
 // Forward transform (Sec. II-B with the psi twist folded into bit-reversed
 // twiddles; Cooley-Tukey stages with Harvey's lazy butterfly, Algorithm 1):
@@ -13,10 +13,10 @@
 //     radix-C network in registers and scatters element t to CTA t through
 //     distributed shared memory (st.shared::cluster). This is the paper's
 //     "global memory" stage group, done without a second pass over HBM.
-//   * The remaining log B stages stay inside one CTA: rounds of up to four
-//     stages (radix 16) in registers, exchanging through shared memory
-//     between rounds (the paper's SLM rounds, Sec. III-B, with a higher
-//     radix than its radix-8 because registers are 64-bit pairs here).
+//   * The remaining log B stages stay inside one CTA: rounds of up to LOG_E
+//     stages (radix E) in registers, exchanging through shared memory
+//     between rounds (the paper's SLM rounds, Sec. III-B; its best radix was
+//     8, here radix 8 and radix 16 are both built and the autotuner picks).
 //   * The last round reduces from [0, 4p) to [0, p) (the paper's last-round
 //     offsetting, fused) and hands each canonical value to the caller's store
 //     functor.
@@ -24,9 +24,10 @@
 // [0, 2p); local rounds first, cross-CTA stages last, N^-1 folded into the
 // final stage.
 //
-// Shared-memory layout: element l of the block sits at word
-// l ^ ((l >> 4) & 15), which keeps every access pattern below free of bank
-// conflicts (each half warp touches 16 distinct 8-byte bank pairs).
+// Shared-memory layout: element l of the block sits at word l ^ f(l >> 4)
+// for a per-radix f (a permutation inside each 16-word row) that keeps every
+// access pattern below free of bank conflicts: each half warp touches 16
+// distinct 8-byte bank pairs.
 #pragma once
 #include <stdint.h>
 
@@ -36,7 +37,21 @@
 
 namespace he {
 
-__device__ __forceinline__ u32 swz(u32 l) { return l ^ ((l >> 4) & 15u); }
+template <int LOG_E>
+__device__ __forceinline__ u32 swz(u32 l);
+
+template <>
+__device__ __forceinline__ u32 swz<4>(u32 l)
+{
+    return l ^ ((l >> 4) & 15u);
+}
+
+template <>
+__device__ __forceinline__ u32 swz<3>(u32 l)
+{
+    const u32 r = l >> 4;
+    return l ^ (((r ^ ((r >> 1) << 2)) * 9u) & 15u);
+}
 
 __device__ __forceinline__ u32 cluster_ctarank()
 {
@@ -74,29 +89,37 @@ __device__ __forceinline__ u64 ld_cluster(u32 addr)
 
 __device__ __forceinline__ ulonglong2 ld_tw(const ulonglong2 *tw, u32 idx) { return __ldg(tw + idx); }
 
-template <int LOG_B_, int LOG_C_>
+template <int LOG_B_, int LOG_C_, int LOG_E_ = 4>
 struct NttShape {
     static constexpr int LOG_B = LOG_B_;
     static constexpr int LOG_C = LOG_C_;
+    static constexpr int LOG_E = LOG_E_;
     static constexpr int LOG_N = LOG_B + LOG_C;
     static constexpr u32 B = 1u << LOG_B;
     static constexpr u32 C = 1u << LOG_C;
     static constexpr u32 N = 1u << LOG_N;
-    static constexpr int E = 16;                  // words per thread
+    static constexpr int E = 1 << LOG_E;          // words per thread
     static constexpr u32 T = B / E;               // threads per CTA
-    static constexpr int NROUND = (LOG_B + 3) / 4;
-    static constexpr int LAST_R = LOG_B - 4 * (NROUND - 1);
+    static constexpr int NROUND = (LOG_B + LOG_E - 1) / LOG_E;
+    static constexpr int LAST_R = LOG_B - LOG_E * (NROUND - 1);
     static constexpr u32 SMEM_BYTES = B * 8;
+    // two CTAs per SM unless a CTA has 1024 threads (registers: 128 per
+    // thread at 256 threads, 64 at 512)
+    static constexpr int MIN_CTAS = T <= 512 ? 2 : 1;
     static_assert(LOG_C <= 3, "portable clusters hold at most 8 CTAs");
-    static_assert(LOG_B >= 9, "at least 32 threads per CTA");
+    static_assert(LOG_C <= LOG_E, "a thread holds whole columns of the cross stages");
+    static_assert(LOG_E == 3 || LOG_E == 4, "radix 8 or 16 rounds");
+    static_assert(T >= 32 && T <= 1024, "one to 32 warps per CTA");
 };
 
-template <int R_, int S0_, int LOG_B>
-struct Round {
-    static constexpr int R = R_;                  // stages in this round
-    static constexpr int S0 = S0_;                // first local stage
-    static constexpr int SUB = 16 >> R;           // subgroups per thread
-    static constexpr int LOG_TL = LOG_B - S0 - R; // log of the smallest gap
+// Round RI of the local stages: R stages starting at local stage S0; each
+// thread holds SUB subgroups of 2^R words spaced TL apart.
+template <class Sh, int RI>
+struct RoundOf {
+    static constexpr int R = (RI < Sh::NROUND - 1) ? Sh::LOG_E : Sh::LAST_R;
+    static constexpr int S0 = Sh::LOG_E * RI;
+    static constexpr int SUB = Sh::E >> R;
+    static constexpr int LOG_TL = Sh::LOG_B - S0 - R;
     static constexpr u32 TL = 1u << LOG_TL;
 };
 
@@ -109,20 +132,6 @@ __device__ __forceinline__ u32 round_pos(u32 tid, int i, int u)
     u32 g = sg >> Rd::LOG_TL;
     return (g << (Rd::LOG_TL + Rd::R)) + k + (u32)u * Rd::TL;
 }
-
-// Barrier between two consecutive block transforms in one CTA: the next
-// transform's first writes to shared memory (remote ones for a cluster) must
-// not overtake reads of the previous transform.
-template <class Sh>
-__device__ __forceinline__ void ntt_barrier()
-{
-    if constexpr (Sh::LOG_C > 0)
-        cluster_sync_all();
-    else
-        __syncthreads();
-}
-
-// ---------------------------------------------------------------- forward
 
 // Group base of subgroup i in a round: the index, at the round's first stage,
 // of the butterfly group that holds the subgroup. At internal stage q the
@@ -137,8 +146,42 @@ __device__ __forceinline__ u32 round_group_base(u32 tid, int i, u32 m)
     return (m << (Sh::LOG_B - Rd::LOG_TL - Rd::R)) + g;
 }
 
+// Barrier between two consecutive block transforms in one CTA: the next
+// transform's first writes to shared memory (remote ones for a cluster) must
+// not overtake reads of the previous transform.
+template <class Sh>
+__device__ __forceinline__ void ntt_barrier()
+{
+    if constexpr (Sh::LOG_C > 0)
+        cluster_sync_all();
+    else
+        __syncthreads();
+}
+
+template <class Sh, class Rd>
+__device__ __forceinline__ void round_load_smem(u64 (&x)[Sh::E], const u64 *s, u32 tid)
+{
+#pragma unroll
+    for (int i = 0; i < Rd::SUB; i++)
+#pragma unroll
+        for (int u = 0; u < (1 << Rd::R); u++)
+            x[i * (1 << Rd::R) + u] = s[swz<Sh::LOG_E>(round_pos<Rd>(tid, i, u))];
+}
+
+template <class Sh, class Rd>
+__device__ __forceinline__ void round_store_smem(const u64 (&x)[Sh::E], u64 *s, u32 tid)
+{
+#pragma unroll
+    for (int i = 0; i < Rd::SUB; i++)
+#pragma unroll
+        for (int u = 0; u < (1 << Rd::R); u++)
+            s[swz<Sh::LOG_E>(round_pos<Rd>(tid, i, u))] = x[i * (1 << Rd::R) + u];
+}
+
+// ---------------------------------------------------------------- forward
+
 template <class Sh, class Rd, int q>
-__device__ __forceinline__ void fwd_stage(u64 (&x)[16], u32 tid, u32 m, const ulonglong2 *tw, u64 p,
+__device__ __forceinline__ void fwd_stage(u64 (&x)[Sh::E], u32 tid, u32 m, const ulonglong2 *tw, u64 p,
                                           u64 two_p)
 {
     constexpr int S = Sh::LOG_C + Rd::S0 + q;     // global stage
@@ -159,57 +202,48 @@ __device__ __forceinline__ void fwd_stage(u64 (&x)[16], u32 tid, u32 m, const ul
 }
 
 template <class Sh, class Rd, int... Q>
-__device__ __forceinline__ void fwd_round_stages(u64 (&x)[16], u32 tid, u32 m, const ulonglong2 *tw,
-                                                 u64 p, u64 two_p, std::integer_sequence<int, Q...>)
+__device__ __forceinline__ void fwd_round_stages(u64 (&x)[Sh::E], u32 tid, u32 m, const ulonglong2 *tw, u64 p,
+                                                 u64 two_p, std::integer_sequence<int, Q...>)
 {
     (fwd_stage<Sh, Rd, Q>(x, tid, m, tw, p, two_p), ...);
 }
 
-template <class Sh, class Rd>
-__device__ __forceinline__ void fwd_round_compute(u64 (&x)[16], u32 tid, u32 m, const ulonglong2 *tw,
-                                                  u64 p, u64 two_p)
+template <class Sh, int RI>
+__device__ __forceinline__ void fwd_round(u64 (&x)[Sh::E], u64 *s, u32 tid, u32 m, const ulonglong2 *tw, u64 p,
+                                          u64 two_p)
 {
+    using Rd = RoundOf<Sh, RI>;
+    if constexpr (RI > 0) {
+        round_store_smem<Sh, RoundOf<Sh, RI - 1>>(x, s, tid);
+        __syncthreads();
+        round_load_smem<Sh, Rd>(x, s, tid);
+    }
     fwd_round_stages<Sh, Rd>(x, tid, m, tw, p, two_p, std::make_integer_sequence<int, Rd::R>{});
 }
 
-template <class Sh, class Rd>
-__device__ __forceinline__ void round_load_smem(u64 (&x)[16], const u64 *s, u32 tid)
+template <class Sh, int... RI>
+__device__ __forceinline__ void fwd_rounds(u64 (&x)[Sh::E], u64 *s, u32 tid, u32 m, const ulonglong2 *tw, u64 p,
+                                           u64 two_p, std::integer_sequence<int, RI...>)
 {
-#pragma unroll
-    for (int i = 0; i < Rd::SUB; i++)
-#pragma unroll
-        for (int u = 0; u < (1 << Rd::R); u++) x[i * (1 << Rd::R) + u] = s[swz(round_pos<Rd>(tid, i, u))];
+    (fwd_round<Sh, RI>(x, s, tid, m, tw, p, two_p), ...);
 }
-
-template <class Sh, class Rd>
-__device__ __forceinline__ void round_store_smem(const u64 (&x)[16], u64 *s, u32 tid)
-{
-#pragma unroll
-    for (int i = 0; i < Rd::SUB; i++)
-#pragma unroll
-        for (int u = 0; u < (1 << Rd::R); u++) s[swz(round_pos<Rd>(tid, i, u))] = x[i * (1 << Rd::R) + u];
-}
-
-template <class Sh, int RI>
-struct RoundOf {
-    using type = Round<(RI < Sh::NROUND - 1) ? 4 : Sh::LAST_R, 4 * RI, Sh::LOG_B>;
-};
 
 // Cross-CTA stages of the forward transform: load columns, radix-C network,
-// scatter into the owning CTAs' shared memory, cluster barrier.
+// scatter into the owning CTAs' shared memory (ranks rbase .. rbase + C - 1
+// of the cluster), cluster barrier.
 template <class Sh, class Load>
-__device__ __forceinline__ void fwd_cross(u64 *s, u32 tid, u32 m, const ulonglong2 *tw, u64 p, u64 two_p,
-                                          Load &load)
+__device__ __forceinline__ void fwd_cross(u64 *s, u32 tid, u32 m, u32 rbase, const ulonglong2 *tw, u64 p,
+                                          u64 two_p, Load &load)
 {
     constexpr u32 C = Sh::C;
-    constexpr int COLS = 16 / (int)C;
+    constexpr int COLS = Sh::E / (int)C;
     ulonglong2 wt[C];
 #pragma unroll
     for (u32 i = 1; i < C; i++) wt[i] = ld_tw(tw, i);
     const u32 s_base = smem_u32(s);
 #pragma unroll
     for (int c = 0; c < COLS; c++) {
-        u32 j = m * (Sh::B / C) + (u32)c * Sh::T + tid;
+        const u32 j = m * (Sh::B / C) + (u32)c * Sh::T + tid;
         u64 v[C];
 #pragma unroll
         for (u32 t = 0; t < C; t++) v[t] = load(t * Sh::B + j);
@@ -219,33 +253,31 @@ __device__ __forceinline__ void fwd_cross(u64 *s, u32 tid, u32 m, const ulonglon
 #pragma unroll
             for (u32 t = 0; t < C; t++) {
                 if (t & half) continue;
-                u32 idx = (1u << S) + (t >> (Sh::LOG_C - S));
+                const u32 idx = (1u << S) + (t >> (Sh::LOG_C - S));
                 ct_butterfly(v[t], v[t + half], wt[idx].x, wt[idx].y, p, two_p);
             }
         }
-        u32 a = s_base + swz(j) * 8u;
+        const u32 a = s_base + swz<Sh::LOG_E>(j) * 8u;
 #pragma unroll
-        for (u32 t = 0; t < C; t++) st_cluster(map_to_rank(a, t), v[t]);
+        for (u32 t = 0; t < C; t++) st_cluster(map_to_rank(a, rbase + t), v[t]);
     }
     cluster_sync_all();
 }
 
-// Forward negacyclic NTT of one limb. load(P) gives input position P in
-// [0, N) (values below 4p); store(P, v) receives the canonical output at
-// bit-reversed evaluation index P. After the call the values also remain in
-// x[] in the last round's order (round_pos of the last round), canonical.
+// Forward negacyclic NTT of one limb. m is this CTA's block (rank within its
+// group of C CTAs, which sit at cluster ranks rbase .. rbase + C - 1).
+// load(P) gives input position P in [0, N) (values below 4p); store(P, v)
+// receives the canonical output at bit-reversed evaluation index P. After
+// the call the canonical values also remain in x[] in the last round's order
+// (see last_pos).
 template <class Sh, class Load, class Store>
-__device__ __forceinline__ void ntt_fwd_block(u64 *s, u32 m, const ulonglong2 *tw, u64 p, u64 two_p,
-                                              Load load, Store store, u64 (&x)[16])
+__device__ __forceinline__ void ntt_fwd_block(u64 *s, u32 m, u32 rbase, const ulonglong2 *tw, u64 p, u64 two_p,
+                                              Load load, Store store, u64 (&x)[Sh::E])
 {
     const u32 tid = threadIdx.x;
-    using R0 = typename RoundOf<Sh, 0>::type;
-    using R1 = typename RoundOf<Sh, (Sh::NROUND > 1 ? 1 : 0)>::type;
-    using R2 = typename RoundOf<Sh, (Sh::NROUND > 2 ? 2 : 0)>::type;
-    using R3 = typename RoundOf<Sh, (Sh::NROUND > 3 ? 3 : 0)>::type;
-
+    using R0 = RoundOf<Sh, 0>;
     if constexpr (Sh::LOG_C > 0) {
-        fwd_cross<Sh>(s, tid, m, tw, p, two_p, load);
+        fwd_cross<Sh>(s, tid, m, rbase, tw, p, two_p, load);
         round_load_smem<Sh, R0>(x, s, tid);
     } else {
 #pragma unroll
@@ -253,35 +285,25 @@ __device__ __forceinline__ void ntt_fwd_block(u64 *s, u32 m, const ulonglong2 *t
 #pragma unroll
             for (int u = 0; u < (1 << R0::R); u++) x[i * (1 << R0::R) + u] = load(round_pos<R0>(tid, i, u));
     }
-    fwd_round_compute<Sh, R0>(x, tid, m, tw, p, two_p);
-    using RL = typename RoundOf<Sh, Sh::NROUND - 1>::type;
-    if constexpr (Sh::NROUND > 1) {
-        round_store_smem<Sh, R0>(x, s, tid);
-        __syncthreads();
-        round_load_smem<Sh, R1>(x, s, tid);
-        fwd_round_compute<Sh, R1>(x, tid, m, tw, p, two_p);
-    }
-    if constexpr (Sh::NROUND > 2) {
-        round_store_smem<Sh, R1>(x, s, tid);
-        __syncthreads();
-        round_load_smem<Sh, R2>(x, s, tid);
-        fwd_round_compute<Sh, R2>(x, tid, m, tw, p, two_p);
-    }
-    if constexpr (Sh::NROUND > 3) {
-        round_store_smem<Sh, R2>(x, s, tid);
-        __syncthreads();
-        round_load_smem<Sh, R3>(x, s, tid);
-        fwd_round_compute<Sh, R3>(x, tid, m, tw, p, two_p);
-    }
-    static_assert(Sh::NROUND <= 4, "at most four local rounds");
+    fwd_rounds<Sh>(x, s, tid, m, tw, p, two_p, std::make_integer_sequence<int, Sh::NROUND>{});
+    using RL = RoundOf<Sh, Sh::NROUND - 1>;
 #pragma unroll
     for (int i = 0; i < RL::SUB; i++)
 #pragma unroll
         for (int u = 0; u < (1 << RL::R); u++) {
-            u64 v = reduce_once(reduce_once(x[i * (1 << RL::R) + u], two_p), p);
+            const u64 v = reduce_once(reduce_once(x[i * (1 << RL::R) + u], two_p), p);
             x[i * (1 << RL::R) + u] = v;
             store(m * Sh::B + round_pos<RL>(tid, i, u), v);
         }
+}
+
+// Position (within the limb) of element e of x[] after ntt_fwd_block, and of
+// the input element e expected by ntt_inv_block with HAVE_X.
+template <class Sh>
+__device__ __forceinline__ u32 last_pos(u32 m, u32 tid, int e)
+{
+    using RL = RoundOf<Sh, Sh::NROUND - 1>;
+    return m * Sh::B + round_pos<RL>(tid, e >> RL::R, e & ((1 << RL::R) - 1));
 }
 
 // ---------------------------------------------------------------- inverse
@@ -290,14 +312,14 @@ __device__ __forceinline__ void ntt_fwd_block(u64 *s, u32 m, const ulonglong2 *t
 // (x, y) -> ((x + y) N^-1, (x - y) psi^-brv(1) N^-1), canonical outputs.
 __device__ __forceinline__ void gs_last(u64 &x, u64 &y, const PrimeConst &pc)
 {
-    u64 X = mul_shoup(x + y, pc.ninv, pc.ninv_sh, pc.p);
-    u64 Y = mul_shoup(x - y + pc.two_p, pc.w1ninv, pc.w1ninv_sh, pc.p);
+    const u64 X = mul_shoup(x + y, pc.ninv, pc.ninv_sh, pc.p);
+    const u64 Y = mul_shoup(x - y + pc.two_p, pc.w1ninv, pc.w1ninv_sh, pc.p);
     x = X;
     y = Y;
 }
 
 template <class Sh, class Rd, int q>
-__device__ __forceinline__ void inv_stage(u64 (&x)[16], u32 tid, u32 m, const ulonglong2 *tw,
+__device__ __forceinline__ void inv_stage(u64 (&x)[Sh::E], u32 tid, u32 m, const ulonglong2 *tw,
                                           const PrimeConst &pc)
 {
     constexpr int S = Sh::LOG_C + Rd::S0 + q;
@@ -328,61 +350,48 @@ __device__ __forceinline__ void inv_stage(u64 (&x)[16], u32 tid, u32 m, const ul
 
 // Stages of an inverse round run in decreasing order (increasing gap).
 template <class Sh, class Rd, int... Q>
-__device__ __forceinline__ void inv_round_stages(u64 (&x)[16], u32 tid, u32 m, const ulonglong2 *tw,
+__device__ __forceinline__ void inv_round_stages(u64 (&x)[Sh::E], u32 tid, u32 m, const ulonglong2 *tw,
                                                  const PrimeConst &pc, std::integer_sequence<int, Q...>)
 {
     (inv_stage<Sh, Rd, Rd::R - 1 - Q>(x, tid, m, tw, pc), ...);
 }
 
-template <class Sh, class Rd>
-__device__ __forceinline__ void inv_round_compute(u64 (&x)[16], u32 tid, u32 m, const ulonglong2 *tw,
-                                                  const PrimeConst &pc)
+// Inverse rounds run from the last local round down to round 0.
+template <class Sh, int RI>
+__device__ __forceinline__ void inv_round(u64 (&x)[Sh::E], u64 *s, u32 tid, u32 m, const ulonglong2 *tw,
+                                          const PrimeConst &pc)
 {
+    using Rd = RoundOf<Sh, RI>;
+    if constexpr (RI < Sh::NROUND - 1) {
+        round_store_smem<Sh, RoundOf<Sh, RI + 1>>(x, s, tid);
+        __syncthreads();
+        round_load_smem<Sh, Rd>(x, s, tid);
+    }
     inv_round_stages<Sh, Rd>(x, tid, m, tw, pc, std::make_integer_sequence<int, Rd::R>{});
 }
 
+template <class Sh, int... Q>
+__device__ __forceinline__ void inv_rounds(u64 (&x)[Sh::E], u64 *s, u32 tid, u32 m, const ulonglong2 *tw,
+                                           const PrimeConst &pc, std::integer_sequence<int, Q...>)
+{
+    (inv_round<Sh, Sh::NROUND - 1 - Q>(x, s, tid, m, tw, pc), ...);
+}
+
 // Inverse negacyclic NTT (with N^-1) of one limb. If the caller already
-// holds the block's values in x[] in the forward transform's last-round
-// order, pass have_x = true and load is not called; otherwise load(P) gives
-// the NTT-domain value at position P (below 2p). store(P, v) receives the
-// canonical coefficient P.
+// holds the block's values in x[] in last_pos order, pass HAVE_X = true and
+// load is not called; otherwise load(P) gives the NTT-domain value at
+// position P (below 2p). store(P, v) receives the canonical coefficient P.
 template <class Sh, bool HAVE_X, class Load, class Store>
-__device__ __forceinline__ void ntt_inv_block(u64 *s, u32 m, const ulonglong2 *tw, const PrimeConst &pc,
-                                              Load load, Store store, u64 (&x)[16])
+__device__ __forceinline__ void ntt_inv_block(u64 *s, u32 m, u32 rbase, const ulonglong2 *tw, const PrimeConst &pc,
+                                              Load load, Store store, u64 (&x)[Sh::E])
 {
     const u32 tid = threadIdx.x;
-    constexpr int NR = Sh::NROUND;
-    using RL = typename RoundOf<Sh, NR - 1>::type;
-    using RL1 = typename RoundOf<Sh, (NR >= 2 ? NR - 2 : 0)>::type;
-    using RL2 = typename RoundOf<Sh, (NR >= 3 ? NR - 3 : 0)>::type;
-    using RL3 = typename RoundOf<Sh, (NR >= 4 ? NR - 4 : 0)>::type;
-    static_assert(NR >= 2 && NR <= 4, "two to four local rounds");
-
     if constexpr (!HAVE_X) {
 #pragma unroll
-        for (int i = 0; i < RL::SUB; i++)
-#pragma unroll
-            for (int u = 0; u < (1 << RL::R); u++)
-                x[i * (1 << RL::R) + u] = load(m * Sh::B + round_pos<RL>(tid, i, u));
+        for (int e = 0; e < Sh::E; e++) x[e] = load(last_pos<Sh>(m, tid, e));
     }
-    inv_round_compute<Sh, RL>(x, tid, m, tw, pc);
-    round_store_smem<Sh, RL>(x, s, tid);
-    __syncthreads();
-    round_load_smem<Sh, RL1>(x, s, tid);
-    inv_round_compute<Sh, RL1>(x, tid, m, tw, pc);
-    if constexpr (NR > 2) {
-        round_store_smem<Sh, RL1>(x, s, tid);
-        __syncthreads();
-        round_load_smem<Sh, RL2>(x, s, tid);
-        inv_round_compute<Sh, RL2>(x, tid, m, tw, pc);
-    }
-    if constexpr (NR > 3) {
-        round_store_smem<Sh, RL2>(x, s, tid);
-        __syncthreads();
-        round_load_smem<Sh, RL3>(x, s, tid);
-        inv_round_compute<Sh, RL3>(x, tid, m, tw, pc);
-    }
-    using R0 = typename RoundOf<Sh, 0>::type;
+    inv_rounds<Sh>(x, s, tid, m, tw, pc, std::make_integer_sequence<int, Sh::NROUND>{});
+    using R0 = RoundOf<Sh, 0>;
     if constexpr (Sh::LOG_C == 0) {
         // round 0 ended with the final stage: values are canonical
 #pragma unroll
@@ -393,18 +402,18 @@ __device__ __forceinline__ void ntt_inv_block(u64 *s, u32 m, const ulonglong2 *t
         round_store_smem<Sh, R0>(x, s, tid);
         cluster_sync_all();
         constexpr u32 C = Sh::C;
-        constexpr int COLS = 16 / (int)C;
+        constexpr int COLS = Sh::E / (int)C;
         ulonglong2 wt[C];
 #pragma unroll
         for (u32 i = 2; i < C; i++) wt[i] = ld_tw(tw, i);
         const u32 s_base = smem_u32(s);
 #pragma unroll
         for (int c = 0; c < COLS; c++) {
-            u32 j = m * (Sh::B / C) + (u32)c * Sh::T + tid;
-            u32 a = s_base + swz(j) * 8u;
+            const u32 j = m * (Sh::B / C) + (u32)c * Sh::T + tid;
+            const u32 a = s_base + swz<Sh::LOG_E>(j) * 8u;
             u64 v[C];
 #pragma unroll
-            for (u32 t = 0; t < C; t++) v[t] = ld_cluster(map_to_rank(a, t));
+            for (u32 t = 0; t < C; t++) v[t] = ld_cluster(map_to_rank(a, rbase + t));
 #pragma unroll
             for (int SS = 0; SS < Sh::LOG_C; SS++) {
                 const int S = Sh::LOG_C - 1 - SS;
@@ -415,7 +424,7 @@ __device__ __forceinline__ void ntt_inv_block(u64 *s, u32 m, const ulonglong2 *t
                     if (S == 0) {
                         gs_last(v[t], v[t + half], pc);
                     } else {
-                        u32 idx = (1u << S) + (t >> (Sh::LOG_C - S));
+                        const u32 idx = (1u << S) + (t >> (Sh::LOG_C - S));
                         gs_butterfly(v[t], v[t + half], wt[idx].x, wt[idx].y, pc.p, pc.two_p);
                     }
                 }

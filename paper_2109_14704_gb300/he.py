@@ -36,7 +36,8 @@ class PolyDesc(ctypes.Structure):
 
 
 class NttShape(ctypes.Structure):
-    _fields_ = [("N", ctypes.c_uint32), ("log_block", ctypes.c_uint32)]
+    _fields_ = [("N", ctypes.c_uint32), ("log_block", ctypes.c_uint32), ("log_thread_words", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
 
 
 _SIGS = {
@@ -74,6 +75,9 @@ _SIGS = {
     "he_ntt_plan_inv": (ctypes.c_int32, [_vp, _vp]),
     "he_plan_destroy": (ctypes.c_int32, [_vp]),
     "he_plan_launches": (ctypes.c_uint32, [_vp]),
+    "he_ntt_shapes": (ctypes.c_int32, [ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32), ctypes.c_uint32,
+                                       ctypes.POINTER(ctypes.c_uint32)]),
+    "he_ntt_set_shape": (ctypes.c_int32, [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32]),
     "he_butterfly_probe": (ctypes.c_int32, [_vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, _vp]),
     "he_mul_relin_rescale_noalloc": (ctypes.c_int32, [_vp, _vp, _vp, ctypes.c_uint32, _vp, _vp, ctypes.c_uint32,
                                                       _vp]),
@@ -198,6 +202,20 @@ class NttTables:
             pass
 
 
+def ntt_shapes(N: int) -> list[tuple[int, int]]:
+    """Transform shapes (log_block, log_thread_words) built for degree N,
+    default first."""
+    n = ctypes.c_uint32()
+    buf = (ctypes.c_uint32 * 32)()
+    _check(load().he_ntt_shapes(N, buf, 16, ctypes.byref(n)))
+    return [(buf[2 * i], buf[2 * i + 1]) for i in range(min(n.value, 16))]
+
+
+def ntt_set_shape(N: int, log_block: int = 0, log_thread_words: int = 0):
+    """Shape used by ntt_fwd / ntt_inv at degree N (0, 0 = default)."""
+    _check(load().he_ntt_set_shape(N, log_block, log_thread_words))
+
+
 def _moduli_arg(tables: NttTables, limbs: int, moduli):
     m = _host_u64(tables.moduli[:limbs] if moduli is None else list(moduli)[:limbs])
     return m
@@ -312,7 +330,8 @@ def mul_relin_rescale(ct_out, ct_a, ct_b, count: int, key: RelinKey, ctx: Contex
 
 
 class NttPlan:
-    """he_plan over a list of (tensor, tables, N, limbs, first_prime)."""
+    """he_plan over a list of (tensor, tables, N, limbs, first_prime).
+    `shapes` maps N to log_block or to (log_block, log_thread_words)."""
 
     def __init__(self, polys, shapes=None):
         arr = (PolyDesc * max(len(polys), 1))()
@@ -326,8 +345,9 @@ class NttPlan:
             self._keep.append((data, tables))
         shapes = shapes or {}
         sh = (NttShape * max(len(shapes), 1))()
-        for i, (N, lb) in enumerate(shapes.items()):
-            sh[i].N, sh[i].log_block = N, lb
+        for i, (N, shape) in enumerate(shapes.items()):
+            lb, le = (shape, 4) if isinstance(shape, int) else shape
+            sh[i].N, sh[i].log_block, sh[i].log_thread_words = N, lb, le
         h = _vp()
         _check(load().he_ntt_plan_create(arr, len(polys), sh, len(shapes), ctypes.byref(h)))
         self.handle = h

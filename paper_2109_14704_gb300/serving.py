@@ -1,0 +1,302 @@
+"""Continuous-batching request loop for mul-relin-rescale (MulLinRS) jobs.
+
+The paper's client/server flow (Sec. III): the host encrypts, ships
+ciphertexts and static data (keys) to the GPU once, the GPU evaluates
+asynchronously and the host synchronises only to read results back; device
+buffers come from a memory cache that reuses any free buffer large enough
+(Sec. III-C, "memory cache"). This module turns that into a server:
+
+* Requests (N, level, input pair) arrive by an open-loop Poisson process.
+* Relinearization keys of every degree stay resident on the device.
+* A request is admitted into the open batch of its (N, level) bucket as soon
+  as the batch has a free slot and the device-memory ledger (keys + tables +
+  every batch buffer in use, against an HBM budget) can hold the batch; its
+  input ciphertexts are copied from pinned host memory straight into the
+  batch slot.
+* A bucket's open batch is launched (one he_mul_relin_rescale call over all
+  its slots: four kernels) when it is full, when a stream is idle, or when
+  its oldest request has waited max_wait_s; meanwhile new arrivals fill the
+  next open batch (continuous batching), and batches in flight on several
+  streams overlap on the device.
+* Completion is timed with CUDA events; latency = completion - arrival on
+  one clock (events are anchored to the host clock at start). Buffers go
+  back to the memory cache when the batch's completion event has fired.
+"""
+from __future__ import annotations
+
+import collections
+import statistics
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import he
+from .synth import Rng
+
+
+class DeviceMemoryCache:
+    """Device buffer pool: allocate reuses any free buffer with capacity at
+    least the request (smallest such first), else allocates; free returns a
+    buffer to the pool. `in_use` and `reserved` feed the admission ledger."""
+
+    def __init__(self, device):
+        import torch
+        self.torch = torch
+        self.device = device
+        self.free_list: list = []          # (capacity_words, tensor)
+        self.reserved = 0                  # bytes held by the cache (free + in use)
+        self.in_use = 0
+        self.hits = 0
+        self.misses = 0
+
+    def allocate(self, words: int):
+        best = None
+        for i, (cap, _) in enumerate(self.free_list):
+            if cap >= words and (best is None or cap < self.free_list[best][0]):
+                best = i
+        if best is not None:
+            cap, t = self.free_list.pop(best)
+            self.hits += 1
+        else:
+            t = self.torch.empty(words, dtype=self.torch.int64, device=self.device)
+            cap = words
+            self.reserved += cap * 8
+            self.misses += 1
+        self.in_use += cap * 8
+        return cap, t
+
+    def free(self, cap: int, t):
+        self.in_use -= cap * 8
+        self.free_list.append((cap, t))
+
+
+@dataclass
+class Request:
+    rid: int
+    arrival: float
+    N: int
+    level: int
+    src: int                               # index into the host input pool
+    done: float = -1.0
+    batch: "Batch | None" = None
+    slot: int = -1
+
+
+@dataclass
+class Batch:
+    key: tuple
+    cap: int
+    bufs: list = field(default_factory=list)   # (capacity, tensor) for a, b, out, scratch
+    reqs: list = field(default_factory=list)
+    opened: float = 0.0
+    stream: object = None
+    done_event: object = None
+    launched: bool = False
+
+
+class Server:
+    """MulLinRS server over degrees `degrees` and levels [min_level, max_level]."""
+
+    def __init__(self, degrees=(8192, 16384, 32768), min_level=2, max_level=16, budget_bytes=64 << 30,
+                 slots=16, streams=4, max_wait_s=0.002, pool_per_bucket=2, seed=5, device=None):
+        import torch
+        self.torch = torch
+        self.device = device or torch.device("cuda", torch.cuda.current_device())
+        self.degrees = list(degrees)
+        self.min_level, self.max_level = min_level, max_level
+        self.budget = budget_bytes
+        self.slots = slots
+        self.max_wait = max_wait_s
+        self.streams = [torch.cuda.Stream(device=self.device) for _ in range(streams)]
+        self.busy = {i: None for i in range(streams)}
+        self.cache = DeviceMemoryCache(self.device)
+        self.rng = Rng(seed)
+        self.ctx, self.key, self.moduli = {}, {}, {}
+        self.static_bytes = 0
+        n_data = max_level + 1
+        for N in self.degrees:
+            data, P = he.chain_primes(N, [60] + [50] * (n_data - 1), 60)
+            self.moduli[N] = data
+            self.ctx[N] = he.Context(N, data, P)
+            evk = np.stack([np.stack([self.rng.uniform_limbs(data + [P], N) for _ in range(2)])
+                            for _ in range(n_data)])
+            self.key[N] = he.RelinKey(self.ctx[N], evk)
+            # resident: key words with Shoup quotients, twiddles of n_data+1 primes, constants
+            self.static_bytes += evk.size * 16 + (n_data + 1) * N * 32
+        # Client-side input pool: pinned host ciphertext pairs per (N, level).
+        self.pool = {}
+        for N in self.degrees:
+            for lvl in range(min_level, max_level + 1):
+                qs = self.moduli[N][:lvl + 1]
+                pairs = np.stack([np.stack([np.stack([self.rng.uniform_limbs(qs, N) for _ in range(2)])
+                                            for _ in range(2)]) for _ in range(pool_per_bucket)])
+                self.pool[(N, lvl)] = torch.from_numpy(pairs.view(np.int64)).pin_memory()  # [P][2 a/b][2][n][N]
+        self.open = {}
+        self.inflight: list[Batch] = []
+        self.waiting: collections.deque = collections.deque()
+        self.completed: list[Request] = []
+        self.keep: dict = {}                   # rid -> result copy (host) for requests to check
+        self.peak_ledger = 0
+        self.batches_launched = 0
+
+    # ---- ledger
+    def ledger(self) -> int:
+        return self.static_bytes + self.cache.in_use
+
+    def _batch_words(self, N, lvl, cap):
+        n = lvl + 1
+        ct_in = 2 * n * N
+        return [cap * ct_in, cap * ct_in, cap * 2 * lvl * N, self.ctx[N].mrr_scratch_bytes(lvl, cap) // 8]
+
+    def _open_batch(self, key, now):
+        N, lvl = key
+        words = self._batch_words(N, lvl, self.slots)
+        need = sum(words) * 8
+        if self.ledger() + need > self.budget:
+            return None
+        b = Batch(key=key, cap=self.slots, opened=now)
+        b.bufs = [self.cache.allocate(w) for w in words]
+        self.open[key] = b
+        self.peak_ledger = max(self.peak_ledger, self.ledger())
+        return b
+
+    # ---- request flow
+    def _admit(self, req: Request, now) -> bool:
+        key = (req.N, req.level)
+        b = self.open.get(key)
+        if b is None:
+            b = self._open_batch(key, now)
+            if b is None:
+                return False
+        slot = len(b.reqs)
+        n = req.level + 1
+        per = 2 * n * req.N
+        src = self.pool[key][req.src]
+        a_t, b_t = b.bufs[0][1], b.bufs[1][1]
+        # upload of the request's two ciphertexts into the batch slot
+        with self.torch.cuda.stream(self.streams[0]):
+            a_t[slot * per:(slot + 1) * per].copy_(src[0].reshape(-1), non_blocking=True)
+            b_t[slot * per:(slot + 1) * per].copy_(src[1].reshape(-1), non_blocking=True)
+        req.batch, req.slot = b, slot
+        b.reqs.append(req)
+        if len(b.reqs) == b.cap:
+            self._launch(b)
+        return True
+
+    def _free_stream(self):
+        for i, bt in self.busy.items():
+            if bt is None:
+                return i
+        return None
+
+    def _launch(self, b: Batch, stream_index=None):
+        torch = self.torch
+        if stream_index is None:
+            stream_index = self._free_stream()
+            if stream_index is None:
+                stream_index = min(self.busy, key=lambda i: self.busy[i].opened if self.busy[i] else 0)
+        s = self.streams[stream_index]
+        s.wait_stream(self.streams[0])          # the uploads
+        N, lvl = b.key
+        n = lvl + 1
+        count = len(b.reqs)
+        per_in, per_out = 2 * n * N, 2 * lvl * N
+        a = b.bufs[0][1][:count * per_in]
+        bb = b.bufs[1][1][:count * per_in]
+        out = b.bufs[2][1][:count * per_out]
+        scratch = b.bufs[3][1]
+        he.mul_relin_rescale(out, a, bb, count, self.key[N], self.ctx[N], lvl, scratch, stream=s)
+        ev = torch.cuda.Event(enable_timing=True)
+        ev.record(s)
+        b.done_event, b.stream, b.launched = ev, s, True
+        self.busy[stream_index] = b
+        b.stream_index = stream_index
+        self.open.pop(b.key, None)
+        self.inflight.append(b)
+        self.batches_launched += 1
+
+    def _retire(self):
+        still = []
+        for b in self.inflight:
+            if b.done_event.query():
+                t = self.t0_host + self.anchor.elapsed_time(b.done_event) / 1e3
+                N, lvl = b.key
+                per_out = 2 * lvl * N
+                for r in b.reqs:
+                    r.done = t
+                    self.completed.append(r)
+                    if r.rid in self.keep:
+                        self.keep[r.rid] = b.bufs[2][1][r.slot * per_out:(r.slot + 1) * per_out].cpu().clone()
+                for cap, t_ in b.bufs:
+                    self.cache.free(cap, t_)
+                if self.busy.get(b.stream_index) is b:
+                    self.busy[b.stream_index] = None
+            else:
+                still.append(b)
+        self.inflight = still
+
+    def make_requests(self, n_requests: int, rate: float, seed: int = 5) -> list[Request]:
+        r = Rng(seed, stream=1)
+        gaps = r.exponential(n_requests, rate)
+        arrivals = np.cumsum(gaps)
+        degs = r.choice(self.degrees, n_requests)
+        lvls = r.choice(list(range(self.min_level, self.max_level + 1)), n_requests)
+        srcs = r.choice(list(range(self.pool[(self.degrees[0], self.min_level)].shape[0])), n_requests)
+        return [Request(i, float(arrivals[i]), int(degs[i]), int(lvls[i]), int(srcs[i])) for i in range(n_requests)]
+
+    def run(self, requests: list[Request], keep_ids=()) -> dict:
+        """Serve `requests` (arrival times in seconds from start) in real time."""
+        torch = self.torch
+        self.keep = {rid: None for rid in keep_ids}
+        pending = collections.deque(sorted(requests, key=lambda q: q.arrival))
+        torch.cuda.synchronize()
+        self.anchor = torch.cuda.Event(enable_timing=True)
+        self.anchor.record(self.streams[0])
+        self.anchor.synchronize()
+        self.t0_host = time.perf_counter()
+        total = len(pending)
+        while len(self.completed) < total:
+            now = time.perf_counter() - self.t0_host
+            while pending and pending[0].arrival <= now:
+                self.waiting.append(pending.popleft())
+            while self.waiting:
+                if not self._admit(self.waiting[0], now):
+                    break
+                self.waiting.popleft()
+            for key, b in list(self.open.items()):
+                if b.reqs and (self._free_stream() is not None or now - b.reqs[0].arrival >= self.max_wait):
+                    self._launch(b)
+            self._retire()
+            if not pending and not self.waiting:
+                for b in list(self.open.values()):
+                    if b.reqs:
+                        self._launch(b)
+            if pending and not self.inflight and not self.waiting:
+                time.sleep(max(0.0, min(pending[0].arrival - now, 0.0005)))
+        torch.cuda.synchronize()
+        lat = [(r.done - r.arrival) * 1e3 for r in self.completed]
+        span = max(r.done for r in self.completed) - min(r.arrival for r in self.completed)
+        return {
+            "requests": total,
+            "throughput_per_s": total / span if span > 0 else float("nan"),
+            "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": statistics.mean(lat),
+            "batches": self.batches_launched,
+            "mean_batch": total / max(1, self.batches_launched),
+            "peak_ledger_gb": self.peak_ledger / 2 ** 30,
+            "budget_gb": self.budget / 2 ** 30,
+            "cache_hits": self.cache.hits, "cache_misses": self.cache.misses,
+        }
+
+    def serve_alone(self, req: Request):
+        """The result of one request run by itself (a batch of one)."""
+        torch = self.torch
+        N, lvl = req.N, req.level
+        src = self.pool[(N, lvl)][req.src].to(self.device)
+        out = torch.empty(2 * lvl * N, dtype=torch.int64, device=self.device)
+        scratch = torch.empty(self.ctx[N].mrr_scratch_bytes(lvl, 1) // 8, dtype=torch.int64, device=self.device)
+        he.mul_relin_rescale(out, src[0].contiguous(), src[1].contiguous(), 1, self.key[N], self.ctx[N], lvl, scratch)
+        torch.cuda.synchronize()
+        return out.cpu()

@@ -48,22 +48,71 @@ def test_ntt_parity_every_degree(log_n):
         assert np.array_equal(got[p], oracle.ntt_inv(y[p], qs)), p
 
 
-@pytest.mark.parametrize("log_n,log_b", [(12, 11), (12, 10), (13, 13), (13, 11), (14, 13), (14, 11), (15, 13),
-                                         (11, 10)])
-def test_ntt_parity_alternate_shapes(log_n, log_b):
-    """Every kernel shape the autotuner may choose, through a plan."""
+SHAPES = [(10, 10, 3), (11, 11, 3), (11, 10, 4), (12, 12, 3), (12, 11, 4), (12, 10, 4), (13, 13, 4),
+          (13, 12, 3), (13, 11, 4), (14, 13, 4), (14, 12, 3), (14, 11, 4), (15, 13, 4), (15, 12, 3),
+          (15, 13, 3), (16, 13, 3)]
+
+
+@pytest.mark.parametrize("log_n,log_b,log_e", SHAPES)
+def test_ntt_parity_alternate_shapes(log_n, log_b, log_e):
+    """Every non-default kernel shape the autotuner may choose, through a
+    plan (persistent launch), forward and inverse."""
     N = 1 << log_n
     qs = _moduli(N, 4)
     tables = he.NttTables(N, qs)
-    x = np.stack([Rng(300 + log_b + p).uniform_limbs(qs, N) for p in range(3)])
+    x = np.stack([Rng(300 + log_b + 7 * log_e + p).uniform_limbs(qs, N) for p in range(3)])
     d = dev(x)
-    plan = he.NttPlan([(d[p], tables, N, 4, 0) for p in range(3)], shapes={N: log_b})
+    plan = he.NttPlan([(d[p], tables, N, 4, 0) for p in range(3)], shapes={N: (log_b, log_e)})
+    assert plan.launches == 1
     plan.fwd()
     got = host(d)
     for p in range(3):
         assert np.array_equal(got[p], oracle.ntt_fwd(x[p], qs))
     plan.inv()
     assert np.array_equal(host(d), x)
+
+
+def test_mixed_degree_plan_single_launch():
+    """Uneven batch (N from 2^12 to 2^15, 1 to 16 limbs from a pool of
+    50-60-bit primes = 1 mod 2^16) in one launch per direction, with ragged
+    limb counts that leave sub-clusters idle in the last unit of a degree."""
+    pool = he.primes_generate(60, 1 << 16, 6) + he.primes_generate(55, 1 << 16, 5) + \
+        he.primes_generate(50, 1 << 16, 5)
+    tables = {N: he.NttTables(N, pool) for N in (4096, 8192, 16384, 32768)}
+    r = Rng(3)
+    Ns = [4096, 32768, 8192, 16384, 4096, 8192, 16384, 32768, 4096, 16384, 8192, 4096]
+    limbs = [1, 3, 16, 5, 7, 2, 1, 1, 16, 3, 9, 4]
+    firsts = [0, 2, 0, 11, 4, 14, 15, 5, 0, 1, 7, 12]
+    polys = []
+    for N, L, f in zip(Ns, limbs, firsts):
+        polys.append(r.uniform_limbs(pool[f:f + L], N))
+    d = [dev(x) for x in polys]
+    plan = he.NttPlan([(d[i], tables[N], N, L, f) for i, (N, L, f) in enumerate(zip(Ns, limbs, firsts))])
+    assert plan.launches == 1
+    plan.fwd()
+    for i, (N, L, f) in enumerate(zip(Ns, limbs, firsts)):
+        assert np.array_equal(host(d[i]), oracle.ntt_fwd(polys[i], pool[f:f + L])), i
+    plan.inv()
+    for i in range(len(polys)):
+        assert np.array_equal(host(d[i]), polys[i]), i
+
+
+def test_per_degree_plan_with_shapes():
+    """A plan with shape overrides runs one persistent launch per degree."""
+    pool = he.primes_generate(60, 1 << 16, 3)
+    tabs = {N: he.NttTables(N, pool) for N in (1024, 4096, 65536)}
+    r = Rng(8)
+    xs = [r.uniform_limbs(pool, N) for N in (1024, 4096, 65536)]
+    ds = [dev(x) for x in xs]
+    plan = he.NttPlan([(ds[i], tabs[N], N, 3, 0) for i, N in enumerate((1024, 4096, 65536))],
+                      shapes={65536: (13, 3)})
+    assert plan.launches == 3
+    plan.fwd()
+    for i in range(3):
+        assert np.array_equal(host(ds[i]), oracle.ntt_fwd(xs[i], pool))
+    plan.inv()
+    for i in range(3):
+        assert np.array_equal(host(ds[i]), xs[i])
 
 
 def test_ntt_edge_values():

@@ -1,0 +1,24 @@
+"""The device memory cache's reuse policy (Sec. III-C memory cache: reuse a
+free buffer whose capacity covers the request), exercised on host tensors."""
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2109_14704_gb300.serving import DeviceMemoryCache  # noqa: E402
+
+
+def test_reuse_smallest_sufficient_buffer():
+    c = DeviceMemoryCache(torch.device("cpu"))
+    a = c.allocate(100)
+    b = c.allocate(400)
+    assert c.misses == 2 and c.in_use == 500 * 8 and c.reserved == 500 * 8
+    c.free(*a)
+    c.free(*b)
+    assert c.in_use == 0
+    cap, t = c.allocate(90)            # fits both; the smaller one is taken
+    assert cap == 100 and c.hits == 1
+    cap2, t2 = c.allocate(300)         # only the larger one fits
+    assert cap2 == 400 and c.hits == 2
+    cap3, _ = c.allocate(500)          # nothing fits: a new buffer
+    assert cap3 == 500 and c.misses == 3 and c.reserved == 1000 * 8
+    assert c.in_use == 1000 * 8
