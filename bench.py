@@ -304,9 +304,9 @@ def run_ours(args, rank, world, local):
 
     ms_e2e = max_over_ranks(_time_steps(step_e2e, max(3, args.steps // 2), 1, stream, barrier))
     clk = clocks.stop()
+    assert torch.equal(back, pinned), "round trip changed the data"
     del pinned, back
     serve = bench_serving(args) if "serving" not in args.skip else None
-    assert torch.equal(back, pinned), "round trip changed the data"
 
     # integer roof: register-resident butterflies on every SM
     sink = torch.empty(sms * 8 * 256, dtype=torch.int64, device=dev)
@@ -520,8 +520,13 @@ def bench_serving(args):
         srv.run(srv.make_requests(300, rate=2000.0, seed=55))              # warm-up
         srv.completed.clear()
         srv.batches_launched = 0
-        stats = srv.run(srv.make_requests(args.serve_requests, rate=2000.0, seed=5))
-        out[name] = stats
+        out[name] = srv.run(srv.make_requests(args.serve_requests, rate=2000.0, seed=5))
+        # capacity: the same request mix arriving far faster than it can be served
+        srv.completed.clear()
+        srv.batches_launched = 0
+        sat = srv.run(srv.make_requests(args.serve_requests, rate=1e6, seed=6))
+        out[name]["saturated_throughput_per_s"] = sat["throughput_per_s"]
+        out[name]["saturated_mean_batch"] = sat["mean_batch"]
         del srv
     return out
 

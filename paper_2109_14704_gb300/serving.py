@@ -10,7 +10,8 @@ buffers come from a memory cache that reuses any free buffer large enough
 * Relinearization keys of every degree stay resident on the device.
 * A request is admitted into the open batch of its (N, level) bucket as soon
   as the batch has a free slot and the device-memory ledger (keys + tables +
-  every batch buffer in use, against an HBM budget) can hold the batch; its
+  every buffer the memory cache holds, against an HBM budget; free cached
+  buffers are evicted to make room) can hold the batch; its
   input ciphertexts are copied from pinned host memory straight into the
   batch slot.
 * A bucket's open batch is launched (one he_mul_relin_rescale call over all
@@ -38,7 +39,8 @@ from .synth import Rng
 class DeviceMemoryCache:
     """Device buffer pool: allocate reuses any free buffer with capacity at
     least the request (smallest such first), else allocates; free returns a
-    buffer to the pool. `in_use` and `reserved` feed the admission ledger."""
+    buffer to the pool. `reserved` (bytes held, free or in use) is what the
+    admission ledger counts; free buffers can be evicted to make room."""
 
     def __init__(self, device):
         import torch
@@ -49,12 +51,50 @@ class DeviceMemoryCache:
         self.in_use = 0
         self.hits = 0
         self.misses = 0
+        self.evicted = 0
 
-    def allocate(self, words: int):
+    def _pick(self, words, taken):
         best = None
         for i, (cap, _) in enumerate(self.free_list):
-            if cap >= words and (best is None or cap < self.free_list[best][0]):
+            if i not in taken and cap >= words and (best is None or cap < self.free_list[best][0]):
                 best = i
+        return best
+
+    def growth(self, words_list) -> int:
+        """Bytes of new memory that allocating all of words_list would add."""
+        taken, grow = set(), 0
+        for w in words_list:
+            i = self._pick(w, taken)
+            if i is None:
+                grow += w * 8
+            else:
+                taken.add(i)
+        return grow
+
+    def allocate_within(self, words_list, limit_bytes: int, base_bytes: int = 0):
+        """Allocate every request of words_list so that base_bytes + reserved
+        stays within limit_bytes, evicting free buffers when that makes room;
+        None (and nothing allocated) if it cannot."""
+        while base_bytes + self.reserved + self.growth(words_list) > limit_bytes:
+            if not self.free_list:
+                return None
+            # evict the largest free buffer not needed by this request
+            taken = set()
+            for w in words_list:
+                i = self._pick(w, taken)
+                if i is not None:
+                    taken.add(i)
+            spare = [i for i in range(len(self.free_list)) if i not in taken]
+            if not spare:
+                return None
+            j = max(spare, key=lambda i: self.free_list[i][0])
+            cap, _ = self.free_list.pop(j)
+            self.reserved -= cap * 8
+            self.evicted += 1
+        return [self.allocate(w) for w in words_list]
+
+    def allocate(self, words: int):
+        best = self._pick(words, set())
         if best is not None:
             cap, t = self.free_list.pop(best)
             self.hits += 1
@@ -142,7 +182,7 @@ class Server:
 
     # ---- ledger
     def ledger(self) -> int:
-        return self.static_bytes + self.cache.in_use
+        return self.static_bytes + self.cache.reserved
 
     def _batch_words(self, N, lvl, cap):
         n = lvl + 1
@@ -152,11 +192,11 @@ class Server:
     def _open_batch(self, key, now):
         N, lvl = key
         words = self._batch_words(N, lvl, self.slots)
-        need = sum(words) * 8
-        if self.ledger() + need > self.budget:
+        bufs = self.cache.allocate_within(words, self.budget, self.static_bytes)
+        if bufs is None:
             return None
         b = Batch(key=key, cap=self.slots, opened=now)
-        b.bufs = [self.cache.allocate(w) for w in words]
+        b.bufs = bufs
         self.open[key] = b
         self.peak_ledger = max(self.peak_ledger, self.ledger())
         return b
@@ -220,7 +260,7 @@ class Server:
         still = []
         for b in self.inflight:
             if b.done_event.query():
-                t = self.t0_host + self.anchor.elapsed_time(b.done_event) / 1e3
+                t = self.anchor.elapsed_time(b.done_event) / 1e3     # seconds since start
                 N, lvl = b.key
                 per_out = 2 * lvl * N
                 for r in b.reqs:
@@ -287,7 +327,7 @@ class Server:
             "mean_batch": total / max(1, self.batches_launched),
             "peak_ledger_gb": self.peak_ledger / 2 ** 30,
             "budget_gb": self.budget / 2 ** 30,
-            "cache_hits": self.cache.hits, "cache_misses": self.cache.misses,
+            "cache_hits": self.cache.hits, "cache_misses": self.cache.misses, "cache_evictions": self.cache.evicted,
         }
 
     def serve_alone(self, req: Request):

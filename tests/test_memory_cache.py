@@ -22,3 +22,23 @@ def test_reuse_smallest_sufficient_buffer():
     cap3, _ = c.allocate(500)          # nothing fits: a new buffer
     assert cap3 == 500 and c.misses == 3 and c.reserved == 1000 * 8
     assert c.in_use == 1000 * 8
+
+
+def test_allocate_within_budget_evicts_free_buffers():
+    c = DeviceMemoryCache(torch.device("cpu"))
+    a = c.allocate(100)
+    b = c.allocate(200)
+    c.free(*a)
+    c.free(*b)
+    assert c.reserved == 300 * 8
+    # 150 words reuse the 200-word buffer: no growth, fits a 300-word budget
+    got = c.allocate_within([150], limit_bytes=300 * 8)
+    assert got is not None and got[0][0] == 200 and c.reserved == 300 * 8
+    c.free(*got[0])
+    # 250 words need new memory; evicting free buffers makes room
+    got = c.allocate_within([250], limit_bytes=300 * 8)
+    assert got is not None and c.reserved <= 300 * 8 and c.evicted >= 1
+    # nothing free to evict and no room: refused, nothing allocated
+    before = (c.reserved, c.in_use)
+    assert c.allocate_within([100], limit_bytes=300 * 8) is None
+    assert (c.reserved, c.in_use) == before
