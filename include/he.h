@@ -12,7 +12,7 @@
  * Conventions shared by every call
  * --------------------------------
  * Words.    Every coefficient is a uint64_t residue. Moduli are odd primes
- *           q < 2^60 with q = 1 mod 2N (Sec. III-A-1 bounds them below 60
+ *           2^30 <= q < 2^60 with q = 1 mod 2N (Sec. III-A-1 bounds them below 60
  *           bits so that lazy reduction and the fused multiply-add never
  *           overflow a 64-bit word).
  * Layout.   Limb-major and contiguous: a polynomial with L limbs is
@@ -146,7 +146,7 @@ he_status he_dyadic_mul(uint64_t *out, const uint64_t *a, const uint64_t *b, uin
 /* ---- CKKS evaluation (Sec. II-A) ------------------------------------------- */
 
 /* A modulus chain: n_data data primes q_0..q_L (L = n_data - 1, n_data <= 32)
- * and one special prime P, all distinct, q < 2^60, q = 1 mod 2N. Builds the
+ * and one special prime P, all distinct, 2^30 <= q < 2^60, q = 1 mod 2N. Builds the
  * NTT tables of all n_data + 1 primes and the constants of key switching and
  * rescaling. Synchronises. */
 he_status he_context_create(uint32_t N, uint32_t n_data, const uint64_t *data_moduli_host,
@@ -262,6 +262,16 @@ uint32_t he_plan_launches(const he_plan *plan);
  * compute roof against which the transforms are reported. */
 he_status he_butterfly_probe(uint64_t *sink, uint32_t blocks, uint32_t threads, uint32_t iters,
                              he_stream_t stream);
+
+/* The transform butterflies applied elementwise to device arrays of n
+ * entries, for checking their contract (Algorithm 1) on the device. Forward
+ * (inverse = 0): for x, y in [0, 8p + 2^32), w < p and w_shoup =
+ * floor(w 2^64 / p), x' = x + w y and y' = x - w y (mod p), both again in
+ * [0, 8p + 2^32). Inverse (inverse = 1): for x, y in [0, 4p),
+ * x' = x + y and y' = (x - y) w (mod p), both in [0, 4p). 2^30 <= p < 2^60,
+ * p need not be prime. x and y are updated in place. */
+he_status he_butterfly_apply(uint64_t *x, uint64_t *y, const uint64_t *w, const uint64_t *w_shoup,
+                             uint32_t n, uint64_t p, int32_t inverse, he_stream_t stream);
 
 #ifdef __cplusplus
 }

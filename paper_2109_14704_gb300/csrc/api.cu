@@ -172,6 +172,26 @@ extern "C" he_status he_primes_generate(uint32_t bits, uint64_t two_n, uint32_t 
 
 // ------------------------------------------------------------------ tables
 
+// Per-prime constants of the kernels; w1 = psi^-brv(1), the twiddle of the
+// last inverse stage.
+static he::PrimeConst prime_const(u64 q, u32 N, u64 w1)
+{
+    he::PrimeConst c;
+    memset(&c, 0, sizeof c);
+    c.p = q;
+    c.two_p = 2 * q;
+    c.four_p = 4 * q;
+    c.neg_p = 0 - q;
+    c.h4 = (u32)((4 * (u128)q + 0xffffffffull) >> 32);
+    c.bits = (u32)bit_length(q);
+    c.mu = (u64)(((u128)1 << (2 * c.bits + 2)) / q);
+    c.ninv = h_inv(N % q, q);
+    c.ninv_sh = shoup(c.ninv, q);
+    c.w1ninv = h_mul(w1, c.ninv, q);
+    c.w1ninv_sh = shoup(c.w1ninv, q);
+    return c;
+}
+
 struct he_ntt_tables {
     u32 N = 0;
     int log_n = 0;
@@ -182,9 +202,17 @@ struct he_ntt_tables {
     he::PrimeConst *d_pc = nullptr;
 };
 
+// the lazy butterfly ranges need 2^30 <= q < 2^60 (Sec. III-A-1: below 60 bits)
+static he_status check_modulus_range(u64 q)
+{
+    if (q < (1ull << 30) || q >= (1ull << 60))
+        return fail(HE_EINVAL, "modulus %llu outside [2^30, 2^60)", (unsigned long long)q);
+    return HE_OK;
+}
+
 static he_status check_modulus(u64 q, u32 N)
 {
-    if (q < 3 || q >= (1ull << 60)) return fail(HE_EINVAL, "modulus %llu outside [3, 2^60)", (unsigned long long)q);
+    if (he_status s = check_modulus_range(q)) return s;
     if ((q - 1) % (2ull * N)) return fail(HE_EINVAL, "modulus %llu is not 1 mod 2N (N = %u)", (unsigned long long)q, N);
     if (!h_is_prime(q)) return fail(HE_EINVAL, "modulus %llu is not prime", (unsigned long long)q);
     return HE_OK;
@@ -242,16 +270,7 @@ extern "C" he_status he_ntt_tables_create(uint32_t N, uint32_t limbs, const uint
             fwd[(size_t)l * N + k] = make_ulonglong2(w, shoup(w, q));
             inv[(size_t)l * N + k] = make_ulonglong2(wi, shoup(wi, q));
         }
-        he::PrimeConst &c = pcs[l];
-        memset(&c, 0, sizeof c);
-        c.p = q;
-        c.two_p = 2 * q;
-        c.bits = (u32)bit_length(q);
-        c.mu = (u64)(((u128)1 << (2 * c.bits + 2)) / q);
-        c.ninv = h_inv(N, q);
-        c.ninv_sh = shoup(c.ninv, q);
-        c.w1ninv = h_mul(inv[(size_t)l * N + 1].x, c.ninv, q);
-        c.w1ninv_sh = shoup(c.w1ninv, q);
+        pcs[l] = prime_const(q, N, inv[(size_t)l * N + 1].x);
     }
     cudaError_t e;
     if ((e = cudaMalloc(&t->d_fwd, fwd.size() * sizeof(ulonglong2))) != cudaSuccess ||
@@ -731,18 +750,18 @@ extern "C" he_status he_mul_relin_rescale(uint64_t *ct_out, const uint64_t *ct_a
 // memory traffic, so the launch measures the integer-pipe ceiling of the
 // transform's arithmetic. One word per thread is written so nothing is
 // optimised away.
-__global__ void k_butterfly_probe(u64 *sink, u64 p, u64 w, u64 w_sh, u32 iters)
+__global__ void k_butterfly_probe(u64 *sink, const he::PrimeConst c, u64 w, u64 w_sh, u32 iters)
 {
-    const u64 two_p = 2 * p;
+    const u64 p = c.p;
     u64 x[16];
 #pragma unroll
     for (int i = 0; i < 16; i++) x[i] = (threadIdx.x * 977 + blockIdx.x * 131 + i * 7919) % p;
     for (u32 it = 0; it < iters; it++) {
 #pragma unroll
-        for (int i = 0; i < 8; i++) he::ct_butterfly(x[i], x[i + 8], w, w_sh, p, two_p);
+        for (int i = 0; i < 8; i++) he::ct_butterfly(x[i], x[i + 8], w, w_sh, c);
 #pragma unroll
         for (int i = 0; i < 8; i++) he::ct_butterfly(x[2 * (i & 3) + (i >> 2) * 8], x[2 * (i & 3) + 1 + (i >> 2) * 8],
-                                                     w, w_sh, p, two_p);
+                                                     w, w_sh, c);
     }
     u64 acc = 0;
 #pragma unroll
@@ -757,7 +776,37 @@ extern "C" he_status he_butterfly_probe(uint64_t *sink, uint32_t blocks, uint32_
     if (!blocks || !threads || threads > 1024 || (threads & 31)) return fail(HE_EINVAL, "bad probe shape");
     const u64 p = 1152921504606584833ull;   // the largest 60-bit prime = 1 mod 2^16
     const u64 w = 123456789012345ull % p;
-    k_butterfly_probe<<<blocks, threads, 0, (cudaStream_t)stream>>>(sink, p, w, shoup(w, p), iters);
+    k_butterfly_probe<<<blocks, threads, 0, (cudaStream_t)stream>>>(sink, prime_const(p, 1u << 15, w), w,
+                                                                    shoup(w, p), iters);
+    HE_CUDA(cudaGetLastError());
+    return HE_OK;
+}
+
+// Elementwise application of the transform butterflies, so that their
+// contract can be checked on the device: forward (Algorithm 1 with the range
+// [0, 8p + 2^32)) or inverse (Gentleman-Sande on [0, 4p)).
+__global__ void k_butterfly_apply(u64 *x, u64 *y, const u64 *w, const u64 *w_sh, u32 n, const he::PrimeConst c,
+                                  int inverse)
+{
+    const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    u64 a = x[i], b = y[i];
+    if (inverse)
+        he::gs_butterfly(a, b, w[i], w_sh[i], c);
+    else
+        he::ct_butterfly(a, b, w[i], w_sh[i], c);
+    x[i] = a;
+    y[i] = b;
+}
+
+extern "C" he_status he_butterfly_apply(uint64_t *x, uint64_t *y, const uint64_t *w, const uint64_t *w_shoup,
+                                        uint32_t n, uint64_t p, int32_t inverse, he_stream_t stream)
+{
+    if (he_status s = check_modulus_range(p)) return s;
+    if (!n) return HE_OK;
+    if (!x || !y || !w || !w_shoup) return fail(HE_EINVAL, "NULL array");
+    k_butterfly_apply<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(x, y, w, w_shoup, n,
+                                                                       prime_const(p, 1024, 1), inverse);
     HE_CUDA(cudaGetLastError());
     return HE_OK;
 }

@@ -38,7 +38,7 @@ k_ntt(NttLaunch a)
     auto ld = [&](u32 P) -> u64 { return data[P]; };
     auto st = [&](u32 P, u64 v) { data[P] = v; };
     if constexpr (!INV)
-        ntt_fwd_block<Sh>(smem, m, 0, tw, pc.p, pc.two_p, ld, st, x);
+        ntt_fwd_block<Sh>(smem, m, 0, tw, pc, ld, st, x);
     else
         ntt_inv_block<Sh, false>(smem, m, 0, tw, pc, ld, st, x);
 }
@@ -63,7 +63,7 @@ k_ntt_persistent(NttLaunch a)
         auto ld = [&](u32 P) -> u64 { return data[P]; };
         auto st = [&](u32 P, u64 v) { data[P] = v; };
         if constexpr (!INV)
-            ntt_fwd_block<Sh>(smem, m, 0, j.tw_fwd, pc.p, pc.two_p, ld, st, x);
+            ntt_fwd_block<Sh>(smem, m, 0, j.tw_fwd, pc, ld, st, x);
         else
             ntt_inv_block<Sh, false>(smem, m, 0, j.tw_inv, pc, ld, st, x);
     }
@@ -92,7 +92,7 @@ __device__ __forceinline__ void mixed_unit(u64 *smem, u32 rank, const MixedUnit 
         if (valid) data[P] = v;
     };
     if constexpr (!INV)
-        ntt_fwd_block<Sh>(smem, m, rbase, j.tw_fwd, pc.p, pc.two_p, ld, st, x);
+        ntt_fwd_block<Sh>(smem, m, rbase, j.tw_fwd, pc, ld, st, x);
     else
         ntt_inv_block<Sh, false>(smem, m, rbase, j.tw_inv, pc, ld, st, x);
 }
@@ -121,7 +121,8 @@ __global__ void __launch_bounds__(256, 2) k_ntt_mixed(const MixedUnit *units, u3
 // ======================================================== naive radix-2 ====
 // The baseline of Sec. III-B: one launch per stage, each thread one
 // butterfly, data exchanged through global memory, and a final pass that
-// reduces [0, 4p) to [0, p) (forward) -- 2 N log N + 2 N global accesses.
+// reduces the lazy range to [0, p) (forward) -- 2 N log N + 2 N global
+// accesses.
 
 __global__ void k_ntt_naive_stage(NttLaunch a, u32 log_n, u32 S, bool inv)
 {
@@ -140,12 +141,12 @@ __global__ void k_ntt_naive_stage(NttLaunch a, u32 log_n, u32 S, bool inv)
     u64 x = data[j], y = data[j + t];
     if (!inv) {
         const ulonglong2 w = a.tw_fwd[(size_t)pr * N + (1u << S) + g];
-        ct_butterfly(x, y, w.x, w.y, pc.p, pc.two_p);
+        ct_butterfly(x, y, w.x, w.y, pc);
     } else if (S == 0) {
         gs_last(x, y, pc);
     } else {
         const ulonglong2 w = a.tw_inv[(size_t)pr * N + (1u << S) + g];
-        gs_butterfly(x, y, w.x, w.y, pc.p, pc.two_p);
+        gs_butterfly(x, y, w.x, w.y, pc);
     }
     data[j] = x;
     data[j + t] = y;
@@ -159,7 +160,7 @@ __global__ void k_ntt_naive_final(NttLaunch a, u32 log_n)
     const u32 item = (u32)(gid >> log_n);
     const PrimeConst &pc = a.pc[a.first_prime + item % a.limbs];
     u64 v = a.base[gid];
-    a.base[gid] = reduce_once(reduce_once(v, pc.two_p), pc.p);
+    a.base[gid] = reduce_from_fwd_range(v, pc);
 }
 
 // =========================================================== dyadic ========
@@ -312,7 +313,7 @@ __global__ void __launch_bounds__(NttShape<LOG_B, LOG_C>::T, 2) k_ks_modup(EvalA
             const u64 *src = a.c2 + ((size_t)c * n + j) * Sh::N;
             auto ld = [&](u32 P) -> u64 { return barrett_reduce(0, src[P], pc.p, pc.mu, pc.bits); };
             auto st = [&](u32, u64) {};
-            ntt_fwd_block<Sh>(smem, m, 0, twf, pc.p, pc.two_p, ld, st, x);
+            ntt_fwd_block<Sh>(smem, m, 0, twf, pc, ld, st, x);
         }
 #pragma unroll
         for (int k = 0; k < 2; k++) {
@@ -368,7 +369,7 @@ __global__ void __launch_bounds__(NttShape<LOG_B, LOG_C>::T, 2) k_ks_moddown(Eva
     u64 x[Sh::E];
     auto ld = [&](u32 P) -> u64 { return centred_mod(y[P], half_P, cst[2], pc); };
     auto st = [&](u32, u64) {};
-    ntt_fwd_block<Sh>(smem, m, 0, a.ctx.tw_fwd + (size_t)i * Sh::N, pc.p, pc.two_p, ld, st, x);
+    ntt_fwd_block<Sh>(smem, m, 0, a.ctx.tw_fwd + (size_t)i * Sh::N, pc, ld, st, x);
     const u64 *accp = a.accq + (((size_t)c * 2 + k) * n + i) * Sh::N;
     u64 *out = a.out + (((size_t)c * 2 + k) * n + i) * Sh::N;
 #pragma unroll
@@ -416,7 +417,7 @@ __global__ void __launch_bounds__(NttShape<LOG_B, LOG_C>::T, 2) k_rs(EvalArgs a)
     u64 x[Sh::E];
     auto ld = [&](u32 P) -> u64 { return centred_mod(y[P], half_l, cst[2], pc); };
     auto st = [&](u32, u64) {};
-    ntt_fwd_block<Sh>(smem, m, 0, a.ctx.tw_fwd + (size_t)i * Sh::N, pc.p, pc.two_p, ld, st, x);
+    ntt_fwd_block<Sh>(smem, m, 0, a.ctx.tw_fwd + (size_t)i * Sh::N, pc, ld, st, x);
     const u64 *src = a.ct2 + (((size_t)c * 2 + k) * n + i) * Sh::N;
     u64 *out = a.out + (((size_t)c * 2 + k) * l + i) * Sh::N;
 #pragma unroll
@@ -447,7 +448,7 @@ __global__ void __launch_bounds__(NttShape<LOG_B, LOG_C>::T, 2) k_mrr_last(EvalA
     u64 x[Sh::E];
     auto ld = [&](u32 P) -> u64 { return centred_mod(y[P], half_P, cst[2], pc); };
     auto nost = [&](u32, u64) {};
-    ntt_fwd_block<Sh>(smem, m, 0, a.ctx.tw_fwd + (size_t)l * Sh::N, pc.p, pc.two_p, ld, nost, x);
+    ntt_fwd_block<Sh>(smem, m, 0, a.ctx.tw_fwd + (size_t)l * Sh::N, pc, ld, nost, x);
     const u64 *accp = a.accq + (((size_t)c * 2 + k) * n + l) * Sh::N;
 #pragma unroll
     for (int e = 0; e < Sh::E; e++) {
@@ -484,7 +485,7 @@ __global__ void __launch_bounds__(NttShape<LOG_B, LOG_C>::T, 2) k_mrr_rest(EvalA
     u64 x[Sh::E], z[Sh::E];
     auto nost = [&](u32, u64) {};
     auto ld1 = [&](u32 P) -> u64 { return centred_mod(y[P], half_P, cP[2], pc); };
-    ntt_fwd_block<Sh>(smem, m, 0, twf, pc.p, pc.two_p, ld1, nost, x);
+    ntt_fwd_block<Sh>(smem, m, 0, twf, pc, ld1, nost, x);
     const u64 *accp = a.accq + (((size_t)c * 2 + k) * n + i) * Sh::N;
 #pragma unroll
     for (int e = 0; e < Sh::E; e++) {
@@ -495,7 +496,7 @@ __global__ void __launch_bounds__(NttShape<LOG_B, LOG_C>::T, 2) k_mrr_rest(EvalA
     ntt_barrier<Sh>();
     const u64 *y2 = a.lift2 + ((size_t)c * 2 + k) * Sh::N;
     auto ld2 = [&](u32 P) -> u64 { return centred_mod(y2[P], half_l, cl[2], pc); };
-    ntt_fwd_block<Sh>(smem, m, 0, twf, pc.p, pc.two_p, ld2, nost, x);
+    ntt_fwd_block<Sh>(smem, m, 0, twf, pc, ld2, nost, x);
     u64 *out = a.out + (((size_t)c * 2 + k) * l + i) * Sh::N;
 #pragma unroll
     for (int e = 0; e < Sh::E; e++) {

@@ -23,13 +23,15 @@ typedef uint32_t u32;
 struct PrimeConst {
     u64 p;
     u64 two_p;
+    u64 four_p;
+    u64 neg_p;       // 2^64 - p
     u64 mu;          // floor(2^(2b+2) / p), b = bit length of p
     u64 ninv;        // N^-1 mod p
     u64 ninv_sh;     // its Shoup quotient
     u64 w1ninv;      // psi^-brv(1) * N^-1 mod p (last inverse stage)
     u64 w1ninv_sh;
     u32 bits;        // b
-    u32 pad;
+    u32 h4;          // ceil(4p / 2^32): high-word threshold of the lazy reduction
 };
 
 __device__ __forceinline__ u64 reduce_once(u64 x, u64 m) { return x >= m ? x - m : x; }
@@ -49,22 +51,62 @@ __device__ __forceinline__ u64 mul_shoup(u64 y, u64 w, u64 w_sh, u64 p)
     return reduce_once(mul_shoup_lazy(y, w, w_sh, p), p);
 }
 
-// Algorithm 1: x, y in [0, 4p) -> x + W y, x - W y (mod p), both in [0, 4p).
-__device__ __forceinline__ void ct_butterfly(u64 &x, u64 &y, u64 w, u64 w_sh, u64 p, u64 two_p)
+// Shoup quotient from three of the four 32 x 32 partial products of
+// W' Y / 2^64: with W' = Wh 2^32 + Wl and Y = Yh 2^32 + Yl,
+//   W' Y / 2^64 = Wh Yh + hi(Wh Yl) + hi(Wl Yh) + f,  0 <= f < 3,
+// (f collects the two dropped low halves and Wl Yl / 2^64), so the result
+// Q' satisfies Q - 2 <= Q' <= Q for the exact Q = floor(W' Y / 2^64).
+__device__ __forceinline__ u64 shoup_quotient_approx(u64 w_sh, u64 y)
 {
-    u64 X = reduce_once(x, two_p);
-    u64 T = mul_shoup_lazy(y, w, w_sh, p);
-    x = X + T;
-    y = X - T + two_p;
+    const u32 wl = (u32)w_sh, wh = (u32)(w_sh >> 32);
+    const u32 yl = (u32)y, yh = (u32)(y >> 32);
+    const u64 s = (u64)__umulhi(wh, yl) + (u64)__umulhi(wl, yh);
+    return (u64)wh * yh + s;
 }
 
-// Inverse (Gentleman-Sande) butterfly on [0, 2p):
-// x, y -> x + y, (x - y) W^-1 (mod p), both in [0, 2p).
-__device__ __forceinline__ void gs_butterfly(u64 &x, u64 &y, u64 w, u64 w_sh, u64 p, u64 two_p)
+// W * Y mod p in [0, 4p) for any Y < 2^64 and p < 2^62: the exact Shoup
+// remainder lies in [0, 2p) and the quotient may be short by up to 2, so the
+// integer W Y - Q' p lies in [0, 4p) and equals its value mod 2^64, formed as
+// W Y + Q' (2^64 - p) in one multiply-add chain.
+__device__ __forceinline__ u64 mul_shoup_lazy4(u64 y, u64 w, u64 w_sh, u64 neg_p)
 {
-    u64 X = reduce_once(x + y, two_p);
-    u64 T = x - y + two_p;
-    y = mul_shoup_lazy(T, w, w_sh, p);
+    return w * y + shoup_quotient_approx(w_sh, y) * neg_p;
+}
+
+// Forward butterfly (Harvey's, Algorithm 1, with wider lazy ranges): for
+// 2^30 <= p < 2^60 and x, y in [0, 8p + 2^32),
+//   x' = x + W y, y' = x - W y (mod p), both again in [0, 8p + 2^32).
+// The reduction of x tests the high word only: if hi(x) >= ceil(4p / 2^32)
+// then x >= 4p and x - 4p < 4p + 2^32; otherwise x < 4p + 2^32 already. With
+// T = W y mod p in [0, 4p): x' < 8p + 2^32 and 0 < y' = x - T + 4p < 8p + 2^32.
+// (8p + 2^32 < 2^64, so every value fits a word.)
+__device__ __forceinline__ void ct_butterfly(u64 &x, u64 &y, u64 w, u64 w_sh, const PrimeConst &c)
+{
+    u64 X = x;
+    if ((u32)(X >> 32) >= c.h4) X -= c.four_p;
+    const u64 T = mul_shoup_lazy4(y, w, w_sh, c.neg_p);
+    x = X + T;
+    y = X + c.four_p - T;
+}
+
+// [0, 8p + 2^32) -> [0, p) for p >= 2^30 (then 8p + 2^32 <= 12p < 16p).
+__device__ __forceinline__ u64 reduce_from_fwd_range(u64 x, const PrimeConst &c)
+{
+    x = reduce_once(x, c.four_p << 1);
+    x = reduce_once(x, c.four_p);
+    x = reduce_once(x, c.two_p);
+    return reduce_once(x, c.p);
+}
+
+// Inverse (Gentleman-Sande) butterfly on [0, 4p):
+// x, y -> x + y, (x - y) W^-1 (mod p), both in [0, 4p): x + y < 8p reduces
+// exactly once by 4p; x - y + 4p lies in (0, 8p) and its lazy Shoup product
+// in [0, 4p).
+__device__ __forceinline__ void gs_butterfly(u64 &x, u64 &y, u64 w, u64 w_sh, const PrimeConst &c)
+{
+    const u64 X = reduce_once(x + y, c.four_p);
+    const u64 T = x - y + c.four_p;
+    y = mul_shoup_lazy4(T, w, w_sh, c.neg_p);
     x = X;
 }
 

@@ -5,7 +5,8 @@
 // shared memory (B = 2^LOG_B words, E = 2^LOG_E words per thread).
 //
 // Forward transform (Sec. II-B with the psi twist folded into bit-reversed
-// twiddles; Cooley-Tukey stages with Harvey's lazy butterfly, Algorithm 1):
+// twiddles; Cooley-Tukey stages with Harvey's lazy butterfly, Algorithm 1,
+// here on the range [0, 8p + 2^32), see modarith.cuh):
 //   stage S (0 .. log N - 1) has 2^S groups of 2 N / 2^S positions; group g
 //   uses W = psi^brv(2^S + g) and pairs positions j and j + N / 2^(S+1).
 //   * The first log C stages pair positions in different CTAs. Each thread
@@ -17,11 +18,11 @@
 //     stages (radix E) in registers, exchanging through shared memory
 //     between rounds (the paper's SLM rounds, Sec. III-B; its best radix was
 //     8, here radix 8 and radix 16 are both built and the autotuner picks).
-//   * The last round reduces from [0, 4p) to [0, p) (the paper's last-round
+//   * The last round reduces to [0, p) (the paper's last-round
 //     offsetting, fused) and hands each canonical value to the caller's store
 //     functor.
 // Inverse transform: the mirror image with Gentleman-Sande butterflies on
-// [0, 2p); local rounds first, cross-CTA stages last, N^-1 folded into the
+// [0, 4p); local rounds first, cross-CTA stages last, N^-1 folded into the
 // final stage.
 //
 // Shared-memory layout: element l of the block sits at word l ^ f(l >> 4)
@@ -181,8 +182,8 @@ __device__ __forceinline__ void round_store_smem(const u64 (&x)[Sh::E], u64 *s, 
 // ---------------------------------------------------------------- forward
 
 template <class Sh, class Rd, int q>
-__device__ __forceinline__ void fwd_stage(u64 (&x)[Sh::E], u32 tid, u32 m, const ulonglong2 *tw, u64 p,
-                                          u64 two_p)
+__device__ __forceinline__ void fwd_stage(u64 (&x)[Sh::E], u32 tid, u32 m, const ulonglong2 *tw,
+                                          const PrimeConst &pc)
 {
     constexpr int S = Sh::LOG_C + Rd::S0 + q;     // global stage
     constexpr int half = 1 << (Rd::R - 1 - q);
@@ -195,22 +196,22 @@ __device__ __forceinline__ void fwd_stage(u64 (&x)[Sh::E], u32 tid, u32 m, const
 #pragma unroll
             for (int v = 0; v < half; v++) {
                 const int u = grp * 2 * half + v;
-                ct_butterfly(x[i * (1 << Rd::R) + u], x[i * (1 << Rd::R) + u + half], w.x, w.y, p, two_p);
+                ct_butterfly(x[i * (1 << Rd::R) + u], x[i * (1 << Rd::R) + u + half], w.x, w.y, pc);
             }
         }
     }
 }
 
 template <class Sh, class Rd, int... Q>
-__device__ __forceinline__ void fwd_round_stages(u64 (&x)[Sh::E], u32 tid, u32 m, const ulonglong2 *tw, u64 p,
-                                                 u64 two_p, std::integer_sequence<int, Q...>)
+__device__ __forceinline__ void fwd_round_stages(u64 (&x)[Sh::E], u32 tid, u32 m, const ulonglong2 *tw,
+                                                 const PrimeConst &pc, std::integer_sequence<int, Q...>)
 {
-    (fwd_stage<Sh, Rd, Q>(x, tid, m, tw, p, two_p), ...);
+    (fwd_stage<Sh, Rd, Q>(x, tid, m, tw, pc), ...);
 }
 
 template <class Sh, int RI>
-__device__ __forceinline__ void fwd_round(u64 (&x)[Sh::E], u64 *s, u32 tid, u32 m, const ulonglong2 *tw, u64 p,
-                                          u64 two_p)
+__device__ __forceinline__ void fwd_round(u64 (&x)[Sh::E], u64 *s, u32 tid, u32 m, const ulonglong2 *tw,
+                                          const PrimeConst &pc)
 {
     using Rd = RoundOf<Sh, RI>;
     if constexpr (RI > 0) {
@@ -218,22 +219,22 @@ __device__ __forceinline__ void fwd_round(u64 (&x)[Sh::E], u64 *s, u32 tid, u32 
         __syncthreads();
         round_load_smem<Sh, Rd>(x, s, tid);
     }
-    fwd_round_stages<Sh, Rd>(x, tid, m, tw, p, two_p, std::make_integer_sequence<int, Rd::R>{});
+    fwd_round_stages<Sh, Rd>(x, tid, m, tw, pc, std::make_integer_sequence<int, Rd::R>{});
 }
 
 template <class Sh, int... RI>
-__device__ __forceinline__ void fwd_rounds(u64 (&x)[Sh::E], u64 *s, u32 tid, u32 m, const ulonglong2 *tw, u64 p,
-                                           u64 two_p, std::integer_sequence<int, RI...>)
+__device__ __forceinline__ void fwd_rounds(u64 (&x)[Sh::E], u64 *s, u32 tid, u32 m, const ulonglong2 *tw,
+                                           const PrimeConst &pc, std::integer_sequence<int, RI...>)
 {
-    (fwd_round<Sh, RI>(x, s, tid, m, tw, p, two_p), ...);
+    (fwd_round<Sh, RI>(x, s, tid, m, tw, pc), ...);
 }
 
 // Cross-CTA stages of the forward transform: load columns, radix-C network,
 // scatter into the owning CTAs' shared memory (ranks rbase .. rbase + C - 1
 // of the cluster), cluster barrier.
 template <class Sh, class Load>
-__device__ __forceinline__ void fwd_cross(u64 *s, u32 tid, u32 m, u32 rbase, const ulonglong2 *tw, u64 p,
-                                          u64 two_p, Load &load)
+__device__ __forceinline__ void fwd_cross(u64 *s, u32 tid, u32 m, u32 rbase, const ulonglong2 *tw,
+                                          const PrimeConst &pc, Load &load)
 {
     constexpr u32 C = Sh::C;
     constexpr int COLS = Sh::E / (int)C;
@@ -254,7 +255,7 @@ __device__ __forceinline__ void fwd_cross(u64 *s, u32 tid, u32 m, u32 rbase, con
             for (u32 t = 0; t < C; t++) {
                 if (t & half) continue;
                 const u32 idx = (1u << S) + (t >> (Sh::LOG_C - S));
-                ct_butterfly(v[t], v[t + half], wt[idx].x, wt[idx].y, p, two_p);
+                ct_butterfly(v[t], v[t + half], wt[idx].x, wt[idx].y, pc);
             }
         }
         const u32 a = s_base + swz<Sh::LOG_E>(j) * 8u;
@@ -266,18 +267,18 @@ __device__ __forceinline__ void fwd_cross(u64 *s, u32 tid, u32 m, u32 rbase, con
 
 // Forward negacyclic NTT of one limb. m is this CTA's block (rank within its
 // group of C CTAs, which sit at cluster ranks rbase .. rbase + C - 1).
-// load(P) gives input position P in [0, N) (values below 4p); store(P, v)
+// load(P) gives input position P in [0, N) (values below 8p); store(P, v)
 // receives the canonical output at bit-reversed evaluation index P. After
 // the call the canonical values also remain in x[] in the last round's order
 // (see last_pos).
 template <class Sh, class Load, class Store>
-__device__ __forceinline__ void ntt_fwd_block(u64 *s, u32 m, u32 rbase, const ulonglong2 *tw, u64 p, u64 two_p,
-                                              Load load, Store store, u64 (&x)[Sh::E])
+__device__ __forceinline__ void ntt_fwd_block(u64 *s, u32 m, u32 rbase, const ulonglong2 *tw,
+                                              const PrimeConst &pc, Load load, Store store, u64 (&x)[Sh::E])
 {
     const u32 tid = threadIdx.x;
     using R0 = RoundOf<Sh, 0>;
     if constexpr (Sh::LOG_C > 0) {
-        fwd_cross<Sh>(s, tid, m, rbase, tw, p, two_p, load);
+        fwd_cross<Sh>(s, tid, m, rbase, tw, pc, load);
         round_load_smem<Sh, R0>(x, s, tid);
     } else {
 #pragma unroll
@@ -285,13 +286,13 @@ __device__ __forceinline__ void ntt_fwd_block(u64 *s, u32 m, u32 rbase, const ul
 #pragma unroll
             for (int u = 0; u < (1 << R0::R); u++) x[i * (1 << R0::R) + u] = load(round_pos<R0>(tid, i, u));
     }
-    fwd_rounds<Sh>(x, s, tid, m, tw, p, two_p, std::make_integer_sequence<int, Sh::NROUND>{});
+    fwd_rounds<Sh>(x, s, tid, m, tw, pc, std::make_integer_sequence<int, Sh::NROUND>{});
     using RL = RoundOf<Sh, Sh::NROUND - 1>;
 #pragma unroll
     for (int i = 0; i < RL::SUB; i++)
 #pragma unroll
         for (int u = 0; u < (1 << RL::R); u++) {
-            const u64 v = reduce_once(reduce_once(x[i * (1 << RL::R) + u], two_p), p);
+            const u64 v = reduce_from_fwd_range(x[i * (1 << RL::R) + u], pc);
             x[i * (1 << RL::R) + u] = v;
             store(m * Sh::B + round_pos<RL>(tid, i, u), v);
         }
@@ -309,13 +310,14 @@ __device__ __forceinline__ u32 last_pos(u32 m, u32 tid, int e)
 // ---------------------------------------------------------------- inverse
 
 // The final inverse stage (S = 0, one group, gap N/2) with N^-1 folded in:
-// (x, y) -> ((x + y) N^-1, (x - y) psi^-brv(1) N^-1), canonical outputs.
+// (x, y) -> ((x + y) N^-1, (x - y) psi^-brv(1) N^-1), canonical outputs
+// (inputs in [0, 4p); the lazy products land in [0, 4p) and reduce twice).
 __device__ __forceinline__ void gs_last(u64 &x, u64 &y, const PrimeConst &pc)
 {
-    const u64 X = mul_shoup(x + y, pc.ninv, pc.ninv_sh, pc.p);
-    const u64 Y = mul_shoup(x - y + pc.two_p, pc.w1ninv, pc.w1ninv_sh, pc.p);
-    x = X;
-    y = Y;
+    const u64 X = mul_shoup_lazy4(x + y, pc.ninv, pc.ninv_sh, pc.neg_p);
+    const u64 Y = mul_shoup_lazy4(x - y + pc.four_p, pc.w1ninv, pc.w1ninv_sh, pc.neg_p);
+    x = reduce_once(reduce_once(X, pc.two_p), pc.p);
+    y = reduce_once(reduce_once(Y, pc.two_p), pc.p);
 }
 
 template <class Sh, class Rd, int q>
@@ -340,8 +342,7 @@ __device__ __forceinline__ void inv_stage(u64 (&x)[Sh::E], u32 tid, u32 m, const
 #pragma unroll
                 for (int v = 0; v < half; v++) {
                     const int u = grp * 2 * half + v;
-                    gs_butterfly(x[i * (1 << Rd::R) + u], x[i * (1 << Rd::R) + u + half], w.x, w.y, pc.p,
-                                 pc.two_p);
+                    gs_butterfly(x[i * (1 << Rd::R) + u], x[i * (1 << Rd::R) + u + half], w.x, w.y, pc);
                 }
             }
         }
@@ -380,7 +381,7 @@ __device__ __forceinline__ void inv_rounds(u64 (&x)[Sh::E], u64 *s, u32 tid, u32
 // Inverse negacyclic NTT (with N^-1) of one limb. If the caller already
 // holds the block's values in x[] in last_pos order, pass HAVE_X = true and
 // load is not called; otherwise load(P) gives the NTT-domain value at
-// position P (below 2p). store(P, v) receives the canonical coefficient P.
+// position P (below 4p). store(P, v) receives the canonical coefficient P.
 template <class Sh, bool HAVE_X, class Load, class Store>
 __device__ __forceinline__ void ntt_inv_block(u64 *s, u32 m, u32 rbase, const ulonglong2 *tw, const PrimeConst &pc,
                                               Load load, Store store, u64 (&x)[Sh::E])
@@ -425,7 +426,7 @@ __device__ __forceinline__ void ntt_inv_block(u64 *s, u32 m, u32 rbase, const ul
                         gs_last(v[t], v[t + half], pc);
                     } else {
                         const u32 idx = (1u << S) + (t >> (Sh::LOG_C - S));
-                        gs_butterfly(v[t], v[t + half], wt[idx].x, wt[idx].y, pc.p, pc.two_p);
+                        gs_butterfly(v[t], v[t + half], wt[idx].x, wt[idx].y, pc);
                     }
                 }
             }

@@ -79,6 +79,7 @@ _SIGS = {
                                        ctypes.POINTER(ctypes.c_uint32)]),
     "he_ntt_set_shape": (ctypes.c_int32, [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32]),
     "he_butterfly_probe": (ctypes.c_int32, [_vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, _vp]),
+    "he_butterfly_apply": (ctypes.c_int32, [_vp, _vp, _vp, _vp, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32, _vp]),
     "he_mul_relin_rescale_noalloc": (ctypes.c_int32, [_vp, _vp, _vp, ctypes.c_uint32, _vp, _vp, ctypes.c_uint32,
                                                       _vp]),
 }
@@ -392,3 +393,9 @@ def mul_relin_rescale_noalloc(ct_out, ct_a, ct_b, count: int, key: RelinKey, ctx
     Calls that can overlap on the GPU share that buffer and must be ordered."""
     _check(load().he_mul_relin_rescale_noalloc(_ptr(ct_out), _ptr(ct_a), _ptr(ct_b), count, key.handle, ctx.handle,
                                                level, _stream(stream)))
+
+
+def butterfly_apply(x, y, w, w_shoup, p: int, inverse: bool = False, stream=None):
+    """Apply the transform butterfly elementwise (device arrays, in place)."""
+    _check(load().he_butterfly_apply(_ptr(x), _ptr(y), _ptr(w), _ptr(w_shoup), x.numel(), p, int(inverse),
+                                     _stream(stream)))
