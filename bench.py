@@ -57,6 +57,7 @@ def _args():
     ap.add_argument("--profile-case", choices=["ntt", "mrr", "probe"],
                     help="run one small case of a kernel family and exit (for profilers)")
     ap.add_argument("--instances", type=int, default=64, help="NTT instances of --profile-case ntt")
+    ap.add_argument("--shape", default="", help="log_block,log_thread_words for --profile-case ntt")
     ap.add_argument("--skip", default="", help="comma list of sub-benchmarks to skip: uneven,matrix,serving")
     ap.add_argument("--serve-requests", type=int, default=4000)
     ap.add_argument("--no-tune-cache", action="store_true", help="always re-run the autotuner")
@@ -356,7 +357,8 @@ def run_ours(args, rank, world, local):
             "inv_limbs_per_s": world * limbs_total / (inv / 1e3),
             "fwd_ms": fwd, "inv_ms": inv, "speedup_vs_naive": ms_naive / ms,
         },
-        "autotune": {"shape": {"log_block": tune["shape"][0], "log_thread_words": tune["shape"][1]},
+        "autotune": {"shape": {"log_block": tune["shape"][0], "log_thread_words": tune["shape"][1],
+                               "persistent": tune["shape"][2]},
                      "candidates": [{"shape": c["shape"], "ms_fwd_inv": c.get("ms_fwd_inv")} for c in tune["candidates"]]},
         "uneven_batch": uneven,
         "matrix_mul_relin_rescale": matrix,
@@ -625,6 +627,8 @@ def profile_case(args):
         N = 1 << NTT_LOG_N
         qs = _ntt_moduli()
         tables = he.NttTables(N, qs)
+        if args.shape:
+            he.ntt_set_shape(N, *([int(v) for v in args.shape.split(",")] + [0, 0, 0])[:3])
         r = Rng(1)
         d = torch.from_numpy(np.stack([r.uniform_limbs(qs, N) for _ in range(args.instances)]).view(np.int64)).to(dev)
         for _ in range(args.steps):

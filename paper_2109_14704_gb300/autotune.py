@@ -5,7 +5,8 @@ library built for that degree (he_ntt_shapes: words per CTA, i.e. how many
 stages run across the CTAs of a cluster versus inside one CTA's shared
 memory, and words per thread, i.e. radix-8 or radix-16 register rounds --
 the paper tuned the same knobs by hand: radix, SLM threshold and register
-slots, Sec. III-B, Sec. V-A). Each candidate is first checked once: its
+slots, Sec. III-B, Sec. V-A), each launched either as one cluster per limb
+or as a persistent grid walking the limbs. Each candidate is first checked once: its
 forward output must equal the default shape's output bit for bit and its
 inverse must restore the input exactly. Candidates are timed with CUDA
 events (forward + inverse, median of `reps` after warm-up); the fastest wins,
@@ -98,22 +99,23 @@ def tune_uniform(N: int, limbs: int, count: int, moduli=None, reps: int = 10, wa
     shapes = he.ntt_shapes(N)
 
     # reference output: the default shape
-    he.ntt_set_shape(N, 0, 0)
+    he.ntt_set_shape(N, 0, 0, 0)
     d.copy_(x_dev)
     he.ntt_fwd(d, N, limbs, count, tables)
     ref = d.clone()
 
     cands = []
+    configs = [(lb, le, pers) for pers in (0, 1) for (lb, le) in shapes]
     try:
-        for idx, (lb, le) in enumerate(shapes):
-            he.ntt_set_shape(N, lb, le)
+        for idx, (lb, le, pers) in enumerate(configs):
+            he.ntt_set_shape(N, lb, le, pers)
             d.copy_(x_dev)
             he.ntt_fwd(d, N, limbs, count, tables)
             ok_fwd = bool(torch.equal(d, ref))
             he.ntt_inv(d, N, limbs, count, tables)
             ok_inv = bool(torch.equal(d, x_dev))
             if not (ok_fwd and ok_inv):
-                cands.append({"index": idx, "shape": [lb, le], "ok": False})
+                cands.append({"index": idx, "shape": [lb, le, pers], "ok": False})
                 continue
 
             def step():
@@ -121,9 +123,9 @@ def tune_uniform(N: int, limbs: int, count: int, moduli=None, reps: int = 10, wa
                 he.ntt_inv(d, N, limbs, count, tables)
 
             ms = _time(step, reps, warmup)
-            cands.append({"index": idx, "shape": [lb, le], "ok": True, "ms_fwd_inv": ms})
+            cands.append({"index": idx, "shape": [lb, le, pers], "ok": True, "ms_fwd_inv": ms})
     finally:
-        he.ntt_set_shape(N, 0, 0)
+        he.ntt_set_shape(N, 0, 0, 0)
     good = [c for c in cands if c["ok"]]
     if not good:
         raise RuntimeError(f"no transform shape for N = {N} passed its check")

@@ -11,19 +11,48 @@ namespace he {
 
 // ============================================================ plain NTT ====
 
-template <int LOG_B, int LOG_C, int LOG_E, bool INV>
-__global__ void __launch_bounds__(NttShape<LOG_B, LOG_C, LOG_E>::T, NttShape<LOG_B, LOG_C, LOG_E>::MIN_CTAS)
-k_ntt(NttLaunch a)
+// Forward or inverse transform of one limb stored at `data` (in place). The
+// forward transform's last round and the inverse transform's first round
+// give each thread runs of consecutive words, which move as 16-byte pairs
+// (streaming cache hints: every word is read and written once per launch);
+// the cross-CTA columns move as single coalesced words. Stores are skipped
+// when !valid (idle sub-clusters of the mixed-degree kernel).
+template <class Sh, bool INV>
+__device__ __forceinline__ void ntt_limb(u64 *smem, u32 m, u32 rbase, u64 *data, const ulonglong2 *tw,
+                                         const PrimeConst &pc, bool valid = true)
 {
-    using Sh = NttShape<LOG_B, LOG_C, LOG_E>;
-    extern __shared__ __align__(16) u64 smem[];
-    const u32 m = (LOG_C > 0) ? cluster_ctarank() : 0u;
-    const u32 item = blockIdx.x >> LOG_C;
-    u64 *data;
-    const ulonglong2 *tw;
-    const PrimeConst *pcp;
+    u64 x[Sh::E];
+    const u32 tid = threadIdx.x;
+    if constexpr (!INV) {
+        auto ld = [&](u32 P) -> u64 { return __ldcs(reinterpret_cast<const unsigned long long *>(data + P)); };
+        auto nost = [&](u32, u64) {};
+        ntt_fwd_block<Sh>(smem, m, rbase, tw, pc, ld, nost, x);
+        if (valid) {
+#pragma unroll
+            for (int e = 0; e < Sh::E; e += 2)
+                __stcs(reinterpret_cast<ulonglong2 *>(data + last_pos<Sh>(m, tid, e)), make_ulonglong2(x[e], x[e + 1]));
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < Sh::E; e += 2) {
+            const ulonglong2 v = __ldcs(reinterpret_cast<const ulonglong2 *>(data + last_pos<Sh>(m, tid, e)));
+            x[e] = v.x;
+            x[e + 1] = v.y;
+        }
+        auto nold = [&](u32) -> u64 { return 0; };
+        auto st = [&](u32 P, u64 v) {
+            if (valid) __stcs(reinterpret_cast<unsigned long long *>(data + P), (unsigned long long)v);
+        };
+        ntt_inv_block<Sh, true>(smem, m, rbase, tw, pc, nold, st, x);
+    }
+}
+
+template <class Sh, bool INV>
+__device__ __forceinline__ void resolve_item(const NttLaunch &a, u32 item, u64 *&data, const ulonglong2 *&tw,
+                                             const PrimeConst *&pcp)
+{
     if (a.jobs) {
-        const LimbJob j = a.jobs[item];
+        const LimbJob &j = a.jobs[item];
         data = j.data;
         tw = INV ? j.tw_inv : j.tw_fwd;
         pcp = j.pc;
@@ -33,17 +62,26 @@ k_ntt(NttLaunch a)
         tw = (INV ? a.tw_inv : a.tw_fwd) + (size_t)pr * Sh::N;
         pcp = a.pc + pr;
     }
-    const PrimeConst pc = *pcp;
-    u64 x[Sh::E];
-    auto ld = [&](u32 P) -> u64 { return data[P]; };
-    auto st = [&](u32 P, u64 v) { data[P] = v; };
-    if constexpr (!INV)
-        ntt_fwd_block<Sh>(smem, m, 0, tw, pc, ld, st, x);
-    else
-        ntt_inv_block<Sh, false>(smem, m, 0, tw, pc, ld, st, x);
 }
 
-// Persistent form for plans: a fixed grid of clusters walks the job list.
+// One cluster per limb.
+template <int LOG_B, int LOG_C, int LOG_E, bool INV>
+__global__ void __launch_bounds__(NttShape<LOG_B, LOG_C, LOG_E>::T, NttShape<LOG_B, LOG_C, LOG_E>::MIN_CTAS)
+k_ntt(NttLaunch a)
+{
+    using Sh = NttShape<LOG_B, LOG_C, LOG_E>;
+    extern __shared__ __align__(16) u64 smem[];
+    const u32 m = (LOG_C > 0) ? cluster_ctarank() : 0u;
+    u64 *data;
+    const ulonglong2 *tw;
+    const PrimeConst *pcp;
+    resolve_item<Sh, INV>(a, blockIdx.x >> LOG_C, data, tw, pcp);
+    const PrimeConst pc = *pcp;
+    ntt_limb<Sh, INV>(smem, m, 0, data, tw, pc);
+}
+
+// Persistent form: a fixed grid of clusters walks the limbs (job list or
+// uniform batch).
 template <int LOG_B, int LOG_C, int LOG_E, bool INV>
 __global__ void __launch_bounds__(NttShape<LOG_B, LOG_C, LOG_E>::T, NttShape<LOG_B, LOG_C, LOG_E>::MIN_CTAS)
 k_ntt_persistent(NttLaunch a)
@@ -56,16 +94,12 @@ k_ntt_persistent(NttLaunch a)
     for (u32 item = blockIdx.x >> LOG_C; item < a.items; item += clusters) {
         if (!first) ntt_barrier<Sh>();
         first = false;
-        const LimbJob j = a.jobs[item];
-        u64 *data = j.data;
-        const PrimeConst pc = *j.pc;
-        u64 x[Sh::E];
-        auto ld = [&](u32 P) -> u64 { return data[P]; };
-        auto st = [&](u32 P, u64 v) { data[P] = v; };
-        if constexpr (!INV)
-            ntt_fwd_block<Sh>(smem, m, 0, j.tw_fwd, pc, ld, st, x);
-        else
-            ntt_inv_block<Sh, false>(smem, m, 0, j.tw_inv, pc, ld, st, x);
+        u64 *data;
+        const ulonglong2 *tw;
+        const PrimeConst *pcp;
+        resolve_item<Sh, INV>(a, item, data, tw, pcp);
+        const PrimeConst pc = *pcp;
+        ntt_limb<Sh, INV>(smem, m, 0, data, tw, pc);
     }
 }
 
@@ -84,17 +118,8 @@ __device__ __forceinline__ void mixed_unit(u64 *smem, u32 rank, const MixedUnit 
     const u32 rbase = sub << Sh::LOG_C;
     const bool valid = sub < un.n_jobs;
     const LimbJob j = jobs[un.first_job + (valid ? sub : 0u)];
-    u64 *data = j.data;
     const PrimeConst pc = *j.pc;
-    u64 x[Sh::E];
-    auto ld = [&](u32 P) -> u64 { return data[P]; };
-    auto st = [&](u32 P, u64 v) {
-        if (valid) data[P] = v;
-    };
-    if constexpr (!INV)
-        ntt_fwd_block<Sh>(smem, m, rbase, j.tw_fwd, pc, ld, st, x);
-    else
-        ntt_inv_block<Sh, false>(smem, m, rbase, j.tw_inv, pc, ld, st, x);
+    ntt_limb<Sh, INV>(smem, m, rbase, j.data, INV ? j.tw_inv : j.tw_fwd, pc, valid);
 }
 
 template <bool INV>

@@ -104,9 +104,10 @@ struct NttShape {
     static constexpr int NROUND = (LOG_B + LOG_E - 1) / LOG_E;
     static constexpr int LAST_R = LOG_B - LOG_E * (NROUND - 1);
     static constexpr u32 SMEM_BYTES = B * 8;
-    // two CTAs per SM unless a CTA has 1024 threads (registers: 128 per
-    // thread at 256 threads, 64 at 512)
-    static constexpr int MIN_CTAS = T <= 512 ? 2 : 1;
+    // CTAs per SM to aim for: a register budget of 128 per thread for
+    // radix-16 rounds and 64 for radix-8 (16 or 8 words in flight)
+    static constexpr int REGS = LOG_E == 4 ? 128 : 64;
+    static constexpr int MIN_CTAS = (65536 / (int)(T * REGS)) > 0 ? 65536 / (int)(T * REGS) : 1;
     static_assert(LOG_C <= 3, "portable clusters hold at most 8 CTAs");
     static_assert(LOG_C <= LOG_E, "a thread holds whole columns of the cross stages");
     static_assert(LOG_E == 3 || LOG_E == 4, "radix 8 or 16 rounds");

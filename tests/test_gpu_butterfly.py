@@ -22,7 +22,7 @@ def _cases(p, hi_bound, n, seed):
     x = r.uniform_mod(hi_bound, n)
     y = r.uniform_mod(hi_bound, n)
     w = r.uniform_mod(p, n)
-    edges_xy = [0, hi_bound - 1, 4 * p - 1, 4 * p, min(hi_bound - 1, 4 * p + (1 << 32) - 1), p, p - 1]
+    edges_xy = [e for e in (0, hi_bound - 1, 4 * p - 1, 4 * p, 4 * p + (1 << 32) - 1, p, p - 1) if e < hi_bound]
     edges_w = [0, 1, p - 1]
     k = 0
     for ex in edges_xy:
