@@ -73,6 +73,36 @@ __device__ __forceinline__ u64 mul_shoup_lazy4(u64 y, u64 w, u64 w_sh, u64 neg_p
     return w * y + shoup_quotient_approx(w_sh, y) * neg_p;
 }
 
+// W Y mod p in [0, 4p) as mul_shoup_lazy4, with the multiply-add chains
+// written out on 32-bit halves: the quotient Q' = Wh Yh + hi(Wh Yl) +
+// hi(Wl Yh) (three products), then T = lo64(W Y) + lo64(Q' (2^64 - p)) (six
+// products, carries by mad.lo.cc / madc.hi).
+__device__ __forceinline__ u64 mul_shoup_lazy4_asm(u64 y, u64 w, u64 w_sh, u64 neg_p)
+{
+    u32 tl, th;
+    asm("{\n\t"
+        ".reg .u32 a, b, ql, qh;\n\t"
+        "mul.hi.u32 a, %3, %4;\n\t"          // hi(Wh' Yl)
+        "mul.hi.u32 b, %2, %5;\n\t"          // hi(Wl' Yh)
+        "add.cc.u32 ql, a, b;\n\t"
+        "addc.u32 qh, 0, 0;\n\t"
+        "mad.lo.cc.u32 ql, %3, %5, ql;\n\t"  // + Wh' Yh
+        "madc.hi.u32 qh, %3, %5, qh;\n\t"
+        "mul.lo.u32 %0, %6, %4;\n\t"         // lo64(W Y)
+        "mul.hi.u32 %1, %6, %4;\n\t"
+        "mad.lo.u32 %1, %6, %5, %1;\n\t"
+        "mad.lo.u32 %1, %7, %4, %1;\n\t"
+        "mad.lo.cc.u32 %0, ql, %8, %0;\n\t"  // + lo64(Q' (2^64 - p))
+        "madc.hi.u32 %1, ql, %8, %1;\n\t"
+        "mad.lo.u32 %1, ql, %9, %1;\n\t"
+        "mad.lo.u32 %1, qh, %8, %1;\n\t"
+        "}"
+        : "=&r"(tl), "=&r"(th)
+        : "r"((u32)w_sh), "r"((u32)(w_sh >> 32)), "r"((u32)y), "r"((u32)(y >> 32)), "r"((u32)w),
+          "r"((u32)(w >> 32)), "r"((u32)neg_p), "r"((u32)(neg_p >> 32)));
+    return ((u64)th << 32) | tl;
+}
+
 // Forward butterfly (Harvey's, Algorithm 1, with wider lazy ranges): for
 // 2^30 <= p < 2^60 and x, y in [0, 8p + 2^32),
 //   x' = x + W y, y' = x - W y (mod p), both again in [0, 8p + 2^32).
@@ -84,7 +114,11 @@ __device__ __forceinline__ void ct_butterfly(u64 &x, u64 &y, u64 w, u64 w_sh, co
 {
     u64 X = x;
     if ((u32)(X >> 32) >= c.h4) X -= c.four_p;
+#ifdef HE_BUTTERFLY_CXX
     const u64 T = mul_shoup_lazy4(y, w, w_sh, c.neg_p);
+#else
+    const u64 T = mul_shoup_lazy4_asm(y, w, w_sh, c.neg_p);
+#endif
     x = X + T;
     y = X + c.four_p - T;
 }
@@ -106,7 +140,11 @@ __device__ __forceinline__ void gs_butterfly(u64 &x, u64 &y, u64 w, u64 w_sh, co
 {
     const u64 X = reduce_once(x + y, c.four_p);
     const u64 T = x - y + c.four_p;
+#ifdef HE_BUTTERFLY_CXX
     y = mul_shoup_lazy4(T, w, w_sh, c.neg_p);
+#else
+    y = mul_shoup_lazy4_asm(T, w, w_sh, c.neg_p);
+#endif
     x = X;
 }
 

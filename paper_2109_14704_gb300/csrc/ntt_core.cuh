@@ -160,24 +160,39 @@ __device__ __forceinline__ void ntt_barrier()
         __syncthreads();
 }
 
+// Shared-memory word index of element u of subgroup i in a round. Both
+// swizzles are linear over GF(2) and the subgroup base and u * TL occupy
+// disjoint bits (base = g << (LOG_TL + R) | k with k < TL), so
+// swz(base + u TL) = swz(base) ^ swz(u << LOG_TL): one per-thread term and
+// a compile-time constant per element.
+template <class Sh, class Rd>
+__device__ __forceinline__ u32 round_base_swz(u32 tid, int i)
+{
+    return swz<Sh::LOG_E>(round_pos<Rd>(tid, i, 0));
+}
+
 template <class Sh, class Rd>
 __device__ __forceinline__ void round_load_smem(u64 (&x)[Sh::E], const u64 *s, u32 tid)
 {
 #pragma unroll
-    for (int i = 0; i < Rd::SUB; i++)
+    for (int i = 0; i < Rd::SUB; i++) {
+        const u32 pb = round_base_swz<Sh, Rd>(tid, i);
 #pragma unroll
         for (int u = 0; u < (1 << Rd::R); u++)
-            x[i * (1 << Rd::R) + u] = s[swz<Sh::LOG_E>(round_pos<Rd>(tid, i, u))];
+            x[i * (1 << Rd::R) + u] = s[pb ^ swz<Sh::LOG_E>((u32)u << Rd::LOG_TL)];
+    }
 }
 
 template <class Sh, class Rd>
 __device__ __forceinline__ void round_store_smem(const u64 (&x)[Sh::E], u64 *s, u32 tid)
 {
 #pragma unroll
-    for (int i = 0; i < Rd::SUB; i++)
+    for (int i = 0; i < Rd::SUB; i++) {
+        const u32 pb = round_base_swz<Sh, Rd>(tid, i);
 #pragma unroll
         for (int u = 0; u < (1 << Rd::R); u++)
-            s[swz<Sh::LOG_E>(round_pos<Rd>(tid, i, u))] = x[i * (1 << Rd::R) + u];
+            s[pb ^ swz<Sh::LOG_E>((u32)u << Rd::LOG_TL)] = x[i * (1 << Rd::R) + u];
+    }
 }
 
 // ---------------------------------------------------------------- forward
