@@ -276,6 +276,7 @@ def run_ours(args, rank, world, local):
 
     ca = torch.from_numpy(cts().view(np.int64)).to(dev)
     cb = torch.from_numpy(cts().view(np.int64)).to(dev)
+    mrr_tune = autotune.tune_mul_relin_rescale(ctx, key, L, MRR_COUNT, reps=5, warmup=2)
     out = torch.empty((MRR_COUNT, 2, L, MRR_N), dtype=torch.int64, device=dev)
     scratch = torch.empty(ctx.mrr_scratch_bytes(L, MRR_COUNT) // 8, dtype=torch.int64, device=dev)
 
@@ -369,6 +370,7 @@ def run_ours(args, rank, world, local):
             "plain_per_s": world * MRR_COUNT / (ms_mrr_plain / 1e3),
             "ms_per_batch": ms_mrr,
             "transforms_per_op": (L + 1) ** 2 + 5 * (L + 1) + 2,
+            "autotune": mrr_tune,
         },
         "roofline": {
             "kernel": "k_ntt forward, 2^12 words per CTA x cluster of 8",
@@ -500,13 +502,16 @@ def bench_matrix(args, stream, barrier):
     A, B = mk(), mk()
     out = torch.empty((count, 2, L, N), dtype=torch.int64, device="cuda")
     scratch = torch.empty(ctx.mrr_scratch_bytes(L, count) // 8, dtype=torch.int64, device="cuda")
+    from paper_2109_14704_gb300 import autotune
+    tune = autotune.tune_mul_relin_rescale(ctx, key, L, count, reps=3, warmup=1)
 
     def step():
         he.mul_relin_rescale(out, A, B, count, key, ctx, L, scratch, stream=stream)
 
     ms = _time_steps(step, args.steps, args.warmup, stream, barrier)
     return {"workload": "32x32 element-wise, N=8192, primes 60/40/40 + 60, 1024 MulLinRS per step",
-            "ms_per_step": ms, "mul_relin_rescale_per_s": count / (ms / 1e3)}
+            "ms_per_step": ms, "mul_relin_rescale_per_s": count / (ms / 1e3),
+            "eval_log_thread_words": tune["log_thread_words"]}
 
 
 def bench_serving(args):

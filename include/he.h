@@ -156,6 +156,11 @@ he_status he_context_create(uint32_t N, uint32_t n_data, const uint64_t *data_mo
                             uint64_t special_modulus, he_context **out);
 he_status he_context_destroy(he_context *ctx);
 
+/* Words per thread of the context's key-switching and rescale kernels:
+ * 2^3 (radix-8 register rounds) or 2^4 (radix-16, the default; 0 restores
+ * it). The autotuner times both. */
+he_status he_context_set_eval_shape(he_context *ctx, uint32_t log_thread_words);
+
 /* Upload a relinearization key. evk_host is [n_data][2][n_data + 1][N] in the
  * NTT domain: digit j, component k, limbs q_0..q_L then P; it must satisfy
  * evk[j][0] + evk[j][1] s = e_j + [j = i] (P mod q_i) s^2 on limb q_i (and no

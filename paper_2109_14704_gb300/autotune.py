@@ -176,3 +176,36 @@ def tune_plan(polys, reps: int = 10, warmup: int = 3, shapes_per_degree: dict | 
     best = min(good, key=lambda r: (r["ms_fwd_inv"], r["index"]))
     return {"best": best, "candidates": results,
             "shapes": {int(k): tuple(v) for k, v in best["shapes"].items()}}
+
+
+def tune_mul_relin_rescale(ctx, key, level: int, count: int, reps: int = 10, warmup: int = 3,
+                           apply: bool = True) -> dict:
+    """Pick the words per thread (radix-8 or radix-16 rounds) of a context's
+    key-switching and rescale kernels for `count` MulLinRS at `level`:
+    each candidate must reproduce the default's output bit for bit."""
+    import torch
+
+    N = ctx.N
+    qs = ctx.data_moduli[:level + 1]
+    r = Rng(0xA071)
+    mk = lambda: torch.from_numpy(np.stack([np.stack([r.uniform_limbs(qs, N) for _ in range(2)])
+                                            for _ in range(count)]).view(np.int64)).cuda()
+    a, b = mk(), mk()
+    out = torch.empty((count, 2, level, N), dtype=torch.int64, device="cuda")
+    scratch = torch.empty(ctx.mrr_scratch_bytes(level, count) // 8, dtype=torch.int64, device="cuda")
+    ctx.set_eval_shape(0)
+    he.mul_relin_rescale(out, a, b, count, key, ctx, level, scratch)
+    ref = out.clone()
+    cands = []
+    for idx, le in enumerate((4, 3)):
+        ctx.set_eval_shape(le)
+        out.zero_()
+        he.mul_relin_rescale(out, a, b, count, key, ctx, level, scratch)
+        ok = bool(torch.equal(out, ref))
+        ms = _time(lambda: he.mul_relin_rescale(out, a, b, count, key, ctx, level, scratch), reps, warmup) \
+            if ok else None
+        cands.append({"index": idx, "log_thread_words": le, "ok": ok, "ms": ms})
+    good = [c for c in cands if c["ok"]]
+    best = min(good, key=lambda c: (c["ms"], c["index"]))
+    ctx.set_eval_shape(best["log_thread_words"] if apply else 0)
+    return {"log_thread_words": best["log_thread_words"], "candidates": cands}

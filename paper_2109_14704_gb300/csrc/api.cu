@@ -183,6 +183,7 @@ static he::PrimeConst prime_const(u64 q, u32 N, u64 w1)
     c.four_p = 4 * q;
     c.neg_p = 0 - q;
     c.h4 = (u32)((4 * (u128)q + 0xffffffffull) >> 32);
+    c.r32 = q > (1ull << 32) ? (u32)(((u128)1 << 64) / q) : 0u;
     c.bits = (u32)bit_length(q);
     c.mu = (u64)(((u128)1 << (2 * c.bits + 2)) / q);
     c.ninv = h_inv(N % q, q);
@@ -485,6 +486,7 @@ struct he_context {
     u64 P = 0;
     he_ntt_tables *tables = nullptr;   // primes q_0..q_L, P
     u64 *d_cst = nullptr;
+    std::atomic<int> eval_log_e{4};    // words per thread of the evaluation kernels
 };
 
 struct he_relin_key {
@@ -545,6 +547,15 @@ extern "C" he_status he_context_create(uint32_t N, uint32_t n_data, const uint64
         return cuda_fail(e, "context constants");
     }
     *out = c;
+    return HE_OK;
+}
+
+extern "C" he_status he_context_set_eval_shape(he_context *ctx, uint32_t log_thread_words)
+{
+    if (!ctx) return fail(HE_EINVAL, "context is NULL");
+    if (log_thread_words != 0 && log_thread_words != 3 && log_thread_words != 4)
+        return fail(HE_EUNSUPPORTED, "evaluation kernels are built with 2^3 or 2^4 words per thread");
+    ctx->eval_log_e.store(log_thread_words ? (int)log_thread_words : 4);
     return HE_OK;
 }
 
@@ -668,7 +679,7 @@ static he_status run_eval(const he_context *ctx, he::EvalKernel k, const he::Eva
                           cudaStream_t s)
 {
     if (!items) return HE_OK;
-    HE_CUDA(he::degree_ops(ctx->log_n)->eval(k, a, items, s));
+    HE_CUDA(he::degree_ops(ctx->log_n)->eval(k, a, items, ctx->eval_log_e.load(), s));
     return HE_OK;
 }
 

@@ -99,8 +99,8 @@ struct ShapeOps {
     case ID: {                                                                           \
         static std::once_flag f;                                                         \
         static cudaError_t e = cudaSuccess;                                              \
-        if (cudaError_t r = smem_attr(KERNEL<LOG_B, LOG_C>, SMEM, f, e)) return r;       \
-        return launch_k(KERNEL<LOG_B, LOG_C>, grid, Sh::T, SMEM, Sh::C, s, a);           \
+        if (cudaError_t r = smem_attr(KERNEL<LOG_B, LOG_C, LOG_E>, SMEM, f, e)) return r; \
+        return launch_k(KERNEL<LOG_B, LOG_C, LOG_E>, grid, Sh::T, SMEM, Sh::C, s, a);     \
     }
             HE_EVAL_CASE(EK_KS_DIGITS, k_ks_digits, sm1)
             HE_EVAL_CASE(EK_KS_MODUP, k_ks_modup, sm3)
@@ -180,9 +180,11 @@ struct DegreeImpl;
                        : decltype(ops)::template max_clusters<false>();                           \
         });                                                                                        \
     }                                                                                              \
-    static cudaError_t eval_##LOG_N_(EvalKernel k, const EvalArgs &a, u32 items, cudaStream_t s)   \
+    static cudaError_t eval_##LOG_N_(EvalKernel k, const EvalArgs &a, u32 items, int log_e,        \
+                                     cudaStream_t s)                                               \
     {                                                                                              \
         using D = DegreeImpl<LOG_N_>;                                                              \
+        if (log_e == 3) return ShapeOps<D::def_b, LOG_N_ - D::def_b, 3>::eval(k, a, items, s);     \
         return ShapeOps<D::def_b, LOG_N_ - D::def_b, 4>::eval(k, a, items, s);                     \
     }                                                                                              \
     static bool has_##LOG_N_(int log_b, int log_e)                                                 \

@@ -296,10 +296,11 @@ __device__ __forceinline__ DSource dsource(const EvalArgs &a, u32 c)
     return s;
 }
 
-template <int LOG_B, int LOG_C>
-__global__ void __launch_bounds__(NttShape<LOG_B, LOG_C>::T, 2) k_ks_digits(EvalArgs a)
+template <int LOG_B, int LOG_C, int LOG_E>
+__global__ void __launch_bounds__(NttShape<LOG_B, LOG_C, LOG_E>::T, NttShape<LOG_B, LOG_C, LOG_E>::EVAL_MIN_CTAS)
+k_ks_digits(EvalArgs a)
 {
-    using Sh = NttShape<LOG_B, LOG_C>;
+    using Sh = NttShape<LOG_B, LOG_C, LOG_E>;
     extern __shared__ __align__(16) u64 smem[];
     const u32 m = (LOG_C > 0) ? cluster_ctarank() : 0u;
     const u32 item = blockIdx.x >> LOG_C;
@@ -313,10 +314,11 @@ __global__ void __launch_bounds__(NttShape<LOG_B, LOG_C>::T, 2) k_ks_digits(Eval
     ntt_inv_block<Sh, false>(smem, m, 0, a.ctx.tw_inv + (size_t)j * Sh::N, pc, ld, st, x);
 }
 
-template <int LOG_B, int LOG_C>
-__global__ void __launch_bounds__(NttShape<LOG_B, LOG_C>::T, 2) k_ks_modup(EvalArgs a)
+template <int LOG_B, int LOG_C, int LOG_E>
+__global__ void __launch_bounds__(NttShape<LOG_B, LOG_C, LOG_E>::T, NttShape<LOG_B, LOG_C, LOG_E>::EVAL_MIN_CTAS)
+k_ks_modup(EvalArgs a)
 {
-    using Sh = NttShape<LOG_B, LOG_C>;
+    using Sh = NttShape<LOG_B, LOG_C, LOG_E>;
     extern __shared__ __align__(16) u64 smem[];
     u64 *acc = smem + Sh::B;                   // [2][E][T], own positions only
     const u32 tid = threadIdx.x;
@@ -361,7 +363,7 @@ __global__ void __launch_bounds__(NttShape<LOG_B, LOG_C>::T, 2) k_ks_modup(EvalA
         }
     } else {
         // special prime: y_k = INTT_P(acc_k), kept in the coefficient domain
-#pragma unroll
+#pragma unroll 1
         for (int k = 0; k < 2; k++) {
             ntt_barrier<Sh>();
 #pragma unroll
@@ -375,10 +377,11 @@ __global__ void __launch_bounds__(NttShape<LOG_B, LOG_C>::T, 2) k_ks_modup(EvalA
 }
 
 // Relin mod-down (no rescale): out[c][k][i] = d_k[i] + (acc - NTT(r)) P^-1.
-template <int LOG_B, int LOG_C>
-__global__ void __launch_bounds__(NttShape<LOG_B, LOG_C>::T, 2) k_ks_moddown(EvalArgs a)
+template <int LOG_B, int LOG_C, int LOG_E>
+__global__ void __launch_bounds__(NttShape<LOG_B, LOG_C, LOG_E>::T, NttShape<LOG_B, LOG_C, LOG_E>::EVAL_MIN_CTAS)
+k_ks_moddown(EvalArgs a)
 {
-    using Sh = NttShape<LOG_B, LOG_C>;
+    using Sh = NttShape<LOG_B, LOG_C, LOG_E>;
     extern __shared__ __align__(16) u64 smem[];
     const u32 tid = threadIdx.x;
     const u32 m = (LOG_C > 0) ? cluster_ctarank() : 0u;
@@ -406,10 +409,11 @@ __global__ void __launch_bounds__(NttShape<LOG_B, LOG_C>::T, 2) k_ks_moddown(Eva
 }
 
 // RS, first half: y_k = INTT_{q_l}(c_k[q_l]) -> lift2 (coefficient domain).
-template <int LOG_B, int LOG_C>
-__global__ void __launch_bounds__(NttShape<LOG_B, LOG_C>::T, 2) k_rs_lift(EvalArgs a)
+template <int LOG_B, int LOG_C, int LOG_E>
+__global__ void __launch_bounds__(NttShape<LOG_B, LOG_C, LOG_E>::T, NttShape<LOG_B, LOG_C, LOG_E>::EVAL_MIN_CTAS)
+k_rs_lift(EvalArgs a)
 {
-    using Sh = NttShape<LOG_B, LOG_C>;
+    using Sh = NttShape<LOG_B, LOG_C, LOG_E>;
     extern __shared__ __align__(16) u64 smem[];
     const u32 m = (LOG_C > 0) ? cluster_ctarank() : 0u;
     const u32 item = blockIdx.x >> LOG_C;
@@ -425,10 +429,11 @@ __global__ void __launch_bounds__(NttShape<LOG_B, LOG_C>::T, 2) k_rs_lift(EvalAr
 }
 
 // RS, second half: out[c][k][i] = (c_k[q_i] - NTT(r mod q_i)) q_l^-1, i < l.
-template <int LOG_B, int LOG_C>
-__global__ void __launch_bounds__(NttShape<LOG_B, LOG_C>::T, 2) k_rs(EvalArgs a)
+template <int LOG_B, int LOG_C, int LOG_E>
+__global__ void __launch_bounds__(NttShape<LOG_B, LOG_C, LOG_E>::T, NttShape<LOG_B, LOG_C, LOG_E>::EVAL_MIN_CTAS)
+k_rs(EvalArgs a)
 {
-    using Sh = NttShape<LOG_B, LOG_C>;
+    using Sh = NttShape<LOG_B, LOG_C, LOG_E>;
     extern __shared__ __align__(16) u64 smem[];
     const u32 tid = threadIdx.x;
     const u32 m = (LOG_C > 0) ? cluster_ctarank() : 0u;
@@ -454,10 +459,11 @@ __global__ void __launch_bounds__(NttShape<LOG_B, LOG_C>::T, 2) k_rs(EvalArgs a)
 
 // MulLinRS, limb q_l: relin output c_k[q_l] = d_k[l] + (acc - NTT(r)) P^-1,
 // then straight into INTT_{q_l} (values stay in registers) -> lift2.
-template <int LOG_B, int LOG_C>
-__global__ void __launch_bounds__(NttShape<LOG_B, LOG_C>::T, 2) k_mrr_last(EvalArgs a)
+template <int LOG_B, int LOG_C, int LOG_E>
+__global__ void __launch_bounds__(NttShape<LOG_B, LOG_C, LOG_E>::T, NttShape<LOG_B, LOG_C, LOG_E>::EVAL_MIN_CTAS)
+k_mrr_last(EvalArgs a)
 {
-    using Sh = NttShape<LOG_B, LOG_C>;
+    using Sh = NttShape<LOG_B, LOG_C, LOG_E>;
     extern __shared__ __align__(16) u64 smem[];
     const u32 tid = threadIdx.x;
     const u32 m = (LOG_C > 0) ? cluster_ctarank() : 0u;
@@ -488,10 +494,11 @@ __global__ void __launch_bounds__(NttShape<LOG_B, LOG_C>::T, 2) k_mrr_last(EvalA
 }
 
 // MulLinRS, limbs i < l: mod-down by P then rescale by q_l, two NTTs.
-template <int LOG_B, int LOG_C>
-__global__ void __launch_bounds__(NttShape<LOG_B, LOG_C>::T, 2) k_mrr_rest(EvalArgs a)
+template <int LOG_B, int LOG_C, int LOG_E>
+__global__ void __launch_bounds__(NttShape<LOG_B, LOG_C, LOG_E>::T, NttShape<LOG_B, LOG_C, LOG_E>::EVAL_MIN_CTAS)
+k_mrr_rest(EvalArgs a)
 {
-    using Sh = NttShape<LOG_B, LOG_C>;
+    using Sh = NttShape<LOG_B, LOG_C, LOG_E>;
     extern __shared__ __align__(16) u64 smem[];
     const u32 tid = threadIdx.x;
     const u32 m = (LOG_C > 0) ? cluster_ctarank() : 0u;

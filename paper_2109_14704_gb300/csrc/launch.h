@@ -100,8 +100,9 @@ struct DegreeOps {
                                   cudaStream_t s);
     // Largest number of co-resident clusters of the persistent kernel.
     int (*max_clusters)(int log_b, int log_e, bool inverse);
-    // Evaluation kernels over `items` clusters (default shape).
-    cudaError_t (*eval)(EvalKernel k, const EvalArgs &a, u32 items, cudaStream_t s);
+    // Evaluation kernels over `items` clusters (the default words per CTA;
+    // log_e = 3 or 4 words per thread, 0 = 4).
+    cudaError_t (*eval)(EvalKernel k, const EvalArgs &a, u32 items, int log_e, cudaStream_t s);
     // Is the shape built for this degree?
     bool (*has_shape)(int log_b, int log_e);
     // Shapes built for this degree: n pairs (log_b, log_e), default first.

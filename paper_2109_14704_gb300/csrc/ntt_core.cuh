@@ -108,6 +108,8 @@ struct NttShape {
     // radix-16 rounds and 64 for radix-8 (16 or 8 words in flight)
     static constexpr int REGS = LOG_E == 4 ? 128 : 64;
     static constexpr int MIN_CTAS = (65536 / (int)(T * REGS)) > 0 ? 65536 / (int)(T * REGS) : 1;
+    // evaluation kernels carry more state per thread: 128 registers
+    static constexpr int EVAL_MIN_CTAS = (65536 / (int)(T * 128)) > 0 ? 65536 / (int)(T * 128) : 1;
     static_assert(LOG_C <= 3, "portable clusters hold at most 8 CTAs");
     static_assert(LOG_C <= LOG_E, "a thread holds whole columns of the cross stages");
     static_assert(LOG_E == 3 || LOG_E == 4, "radix 8 or 16 rounds");

@@ -59,6 +59,7 @@ _SIGS = {
     "he_context_create": (ctypes.c_int32, [ctypes.c_uint32, ctypes.c_uint32, _u64p, ctypes.c_uint64,
                                            ctypes.POINTER(_vp)]),
     "he_context_destroy": (ctypes.c_int32, [_vp]),
+    "he_context_set_eval_shape": (ctypes.c_int32, [_vp, ctypes.c_uint32]),
     "he_relin_key_upload": (ctypes.c_int32, [_vp, _u64p, ctypes.POINTER(_vp)]),
     "he_relin_key_destroy": (ctypes.c_int32, [_vp]),
     "he_ct_mul": (ctypes.c_int32, [_vp, _vp, _vp, _vp, ctypes.c_uint32, _vp]),
@@ -263,6 +264,11 @@ class Context:
     @property
     def n_data(self) -> int:
         return len(self.data_moduli)
+
+    def set_eval_shape(self, log_thread_words: int):
+        """Words per thread (2^3 or 2^4; 0 = default) of the context's
+        key-switching and rescale kernels."""
+        _check(load().he_context_set_eval_shape(self.handle, log_thread_words))
 
     def relin_scratch_bytes(self, level: int) -> int:
         return int(load().he_relin_scratch_bytes(self.handle, level))

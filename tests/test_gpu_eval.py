@@ -44,10 +44,12 @@ def test_ct_mul(name, level):
     assert np.array_equal(host(out), oracle.tensor(ca, cb, qs))
 
 
+@pytest.mark.parametrize("log_e", [4, 3])
 @pytest.mark.parametrize("name,level", [("ckks16k", 6), ("ckks16k", 2), ("matrix8k", 2), ("small4k", 0),
                                         ("small4k", 3)])
-def test_relin(name, level):
+def test_relin(name, level, log_e):
     N, data, P, ctx, evk, key, r = _setup(name, 20 + level)
+    ctx.set_eval_shape(log_e)
     qs = data[:level + 1]
     c3 = np.stack([r.uniform_limbs(qs, N) for _ in range(3)])
     out = empty(2, level + 1, N)
@@ -56,9 +58,11 @@ def test_relin(name, level):
     assert np.array_equal(host(out), oracle.relin(c3, evk, data, P, level))
 
 
+@pytest.mark.parametrize("log_e", [4, 3])
 @pytest.mark.parametrize("name,level", [("ckks16k", 6), ("ckks16k", 1), ("matrix8k", 2), ("small4k", 3)])
-def test_rescale(name, level):
+def test_rescale(name, level, log_e):
     N, data, P, ctx, evk, key, r = _setup(name, 30 + level)
+    ctx.set_eval_shape(log_e)
     qs = data[:level + 1]
     c = np.stack([r.uniform_limbs(qs, N) for _ in range(2)])
     out = empty(2, level, N)
@@ -67,10 +71,12 @@ def test_rescale(name, level):
     assert np.array_equal(host(out), oracle.rescale(c, data, level))
 
 
+@pytest.mark.parametrize("log_e", [4, 3])
 @pytest.mark.parametrize("name,level,count", [("ckks16k", 6, 3), ("ckks16k", 2, 2), ("matrix8k", 2, 5),
                                               ("small4k", 1, 4), ("small4k", 3, 1)])
-def test_mul_relin_rescale_batch(name, level, count):
+def test_mul_relin_rescale_batch(name, level, count, log_e):
     N, data, P, ctx, evk, key, r = _setup(name, 40 + level + count)
+    ctx.set_eval_shape(log_e)
     qs = data[:level + 1]
     ca = np.stack([np.stack([r.uniform_limbs(qs, N) for _ in range(2)]) for _ in range(count)])
     cb = np.stack([np.stack([r.uniform_limbs(qs, N) for _ in range(2)]) for _ in range(count)])

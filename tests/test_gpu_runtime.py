@@ -52,6 +52,24 @@ def test_autotune_plan():
         assert np.array_equal(host(d), x)                         # every candidate round-tripped
 
 
+def test_autotune_mul_relin_rescale():
+    N = 4096
+    data, P = he.chain_primes(N, [60, 50, 50, 50], 60)
+    ctx = he.Context(N, data, P)
+    r = Rng(21)
+    evk = np.stack([np.stack([r.uniform_limbs(data + [P], N) for _ in range(2)]) for _ in range(len(data))])
+    key = he.RelinKey(ctx, evk)
+    res = autotune.tune_mul_relin_rescale(ctx, key, 3, 4, reps=2, warmup=1)
+    assert res["log_thread_words"] in (3, 4) and all(c["ok"] for c in res["candidates"])
+    # the chosen radix still matches the oracle
+    ca = np.stack([r.uniform_limbs(data, N) for _ in range(2)])
+    cb = np.stack([r.uniform_limbs(data, N) for _ in range(2)])
+    out = torch.empty((1, 2, 3, N), dtype=torch.int64, device="cuda")
+    he.mul_relin_rescale(out, dev(ca[None]), dev(cb[None]), 1, key, ctx, 3,
+                         torch.empty(ctx.mrr_scratch_bytes(3, 1) // 8, dtype=torch.int64, device="cuda"))
+    assert np.array_equal(host(out)[0], oracle.mul_relin_rescale(ca, cb, evk, data, P, 3))
+
+
 def _small_server(**kw):
     args = dict(degrees=(4096, 8192), min_level=2, max_level=4, slots=4, streams=2, max_wait_s=0.001,
                 pool_per_bucket=2, seed=11)
