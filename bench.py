@@ -56,7 +56,8 @@ def _args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle sample")
     ap.add_argument("--profile-case", choices=["ntt", "mrr", "probe"],
                     help="run one small case of a kernel family and exit (for profilers)")
-    ap.add_argument("--instances", type=int, default=64, help="NTT instances of --profile-case ntt")
+    ap.add_argument("--instances", type=int, default=64,
+                    help="NTT instances of --profile-case ntt, ciphertext pairs of --profile-case mrr")
     ap.add_argument("--shape", default="", help="log_block,log_thread_words for --profile-case ntt")
     ap.add_argument("--skip", default="", help="comma list of sub-benchmarks to skip: uneven,matrix,serving")
     ap.add_argument("--serve-requests", type=int, default=4000)
@@ -617,8 +618,8 @@ def run_reference(args, rank, world):
 def profile_case(args):
     """A small case of one kernel family: `ntt` transforms args.instances x 8
     limbs at N = 2^15 (64 instances = 128 MiB, above the L2 size) forward
-    then inverse, `mrr` runs one MulLinRS batch of 8 pairs on the CKKS
-    workload, `probe` the butterfly probe. Each runs `--steps` times."""
+    then inverse, `mrr` runs one MulLinRS batch of args.instances pairs on
+    the CKKS workload, `probe` the butterfly probe. Each runs `--steps` times."""
     import numpy as np
     import torch
 
@@ -642,7 +643,7 @@ def profile_case(args):
     elif args.profile_case == "mrr":
         data, P = he.chain_primes(MRR_N, MRR_BITS, 60)
         ctx = he.Context(MRR_N, data, P)
-        L, count = len(data) - 1, 8
+        L, count = len(data) - 1, args.instances
         rm = Rng(2)
         evk = np.stack([np.stack([rm.uniform_limbs(data + [P], MRR_N) for _ in range(2)]) for _ in range(len(data))])
         key = he.RelinKey(ctx, evk)

@@ -183,7 +183,6 @@ static he::PrimeConst prime_const(u64 q, u32 N, u64 w1)
     c.four_p = 4 * q;
     c.neg_p = 0 - q;
     c.h4 = (u32)((4 * (u128)q + 0xffffffffull) >> 32);
-    c.r32 = q > (1ull << 32) ? (u32)(((u128)1 << 64) / q) : 0u;
     c.bits = (u32)bit_length(q);
     c.mu = (u64)(((u128)1 << (2 * c.bits + 2)) / q);
     c.ninv = h_inv(N % q, q);
