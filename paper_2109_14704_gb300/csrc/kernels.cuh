@@ -271,6 +271,9 @@ __device__ __forceinline__ u64 centred_mod(u64 y, u64 half_m, u64 m_mod_q, const
     return y > half_m ? sub_mod(r, m_mod_q, pc.p) : r;
 }
 
+// Read-only load (the kernel never writes what it reads through this).
+__device__ __forceinline__ u64 rd(const u64 *p) { return __ldg(reinterpret_cast<const unsigned long long *>(p)); }
+
 // d_k[i] at position P for component k (0 or 1): from the tensor of the two
 // input ciphertexts (fused Mul) or from a 3-component input.
 struct DSource {
@@ -279,10 +282,10 @@ struct DSource {
     __device__ __forceinline__ u64 d(int k, u32 limb, u32 log_n, u32 P, const PrimeConst &pc) const
     {
         const size_t off = ((size_t)limb << log_n) + P;
-        if (ct3) return ct3[k * per + off];
-        if (k == 0) return mul_mod(ct_a[off], ct_b[off], pc);
-        if (k == 1) return mad2_mod(ct_a[off], ct_b[per + off], ct_a[per + off], ct_b[off], pc);
-        return mul_mod(ct_a[per + off], ct_b[per + off], pc);
+        if (ct3) return rd(ct3 + k * per + off);
+        if (k == 0) return mul_mod(rd(ct_a + off), rd(ct_b + off), pc);
+        if (k == 1) return mad2_mod(rd(ct_a + off), rd(ct_b + per + off), rd(ct_a + per + off), rd(ct_b + off), pc);
+        return mul_mod(rd(ct_a + per + off), rd(ct_b + per + off), pc);
     }
 };
 
@@ -338,19 +341,31 @@ k_ks_modup(EvalArgs a)
         } else {
             if (j > 0) ntt_barrier<Sh>();
             const u64 *src = a.c2 + ((size_t)c * n + j) * Sh::N;
-            auto ld = [&](u32 P) -> u64 { return barrett_reduce(0, src[P], pc.p, pc.mu, pc.bits); };
             auto st = [&](u32, u64) {};
-            ntt_fwd_block<Sh>(smem, m, 0, twf, pc, ld, st, x);
+            // The transform takes any input below 8t + 2^32 congruent to the
+            // digit: when q_j <= 8t the digit c2_j < q_j goes in as it is.
+            if (a.ctx.pc[j].p <= (pc.four_p << 1)) {
+                auto ld = [&](u32 P) -> u64 { return __ldg(reinterpret_cast<const unsigned long long *>(src + P)); };
+                ntt_fwd_block<Sh>(smem, m, 0, twf, pc, ld, st, x);
+            } else {
+                auto ld = [&](u32 P) -> u64 {
+                    return barrett_reduce(0, __ldg(reinterpret_cast<const unsigned long long *>(src + P)), pc.p,
+                                          pc.mu, pc.bits);
+                };
+                ntt_fwd_block<Sh>(smem, m, 0, twf, pc, ld, st, x);
+            }
         }
+        // multiply-accumulate with the key: lazy products in [0, 4p),
+        // accumulators kept in [0, 4p)
 #pragma unroll
         for (int k = 0; k < 2; k++) {
             const ulonglong2 *key = a.evk + (((size_t)j * 2 + k) * (a.ctx.n_data + 1) + tp) * Sh::N;
 #pragma unroll
             for (int e = 0; e < Sh::E; e++) {
                 const ulonglong2 w = __ldg(key + last_pos<Sh>(m, tid, e));
-                const u64 prod = mul_shoup(x[e], w.x, w.y, pc.p);
+                const u64 prod = mul_shoup_lazy4_asm(x[e], w.x, w.y, pc.neg_p);
                 u64 &slot = acc[(k * Sh::E + e) * Sh::T + tid];
-                slot = (j == 0) ? prod : add_mod(slot, prod, pc.p);
+                slot = (j == 0) ? prod : reduce_once(slot + prod, pc.four_p);
             }
         }
     }
@@ -359,10 +374,13 @@ k_ks_modup(EvalArgs a)
         for (int k = 0; k < 2; k++) {
             u64 *dst = a.accq + (((size_t)c * 2 + k) * n + t) * Sh::N;
 #pragma unroll
-            for (int e = 0; e < Sh::E; e++) dst[last_pos<Sh>(m, tid, e)] = acc[(k * Sh::E + e) * Sh::T + tid];
+            for (int e = 0; e < Sh::E; e++)
+                dst[last_pos<Sh>(m, tid, e)] =
+                    reduce_once(reduce_once(acc[(k * Sh::E + e) * Sh::T + tid], pc.two_p), pc.p);
         }
     } else {
-        // special prime: y_k = INTT_P(acc_k), kept in the coefficient domain
+        // special prime: y_k = INTT_P(acc_k) (inputs in [0, 4p)), kept in the
+        // coefficient domain
 #pragma unroll 1
         for (int k = 0; k < 2; k++) {
             ntt_barrier<Sh>();
@@ -395,7 +413,7 @@ k_ks_moddown(EvalArgs a)
     const DSource ds = dsource(a, c);
     const u64 *y = a.plift + ((size_t)c * 2 + k) * Sh::N;
     u64 x[Sh::E];
-    auto ld = [&](u32 P) -> u64 { return centred_mod(y[P], half_P, cst[2], pc); };
+    auto ld = [&](u32 P) -> u64 { return centred_mod(rd(y + P), half_P, cst[2], pc); };
     auto st = [&](u32, u64) {};
     ntt_fwd_block<Sh>(smem, m, 0, a.ctx.tw_fwd + (size_t)i * Sh::N, pc, ld, st, x);
     const u64 *accp = a.accq + (((size_t)c * 2 + k) * n + i) * Sh::N;
@@ -403,7 +421,7 @@ k_ks_moddown(EvalArgs a)
 #pragma unroll
     for (int e = 0; e < Sh::E; e++) {
         const u32 P = last_pos<Sh>(m, tid, e);
-        const u64 v = mul_shoup(sub_mod(accp[P], x[e], pc.p), cst[0], cst[1], pc.p);
+        const u64 v = mul_shoup(sub_mod(rd(accp + P), x[e], pc.p), cst[0], cst[1], pc.p);
         out[P] = add_mod(ds.d(k, i, Sh::LOG_N, P, pc), v, pc.p);
     }
 }
@@ -423,7 +441,7 @@ k_rs_lift(EvalArgs a)
     const u64 *src = a.ct2 + (((size_t)c * 2 + k) * n + l) * Sh::N;
     u64 *dst = a.lift2 + ((size_t)c * 2 + k) * Sh::N;
     u64 x[Sh::E];
-    auto ld = [&](u32 P) -> u64 { return src[P]; };
+    auto ld = [&](u32 P) -> u64 { return rd(src + P); };
     auto st = [&](u32 P, u64 v) { dst[P] = v; };
     ntt_inv_block<Sh, false>(smem, m, 0, a.ctx.tw_inv + (size_t)l * Sh::N, pc, ld, st, x);
 }
@@ -445,7 +463,7 @@ k_rs(EvalArgs a)
     const u64 half_l = (a.ctx.pc[l].p - 1) / 2;
     const u64 *y = a.lift2 + ((size_t)c * 2 + k) * Sh::N;
     u64 x[Sh::E];
-    auto ld = [&](u32 P) -> u64 { return centred_mod(y[P], half_l, cst[2], pc); };
+    auto ld = [&](u32 P) -> u64 { return centred_mod(rd(y + P), half_l, cst[2], pc); };
     auto st = [&](u32, u64) {};
     ntt_fwd_block<Sh>(smem, m, 0, a.ctx.tw_fwd + (size_t)i * Sh::N, pc, ld, st, x);
     const u64 *src = a.ct2 + (((size_t)c * 2 + k) * n + i) * Sh::N;
@@ -453,7 +471,7 @@ k_rs(EvalArgs a)
 #pragma unroll
     for (int e = 0; e < Sh::E; e++) {
         const u32 P = last_pos<Sh>(m, tid, e);
-        out[P] = mul_shoup(sub_mod(src[P], x[e], pc.p), cst[0], cst[1], pc.p);
+        out[P] = mul_shoup(sub_mod(rd(src + P), x[e], pc.p), cst[0], cst[1], pc.p);
     }
 }
 
@@ -477,14 +495,14 @@ k_mrr_last(EvalArgs a)
     const DSource ds = dsource(a, c);
     const u64 *y = a.plift + ((size_t)c * 2 + k) * Sh::N;
     u64 x[Sh::E];
-    auto ld = [&](u32 P) -> u64 { return centred_mod(y[P], half_P, cst[2], pc); };
+    auto ld = [&](u32 P) -> u64 { return centred_mod(rd(y + P), half_P, cst[2], pc); };
     auto nost = [&](u32, u64) {};
     ntt_fwd_block<Sh>(smem, m, 0, a.ctx.tw_fwd + (size_t)l * Sh::N, pc, ld, nost, x);
     const u64 *accp = a.accq + (((size_t)c * 2 + k) * n + l) * Sh::N;
 #pragma unroll
     for (int e = 0; e < Sh::E; e++) {
         const u32 P = last_pos<Sh>(m, tid, e);
-        const u64 v = mul_shoup(sub_mod(accp[P], x[e], pc.p), cst[0], cst[1], pc.p);
+        const u64 v = mul_shoup(sub_mod(rd(accp + P), x[e], pc.p), cst[0], cst[1], pc.p);
         x[e] = add_mod(ds.d(k, l, Sh::LOG_N, P, pc), v, pc.p);
     }
     u64 *dst = a.lift2 + ((size_t)c * 2 + k) * Sh::N;
@@ -516,18 +534,18 @@ k_mrr_rest(EvalArgs a)
     const u64 *y = a.plift + ((size_t)c * 2 + k) * Sh::N;
     u64 x[Sh::E], z[Sh::E];
     auto nost = [&](u32, u64) {};
-    auto ld1 = [&](u32 P) -> u64 { return centred_mod(y[P], half_P, cP[2], pc); };
+    auto ld1 = [&](u32 P) -> u64 { return centred_mod(rd(y + P), half_P, cP[2], pc); };
     ntt_fwd_block<Sh>(smem, m, 0, twf, pc, ld1, nost, x);
     const u64 *accp = a.accq + (((size_t)c * 2 + k) * n + i) * Sh::N;
 #pragma unroll
     for (int e = 0; e < Sh::E; e++) {
         const u32 P = last_pos<Sh>(m, tid, e);
-        const u64 v = mul_shoup(sub_mod(accp[P], x[e], pc.p), cP[0], cP[1], pc.p);
+        const u64 v = mul_shoup(sub_mod(rd(accp + P), x[e], pc.p), cP[0], cP[1], pc.p);
         z[e] = add_mod(ds.d(k, i, Sh::LOG_N, P, pc), v, pc.p);
     }
     ntt_barrier<Sh>();
     const u64 *y2 = a.lift2 + ((size_t)c * 2 + k) * Sh::N;
-    auto ld2 = [&](u32 P) -> u64 { return centred_mod(y2[P], half_l, cl[2], pc); };
+    auto ld2 = [&](u32 P) -> u64 { return centred_mod(rd(y2 + P), half_l, cl[2], pc); };
     ntt_fwd_block<Sh>(smem, m, 0, twf, pc, ld2, nost, x);
     u64 *out = a.out + (((size_t)c * 2 + k) * l + i) * Sh::N;
 #pragma unroll
