@@ -359,9 +359,10 @@ def run_ours(args, rank, world, local):
             "inv_limbs_per_s": world * limbs_total / (inv / 1e3),
             "fwd_ms": fwd, "inv_ms": inv, "speedup_vs_naive": ms_naive / ms,
         },
-        "autotune": {"shape": {"log_block": tune["shape"][0], "log_thread_words": tune["shape"][1],
-                               "persistent": tune["shape"][2]},
-                     "candidates": [{"shape": c["shape"], "ms_fwd_inv": c.get("ms_fwd_inv")} for c in tune["candidates"]]},
+        "autotune": {"forward": dict(zip(("log_block", "log_thread_words", "persistent"), tune["fwd"])),
+                     "inverse": dict(zip(("log_block", "log_thread_words", "persistent"), tune["inv"])),
+                     "candidates": [{"shape": c["shape"], "ms_fwd": c.get("ms_fwd"), "ms_inv": c.get("ms_inv")}
+                                    for c in tune["candidates"]]},
         "uneven_batch": uneven,
         "matrix_mul_relin_rescale": matrix,
         "serving": serve,
@@ -374,7 +375,8 @@ def run_ours(args, rank, world, local):
             "autotune": mrr_tune,
         },
         "roofline": {
-            "kernel": "k_ntt forward, 2^12 words per CTA x cluster of 8",
+            "kernel": "k_ntt forward, 2^%d words per CTA x cluster of %d, 2^%d words per thread" % (
+                tune["fwd"][0], N >> tune["fwd"][0], tune["fwd"][1]),
             "bound": "alu" if bound_alu else "hbm",
             "achieved": achieved_bfly / 1e12 if bound_alu else achieved_gbs,
             "peak": bfly_rate / 1e12 if bound_alu else hbm_peak,
@@ -634,7 +636,7 @@ def profile_case(args):
         qs = _ntt_moduli()
         tables = he.NttTables(N, qs)
         if args.shape:
-            he.ntt_set_shape(N, *([int(v) for v in args.shape.split(",")] + [0, 0, 0])[:3])
+            he.ntt_set_shape(N, *([int(v) for v in args.shape.split(",")] + [0, 0, 0])[:3], direction=he.BOTH)
         r = Rng(1)
         d = torch.from_numpy(np.stack([r.uniform_limbs(qs, N) for _ in range(args.instances)]).view(np.int64)).to(dev)
         for _ in range(args.steps):

@@ -131,12 +131,13 @@ he_status he_ntt_inv_naive(uint64_t *poly, uint32_t N, uint32_t limbs, uint32_t 
  * register rounds (the paper's radix and SLM-stage choices, Sec. III-B). */
 he_status he_ntt_shapes(uint32_t N, uint32_t *pairs_out, uint32_t cap, uint32_t *n_out);
 
-/* Shape used from now on by he_ntt_fwd / he_ntt_inv at degree N (process
- * wide; 0, 0, 0 restores the built-in default). persistent != 0 launches a
- * fixed grid of as many clusters as fit on the GPU, each walking over the
- * limbs, instead of one cluster per limb. The autotuner's choice is applied
- * here. Returns HE_EUNSUPPORTED for a shape that is not built. */
-he_status he_ntt_set_shape(uint32_t N, uint32_t log_block, uint32_t log_thread_words,
+/* Shape used from now on by he_ntt_fwd (direction 1), he_ntt_inv (2) or
+ * both (0) at degree N (process wide; 0, 0, 0 restores the built-in
+ * default). persistent != 0 launches a fixed grid of as many clusters as fit
+ * on the GPU, each walking over the limbs, instead of one cluster per limb.
+ * The autotuner's choices are applied here. Returns HE_EUNSUPPORTED for a
+ * shape that is not built. */
+he_status he_ntt_set_shape(uint32_t N, uint32_t direction, uint32_t log_block, uint32_t log_thread_words,
                            uint32_t persistent);
 
 /* Dyadic product out[l][i] = a[l][i] * b[l][i] mod q_l for `count`

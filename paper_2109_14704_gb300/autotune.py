@@ -6,7 +6,8 @@ stages run across the CTAs of a cluster versus inside one CTA's shared
 memory, and words per thread, i.e. radix-8 or radix-16 register rounds --
 the paper tuned the same knobs by hand: radix, SLM threshold and register
 slots, Sec. III-B, Sec. V-A), each launched either as one cluster per limb
-or as a persistent grid walking the limbs. Each candidate is first checked once: its
+or as a persistent grid walking the limbs, and keeps the fastest for each
+direction. Each candidate is first checked once: its
 forward output must equal the default shape's output bit for bit and its
 inverse must restore the input exactly. Candidates are timed with CUDA
 events (forward + inverse, median of `reps` after warm-up); the fastest wins,
@@ -78,16 +79,17 @@ def default_moduli(N: int, limbs: int) -> list[int]:
 
 def tune_uniform(N: int, limbs: int, count: int, moduli=None, reps: int = 10, warmup: int = 3,
                  cache_path: str | None = DEFAULT_CACHE, apply: bool = True, force: bool = False) -> dict:
-    """Pick the fastest built shape for he_ntt_fwd / he_ntt_inv on `count`
-    polynomials of `limbs` limbs at degree N."""
+    """Pick, separately for he_ntt_fwd and he_ntt_inv, the fastest built
+    shape (words per CTA, words per thread, one cluster per limb or
+    persistent) on `count` polynomials of `limbs` limbs at degree N."""
     import torch
 
-    key = f"{_device_key()}|uniform|N={N}|limbs={limbs}|count={count}"
+    key = f"{_device_key()}|uniform2|N={N}|limbs={limbs}|count={count}"
     cache = _load_cache(cache_path) if cache_path else {}
     if not force and key in cache:
         res = cache[key]
         if apply:
-            he.ntt_set_shape(N, *res["shape"])
+            _apply(N, res)
         return res
 
     qs = list(moduli) if moduli is not None else default_moduli(N, limbs)
@@ -117,28 +119,31 @@ def tune_uniform(N: int, limbs: int, count: int, moduli=None, reps: int = 10, wa
             if not (ok_fwd and ok_inv):
                 cands.append({"index": idx, "shape": [lb, le, pers], "ok": False})
                 continue
-
-            def step():
-                he.ntt_fwd(d, N, limbs, count, tables)
-                he.ntt_inv(d, N, limbs, count, tables)
-
-            ms = _time(step, reps, warmup)
-            cands.append({"index": idx, "shape": [lb, le, pers], "ok": True, "ms_fwd_inv": ms})
+            ms_f = _time(lambda: he.ntt_fwd(d, N, limbs, count, tables), reps, warmup)
+            ms_i = _time(lambda: he.ntt_inv(d, N, limbs, count, tables), reps, warmup)
+            cands.append({"index": idx, "shape": [lb, le, pers], "ok": True, "ms_fwd": ms_f, "ms_inv": ms_i})
     finally:
         he.ntt_set_shape(N, 0, 0, 0)
     good = [c for c in cands if c["ok"]]
     if not good:
         raise RuntimeError(f"no transform shape for N = {N} passed its check")
-    best = min(good, key=lambda c: (c["ms_fwd_inv"], c["index"]))
-    res = {"shape": best["shape"], "ms_fwd_inv": best["ms_fwd_inv"], "candidates": cands,
-           "default_ms_fwd_inv": next(c["ms_fwd_inv"] for c in good if c["index"] == 0) if cands[0]["ok"] else None}
+    bf = min(good, key=lambda c: (c["ms_fwd"], c["index"]))
+    bi = min(good, key=lambda c: (c["ms_inv"], c["index"]))
+    d0 = next((c for c in good if c["index"] == 0), None)
+    res = {"fwd": bf["shape"], "inv": bi["shape"], "ms_fwd": bf["ms_fwd"], "ms_inv": bi["ms_inv"],
+           "default_ms_fwd_inv": (d0["ms_fwd"] + d0["ms_inv"]) if d0 else None, "candidates": cands}
     if cache_path:
         cache = _load_cache(cache_path)
         cache[key] = res
         _save_cache(cache_path, cache)
     if apply:
-        he.ntt_set_shape(N, *res["shape"])
+        _apply(N, res)
     return res
+
+
+def _apply(N, res):
+    he.ntt_set_shape(N, *res["fwd"], direction=he.FORWARD)
+    he.ntt_set_shape(N, *res["inv"], direction=he.INVERSE)
 
 
 def tune_plan(polys, reps: int = 10, warmup: int = 3, shapes_per_degree: dict | None = None) -> dict:

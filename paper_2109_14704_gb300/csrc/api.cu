@@ -341,7 +341,7 @@ static he::NttLaunch uniform_launch(uint64_t *poly, uint32_t limbs, uint32_t cou
 // Shape used by he_ntt_fwd / he_ntt_inv per degree (0, 0 = built-in default;
 // persistent: a fixed grid walking the limbs instead of one cluster per
 // limb), set by he_ntt_set_shape (e.g. from the autotuner).
-static std::atomic<int> g_shape_b[17], g_shape_e[17], g_shape_persistent[17];
+static std::atomic<int> g_shape_b[2][17], g_shape_e[2][17], g_shape_persistent[2][17];   // [inverse][log N]
 
 extern "C" he_status he_ntt_shapes(uint32_t N, uint32_t *pairs_out, uint32_t cap, uint32_t *n_out)
 {
@@ -358,19 +358,23 @@ extern "C" he_status he_ntt_shapes(uint32_t N, uint32_t *pairs_out, uint32_t cap
     return HE_OK;
 }
 
-extern "C" he_status he_ntt_set_shape(uint32_t N, uint32_t log_block, uint32_t log_thread_words,
-                                      uint32_t persistent)
+extern "C" he_status he_ntt_set_shape(uint32_t N, uint32_t direction, uint32_t log_block,
+                                      uint32_t log_thread_words, uint32_t persistent)
 {
     int log_n;
     if (he_status s = check_degree(N, &log_n)) return s;
+    if (direction > 2) return fail(HE_EINVAL, "direction must be 0 (both), 1 (forward) or 2 (inverse)");
     if (log_block || log_thread_words) {
         if (!he::degree_ops(log_n)->has_shape((int)log_block, (int)log_thread_words))
             return fail(HE_EUNSUPPORTED, "no kernel with 2^%u words per CTA and 2^%u per thread for N = %u",
                         log_block, log_thread_words, N);
     }
-    g_shape_b[log_n].store((int)log_block);
-    g_shape_e[log_n].store((int)log_thread_words);
-    g_shape_persistent[log_n].store(persistent ? 1 : 0);
+    for (int inv = 0; inv < 2; inv++) {
+        if ((direction == 1 && inv) || (direction == 2 && !inv)) continue;
+        g_shape_b[inv][log_n].store((int)log_block);
+        g_shape_e[inv][log_n].store((int)log_thread_words);
+        g_shape_persistent[inv][log_n].store(persistent ? 1 : 0);
+    }
     return HE_OK;
 }
 
@@ -382,9 +386,9 @@ static he_status ntt_common(uint64_t *poly, uint32_t N, uint32_t limbs, uint32_t
     if ((u64)limbs * count == 0) return HE_OK;
     if ((u64)limbs * count * (N / 4096 + 1) > 0x7fffffffull) return fail(HE_EINVAL, "batch too large");
     const he::DegreeOps *ops = he::degree_ops(log_n);
-    const int lb = g_shape_b[log_n].load(), le = g_shape_e[log_n].load();
+    const int lb = g_shape_b[inv][log_n].load(), le = g_shape_e[inv][log_n].load();
     const he::NttLaunch a = uniform_launch(poly, limbs, count, tw);
-    if (g_shape_persistent[log_n].load()) {
+    if (g_shape_persistent[inv][log_n].load()) {
         const u32 clusters = std::min<u32>(a.items, (u32)std::max(ops->max_clusters(lb, le, inv), 1));
         HE_CUDA(ops->ntt_persistent(a, lb, le, inv, clusters, (cudaStream_t)stream));
     } else {

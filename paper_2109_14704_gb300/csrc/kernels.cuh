@@ -123,7 +123,7 @@ __device__ __forceinline__ void mixed_unit(u64 *smem, u32 rank, const MixedUnit 
 }
 
 template <bool INV>
-__global__ void __launch_bounds__(256, 2) k_ntt_mixed(const MixedUnit *units, u32 n_units, const LimbJob *jobs)
+__global__ void __launch_bounds__(256, 4) k_ntt_mixed(const MixedUnit *units, u32 n_units, const LimbJob *jobs)
 {
     extern __shared__ __align__(16) u64 smem[];
     const u32 rank = cluster_ctarank();

@@ -104,9 +104,12 @@ struct NttShape {
     static constexpr int NROUND = (LOG_B + LOG_E - 1) / LOG_E;
     static constexpr int LAST_R = LOG_B - LOG_E * (NROUND - 1);
     static constexpr u32 SMEM_BYTES = B * 8;
-    // CTAs per SM to aim for: a register budget of 128 per thread for
-    // radix-16 rounds and 64 for radix-8 (16 or 8 words in flight)
-    static constexpr int REGS = LOG_E == 4 ? 128 : 64;
+    // CTAs per SM to aim for, from a register budget per thread: occupancy
+    // pays for the transform (measured: radix-8 at 42 registers, three 512-
+    // thread CTAs per SM, beats 64 registers by 8-9%; radix-16 at 64
+    // registers, four 256-thread CTAs, beats 128 by 7-18%), even with the
+    // few spills these budgets cost
+    static constexpr int REGS = LOG_E == 4 ? 64 : 42;
     static constexpr int MIN_CTAS = (65536 / (int)(T * REGS)) > 0 ? 65536 / (int)(T * REGS) : 1;
     // evaluation kernels carry more state per thread: 128 registers
     static constexpr int EVAL_MIN_CTAS = (65536 / (int)(T * 128)) > 0 ? 65536 / (int)(T * 128) : 1;

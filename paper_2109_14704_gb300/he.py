@@ -78,7 +78,8 @@ _SIGS = {
     "he_plan_launches": (ctypes.c_uint32, [_vp]),
     "he_ntt_shapes": (ctypes.c_int32, [ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32), ctypes.c_uint32,
                                        ctypes.POINTER(ctypes.c_uint32)]),
-    "he_ntt_set_shape": (ctypes.c_int32, [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32]),
+    "he_ntt_set_shape": (ctypes.c_int32, [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                          ctypes.c_uint32]),
     "he_butterfly_probe": (ctypes.c_int32, [_vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, _vp]),
     "he_butterfly_apply": (ctypes.c_int32, [_vp, _vp, _vp, _vp, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32, _vp]),
     "he_mul_relin_rescale_noalloc": (ctypes.c_int32, [_vp, _vp, _vp, ctypes.c_uint32, _vp, _vp, ctypes.c_uint32,
@@ -213,9 +214,14 @@ def ntt_shapes(N: int) -> list[tuple[int, int]]:
     return [(buf[2 * i], buf[2 * i + 1]) for i in range(min(n.value, 16))]
 
 
-def ntt_set_shape(N: int, log_block: int = 0, log_thread_words: int = 0, persistent: int = 0):
-    """Shape used by ntt_fwd / ntt_inv at degree N (0, 0, 0 = default)."""
-    _check(load().he_ntt_set_shape(N, log_block, log_thread_words, int(persistent)))
+FORWARD, INVERSE, BOTH = 1, 2, 0
+
+
+def ntt_set_shape(N: int, log_block: int = 0, log_thread_words: int = 0, persistent: int = 0,
+                  direction: int = BOTH):
+    """Shape used by ntt_fwd (direction 1) / ntt_inv (2) / both (0) at
+    degree N (0, 0, 0 = default)."""
+    _check(load().he_ntt_set_shape(N, direction, log_block, log_thread_words, int(persistent)))
 
 
 def _moduli_arg(tables: NttTables, limbs: int, moduli):

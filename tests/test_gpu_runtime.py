@@ -20,11 +20,13 @@ def test_autotune_uniform(tmp_path):
     cache = str(tmp_path / "tune.json")
     res = autotune.tune_uniform(N, limbs, count, reps=3, warmup=1, cache_path=cache)
     shapes = he.ntt_shapes(N)
-    assert tuple(res["shape"][:2]) in shapes and res["shape"][2] in (0, 1)
+    for d in ("fwd", "inv"):
+        assert tuple(res[d][:2]) in shapes and res[d][2] in (0, 1)
     assert all(c["ok"] for c in res["candidates"]) and len(res["candidates"]) == 2 * len(shapes)
-    assert res["ms_fwd_inv"] == min(c["ms_fwd_inv"] for c in res["candidates"])
+    assert res["ms_fwd"] == min(c["ms_fwd"] for c in res["candidates"])
+    assert res["ms_inv"] == min(c["ms_inv"] for c in res["candidates"])
     again = autotune.tune_uniform(N, limbs, count, cache_path=cache)   # from the cache
-    assert again["shape"] == res["shape"]
+    assert again["fwd"] == res["fwd"] and again["inv"] == res["inv"]
     # the applied shape still computes the oracle's transform
     qs = autotune.default_moduli(N, limbs)
     tables = he.NttTables(N, qs)
@@ -32,6 +34,8 @@ def test_autotune_uniform(tmp_path):
     d = dev(x)
     he.ntt_fwd(d, N, limbs, 1, tables)
     assert np.array_equal(host(d), oracle.ntt_fwd(x, qs))
+    he.ntt_inv(d, N, limbs, 1, tables)
+    assert np.array_equal(host(d), x)
     he.ntt_set_shape(N, 0, 0, 0)
 
 
