@@ -43,6 +43,10 @@ MRR_N = 16384
 MRR_BITS = [60] + [50] * 6
 MRR_COUNT = 64
 METRIC = "NTT limbs/s at N=2^15 + HE mul-relin-rescale/s, batched vs plain; p99 latency"
+# DRAM bytes (read + write) of one forward launch of the 1024 x 8 x 2^15
+# batch in the radix-8 shape below: an ncu capture of the same kernel on 256
+# instances (542019328 B read, 484354560 B written) scaled by 4.
+FWD_TRAFFIC = {"shape": [12, 3, 0], "bytes": 4 * (542019328 + 484354560)}
 UNIT = "limb-NTT/s"
 
 
@@ -58,7 +62,8 @@ def _args():
                     help="run one small case of a kernel family and exit (for profilers)")
     ap.add_argument("--instances", type=int, default=64,
                     help="NTT instances of --profile-case ntt, ciphertext pairs of --profile-case mrr")
-    ap.add_argument("--shape", default="", help="log_block,log_thread_words for --profile-case ntt")
+    ap.add_argument("--shape", default="",
+                    help="log_block,log_thread_words[,persistent] for --profile-case ntt (or fwd/inv)")
     ap.add_argument("--skip", default="", help="comma list of sub-benchmarks to skip: uneven,matrix,serving")
     ap.add_argument("--serve-requests", type=int, default=4000)
     ap.add_argument("--no-tune-cache", action="store_true", help="always re-run the autotuner")
@@ -382,7 +387,7 @@ def run_ours(args, rank, world, local):
             "peak": bfly_rate / 1e12 if bound_alu else hbm_peak,
             "unit": "Tbutterfly/s" if bound_alu else "GB/s",
             "frac": frac_alu if bound_alu else frac_hbm,
-            "traffic": None,
+            "traffic": FWD_TRAFFIC["bytes"] if list(tune["fwd"]) == FWD_TRAFFIC["shape"] else None,
             "hbm": {"achieved_gbs": achieved_gbs, "peak_gbs": hbm_peak, "frac": frac_hbm,
                     "peak_source": "measured copy bandwidth" if peaks.get("hbm_gbs") else "fallback"},
             "alu": {"achieved_tbfly": achieved_bfly / 1e12, "peak_tbfly": bfly_rate / 1e12, "frac": frac_alu,
@@ -635,8 +640,10 @@ def profile_case(args):
         N = 1 << NTT_LOG_N
         qs = _ntt_moduli()
         tables = he.NttTables(N, qs)
-        if args.shape:
-            he.ntt_set_shape(N, *([int(v) for v in args.shape.split(",")] + [0, 0, 0])[:3], direction=he.BOTH)
+        if args.shape:   # "lb,le[,persistent]" for both directions, or "fwd/inv"
+            parts = args.shape.split("/")
+            for direction, spec in zip((he.FORWARD, he.INVERSE), parts if len(parts) == 2 else parts * 2):
+                he.ntt_set_shape(N, *([int(v) for v in spec.split(",")] + [0, 0, 0])[:3], direction=direction)
         r = Rng(1)
         d = torch.from_numpy(np.stack([r.uniform_limbs(qs, N) for _ in range(args.instances)]).view(np.int64)).to(dev)
         for _ in range(args.steps):
