@@ -12,8 +12,10 @@ needed). The same run also measures, as sub-results:
   * mul-relin-rescale (MulLinRS) per second on the CKKS workload (N = 16384,
     one 60-bit + six 50-bit data primes, 60-bit special prime, 64 ciphertext
     pairs), batched versus one call per pair;
-  * the end-to-end NTT rate through host buffers (pinned host -> device,
-    forward, inverse, device -> host, every step);
+  * the end-to-end NTT rate through host buffers: every step one
+    he_ntt_host call copies the batch from pinned host memory, runs forward
+    and inverse and copies it back, pipelined in chunks over four streams
+    (and, for comparison, the same with one whole-batch copy each way);
   * the register-resident butterfly probe (integer roof) and the roofline of
     the forward transform kernel;
   * the CPU oracle on a bounded sample (cpu_baseline).
@@ -47,6 +49,13 @@ METRIC = "NTT limbs/s at N=2^15 + HE mul-relin-rescale/s, batched vs plain; p99 
 # batch in the radix-8 shape below: an ncu capture of the same kernel on 256
 # instances (542019328 B read, 484354560 B written) scaled by 4.
 FWD_TRAFFIC = {"shape": [12, 3, 0], "bytes": 4 * (542019328 + 484354560)}
+# The production forward butterfly keeps the IMAD (fmaheavy) pipe busy for
+# 0.2536 cycles per butterfly per SM: ncu on the register-resident probe
+# (1216 x 256 threads x 16 x 1024 butterflies) counts that pipe 94.2 % active
+# over 9.034 M cycles, i.e. 8.51 M busy cycles for 33.55 M butterflies per SM.
+# It is the binding unit (issue slots are 61 % used), so the integer peak is
+# SMs x clock / FMAHEAVY_CYCLES_PER_BFLY butterflies per second.
+FMAHEAVY_CYCLES_PER_BFLY = 0.2536
 UNIT = "limb-NTT/s"
 
 
@@ -301,16 +310,28 @@ def run_ours(args, rank, world, local):
     uneven = bench_uneven(args, stream, barrier) if "uneven" not in args.skip else None
     matrix = bench_matrix(args, stream, barrier) if "matrix" not in args.skip else None
 
-    # end to end through host buffers: H2D, forward, inverse, D2H every step
+    # end to end through host buffers: one he_ntt_host call per step (copy in,
+    # forward, inverse, copy out, pipelined over chunks of 32 polynomials)
     back = torch.empty_like(pinned).pin_memory()
+    work = torch.empty(4 * 32 * NTT_LIMBS * N, dtype=torch.int64, device=dev)
 
     def step_e2e():
+        he.ntt_host(pinned, back, N, NTT_LIMBS, NTT_INSTANCES, tables,
+                    he.NTT_OP_FORWARD | he.NTT_OP_INVERSE, work, stream=stream)
+
+    ms_e2e = max_over_ranks(_time_steps(step_e2e, max(3, args.steps // 2), 1, stream, barrier))
+    torch.cuda.synchronize()
+    assert torch.equal(back, pinned), "round trip changed the data"
+    back.zero_()
+
+    def step_serial():
         d.copy_(pinned, non_blocking=True)
         he.ntt_fwd(d, N, NTT_LIMBS, NTT_INSTANCES, tables, stream=stream)
         he.ntt_inv(d, N, NTT_LIMBS, NTT_INSTANCES, tables, stream=stream)
         back.copy_(d, non_blocking=True)
 
-    ms_e2e = max_over_ranks(_time_steps(step_e2e, max(3, args.steps // 2), 1, stream, barrier))
+    ms_serial = max_over_ranks(_time_steps(step_serial, 3, 1, stream, barrier))
+    del work
     clk = clocks.stop()
     assert torch.equal(back, pinned), "round trip changed the data"
     del pinned, back
@@ -331,8 +352,11 @@ def run_ours(args, rank, world, local):
     hbm_peak = peaks.get("hbm_gbs") or 6800.0
     achieved_gbs = bytes_per_launch / (fwd / 1e3) / 1e9
     achieved_bfly = bfly_per_launch / (fwd / 1e3)
+    # derived integer peak: the IMAD pipe fully busy at the sampled clock
+    clock_hz = (clk.get("sm_mhz") or peaks.get("sm_max_mhz") or 2070.0) * 1e6
+    alu_peak = sms * clock_hz / FMAHEAVY_CYCLES_PER_BFLY
     frac_hbm = achieved_gbs / hbm_peak
-    frac_alu = achieved_bfly / bfly_rate
+    frac_alu = achieved_bfly / alu_peak
     bound_alu = frac_alu >= frac_hbm
     value = world * 2 * limbs_total / (ms / 1e3)
     e2e_value = world * 2 * limbs_total / (ms_e2e / 1e3)
@@ -384,19 +408,24 @@ def run_ours(args, rank, world, local):
                 tune["fwd"][0], N >> tune["fwd"][0], tune["fwd"][1]),
             "bound": "alu" if bound_alu else "hbm",
             "achieved": achieved_bfly / 1e12 if bound_alu else achieved_gbs,
-            "peak": bfly_rate / 1e12 if bound_alu else hbm_peak,
+            "peak": alu_peak / 1e12 if bound_alu else hbm_peak,
             "unit": "Tbutterfly/s" if bound_alu else "GB/s",
             "frac": frac_alu if bound_alu else frac_hbm,
             "traffic": FWD_TRAFFIC["bytes"] if list(tune["fwd"]) == FWD_TRAFFIC["shape"] else None,
             "hbm": {"achieved_gbs": achieved_gbs, "peak_gbs": hbm_peak, "frac": frac_hbm,
                     "peak_source": "measured copy bandwidth" if peaks.get("hbm_gbs") else "fallback"},
-            "alu": {"achieved_tbfly": achieved_bfly / 1e12, "peak_tbfly": bfly_rate / 1e12, "frac": frac_alu,
-                    "peak_source": "register-resident butterfly probe, same run"},
+            "alu": {"achieved_tbfly": achieved_bfly / 1e12, "peak_tbfly": alu_peak / 1e12, "frac": frac_alu,
+                    "peak_source": f"derived: {sms} SMs x {clock_hz / 1e6:.0f} MHz / "
+                                   f"{FMAHEAVY_CYCLES_PER_BFLY} IMAD-pipe cycles per butterfly",
+                    "probe_tbfly": bfly_rate / 1e12, "frac_of_probe": achieved_bfly / bfly_rate,
+                    "probe_source": "register-resident butterfly probe, same run"},
             "algorithmic_bytes_per_launch": bytes_per_launch,
             "butterflies_per_launch": bfly_per_launch,
         },
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * limbs_total * N,
-                "d2h_bytes_per_step": 8 * limbs_total * N},
+                "d2h_bytes_per_step": 8 * limbs_total * N, "ms_per_step": ms_e2e,
+                "call": "he_ntt_host(forward | inverse), pinned host buffers, 4 streams x 32-polynomial chunks",
+                "whole_batch_copies_value": world * 2 * limbs_total / (ms_serial / 1e3)},
         "gpu_launches": 2 * args.steps,
         "clocks": clk,
     }

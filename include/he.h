@@ -262,6 +262,38 @@ he_status he_plan_destroy(he_plan *plan);
 /* Number of kernel launches one execution of the plan enqueues. */
 uint32_t he_plan_launches(const he_plan *plan);
 
+/* ---- host-resident batches (Sec. III asynchronous pipeline, multiple queues) -- */
+
+#define HE_NTT_OP_FORWARD 1u
+#define HE_NTT_OP_INVERSE 2u
+
+/* Transforms `count` polynomials of `limbs` limbs that live in HOST memory
+ * (same layout and checks as he_ntt_fwd): in_host is copied to the device,
+ * transformed and copied back to out_host. ops = HE_NTT_OP_FORWARD,
+ * HE_NTT_OP_INVERSE or both (forward, then inverse). The batch is cut into
+ * chunks of whole polynomials that flow through up to four internal streams,
+ * so that the host-to-device copy of one chunk, the kernels of another and
+ * the device-to-host copy of a third run at the same time (the paper's
+ * asynchronous pipeline: transfers and kernels queued without host
+ * synchronisation, over several queues).
+ *   work / work_bytes: device scratch owned by the caller, 16-byte aligned,
+ *     room for at least one polynomial (limbs * N * 8 bytes); more room
+ *     (e.g. 4 x 32 polynomials) gives larger chunks and full overlap.
+ *   in_host, out_host: equal (in place) or disjoint, count * limbs * N
+ *     words each. Page-locked memory (cudaHostAlloc / cudaHostRegister) is
+ *     needed for the copies to overlap and for use under stream capture;
+ *     pageable memory works but its copies do not overlap.
+ * Asynchronous with respect to the host: the work is ordered after
+ * everything already queued on `stream`, and `stream` waits for all of it,
+ * so host buffers must stay valid until `stream` has reached this point.
+ * Calls from several threads are serialised on the internal streams.
+ * Returns HE_EINVAL for a bad ops value, NULL or partly overlapping host
+ * buffers, or scratch smaller than one polynomial. Allocates nothing but,
+ * on the first call on a device, its internal streams and events. */
+he_status he_ntt_host(const uint64_t *in_host, uint64_t *out_host, uint32_t N, uint32_t limbs,
+                      uint32_t count, const uint64_t *moduli_host, const he_ntt_tables *tw, uint32_t ops,
+                      uint64_t *work, size_t work_bytes, he_stream_t stream);
+
 /* ---- measurement -------------------------------------------------------------- */
 
 /* Integer-throughput probe: blocks x threads threads each run 16 * iters

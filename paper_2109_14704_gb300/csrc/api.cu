@@ -992,6 +992,112 @@ extern "C" uint32_t he_plan_launches(const he_plan *plan)
     return plan ? (plan->mixed ? 1u : (uint32_t)plan->groups.size()) : 0;
 }
 
+// ------------------------------------------------ host-resident batches
+//
+// The asynchronous pipeline of Sec. III for data that lives in host memory:
+// chunk c of the batch goes to internal stream c mod S and scratch slot
+// c mod S, where it is copied in, transformed and copied out. Chunks on one
+// stream run in order, so a slot is reused only after its previous chunk has
+// been copied out; chunks on different streams overlap, which lets the two
+// copy directions and the kernels run at the same time. The caller's stream
+// forks into the internal streams with one event and joins them with one
+// event per stream, so the call is ordered like any other stream operation
+// and stays capturable. Streams and events are created once per device and
+// reused; the mutex keeps concurrent callers from interleaving their event
+// records.
+static const int kHostStreams = 4;
+static const u32 kHostMinChunks = 16;   // chunks per batch when the scratch allows
+
+struct HostPipeline {
+    std::mutex mu;
+    bool ready = false;
+    cudaStream_t st[kHostStreams] = {};
+    cudaEvent_t fork = nullptr;
+    cudaEvent_t join[kHostStreams] = {};
+};
+
+static std::mutex g_host_pipeline_init;
+static HostPipeline g_host_pipeline[256];   // per device ordinal
+
+static he_status host_pipeline(HostPipeline **out)
+{
+    int dev = 0;
+    HE_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) return fail(HE_EUNSUPPORTED, "device ordinal %d out of range", dev);
+    HostPipeline &p = g_host_pipeline[dev];
+    std::lock_guard<std::mutex> lock(g_host_pipeline_init);
+    if (!p.ready) {
+        HE_CUDA(cudaEventCreateWithFlags(&p.fork, cudaEventDisableTiming));
+        for (int i = 0; i < kHostStreams; i++) {
+            HE_CUDA(cudaStreamCreateWithFlags(&p.st[i], cudaStreamNonBlocking));
+            HE_CUDA(cudaEventCreateWithFlags(&p.join[i], cudaEventDisableTiming));
+        }
+        p.ready = true;
+    }
+    *out = &p;
+    return HE_OK;
+}
+
+extern "C" he_status he_ntt_host(const uint64_t *in_host, uint64_t *out_host, uint32_t N, uint32_t limbs,
+                                 uint32_t count, const uint64_t *moduli_host, const he_ntt_tables *tw, uint32_t ops,
+                                 uint64_t *work, size_t work_bytes, he_stream_t stream)
+{
+    int log_n;
+    if (he_status s = check_poly_args(work, N, limbs, moduli_host, tw, &log_n)) return s;
+    if (ops == 0 || (ops & ~(HE_NTT_OP_FORWARD | HE_NTT_OP_INVERSE)))
+        return fail(HE_EINVAL, "ops must be HE_NTT_OP_FORWARD, HE_NTT_OP_INVERSE or both, got %u", ops);
+    if ((u64)limbs * count == 0) return HE_OK;
+    if (!in_host || !out_host) return fail(HE_EINVAL, "host buffer is NULL");
+    const size_t poly_words = (size_t)limbs * N;
+    const size_t poly_bytes = poly_words * 8;
+    const size_t total_bytes = poly_bytes * count;
+    const uintptr_t ib = (uintptr_t)in_host, ob = (uintptr_t)out_host;
+    if (ib != ob && ib < ob + total_bytes && ob < ib + total_bytes)
+        return fail(HE_EINVAL, "in_host and out_host overlap without being equal");
+    const size_t fit = work_bytes / poly_bytes;
+    if (fit == 0)
+        return fail(HE_EINVAL, "scratch of %zu bytes holds no polynomial of %zu bytes", work_bytes, poly_bytes);
+    const u32 slots = (u32)std::min<size_t>({(size_t)kHostStreams, fit, (size_t)count});
+    const u32 want = (count + kHostMinChunks - 1) / kHostMinChunks;
+    const u32 chunk = (u32)std::max<size_t>(1, std::min<size_t>(fit / slots, want));
+    const u32 chunks = (count + chunk - 1) / chunk;
+    const bool fwd = ops & HE_NTT_OP_FORWARD, inv = ops & HE_NTT_OP_INVERSE;
+
+    HostPipeline *p = nullptr;
+    if (he_status s = host_pipeline(&p)) return s;
+    std::lock_guard<std::mutex> lock(p->mu);
+    cudaStream_t caller = (cudaStream_t)stream;
+    HE_CUDA(cudaEventRecord(p->fork, caller));
+    const u32 used = std::min(slots, chunks);
+    for (u32 i = 0; i < used; i++) HE_CUDA(cudaStreamWaitEvent(p->st[i], p->fork, 0));
+
+    he_status status = HE_OK;
+    for (u32 c = 0; c < chunks && status == HE_OK; c++) {
+        const u32 i = c % slots;
+        const u32 n = std::min(chunk, count - c * chunk);
+        const size_t off = (size_t)c * chunk * poly_words;
+        uint64_t *dev = work + (size_t)i * chunk * poly_words;
+        cudaError_t e = cudaMemcpyAsync(dev, in_host + off, n * poly_bytes, cudaMemcpyHostToDevice, p->st[i]);
+        if (e != cudaSuccess) {
+            status = cuda_fail(e, "copy to device");
+            break;
+        }
+        if (fwd) status = ntt_common(dev, N, limbs, n, moduli_host, tw, (he_stream_t)p->st[i], false);
+        if (status == HE_OK && inv) status = ntt_common(dev, N, limbs, n, moduli_host, tw, (he_stream_t)p->st[i], true);
+        if (status != HE_OK) break;
+        e = cudaMemcpyAsync(out_host + off, dev, n * poly_bytes, cudaMemcpyDeviceToHost, p->st[i]);
+        if (e != cudaSuccess) status = cuda_fail(e, "copy to host");
+    }
+    // join even after a failure, so that the caller's stream stays ordered
+    // after whatever was queued
+    for (u32 i = 0; i < used; i++) {
+        cudaError_t e = cudaEventRecord(p->join[i], p->st[i]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(caller, p->join[i], 0);
+        if (e != cudaSuccess && status == HE_OK) status = cuda_fail(e, "join the pipeline streams");
+    }
+    return status;
+}
+
 // ------------------------------------------- allocation-free MulLinRS
 //
 // Some callers cannot allocate device memory at the point where they need a

@@ -76,6 +76,8 @@ _SIGS = {
     "he_ntt_plan_inv": (ctypes.c_int32, [_vp, _vp]),
     "he_plan_destroy": (ctypes.c_int32, [_vp]),
     "he_plan_launches": (ctypes.c_uint32, [_vp]),
+    "he_ntt_host": (ctypes.c_int32, [_vp, _vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, _u64p, _vp,
+                                     ctypes.c_uint32, _vp, ctypes.c_size_t, _vp]),
     "he_ntt_shapes": (ctypes.c_int32, [ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32), ctypes.c_uint32,
                                        ctypes.POINTER(ctypes.c_uint32)]),
     "he_ntt_set_shape": (ctypes.c_int32, [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
@@ -237,6 +239,40 @@ def ntt_fwd(poly, N, limbs, count, tables: NttTables, moduli=None, stream=None):
 def ntt_inv(poly, N, limbs, count, tables: NttTables, moduli=None, stream=None):
     m = _moduli_arg(tables, limbs, moduli)
     _check(load().he_ntt_inv(_ptr(poly), N, limbs, count, _hp(m), tables.handle, _stream(stream)))
+
+
+NTT_OP_FORWARD, NTT_OP_INVERSE = 1, 2
+
+
+def _host_ptr(x, words: int):
+    """Host address of a numpy array or CPU torch tensor of >= `words`
+    64-bit words (or an int address)."""
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"] or x.itemsize != 8:
+            raise ValueError("expected a contiguous array of 64-bit words")
+        if x.size < words:
+            raise ValueError(f"host array holds {x.size} words, need {words}")
+        return x.ctypes.data
+    if x.is_cuda:
+        raise ValueError("expected a host (CPU) tensor")
+    if not x.is_contiguous() or x.element_size() != 8:
+        raise ValueError("expected a contiguous tensor of 64-bit words")
+    if x.numel() < words:
+        raise ValueError(f"host tensor holds {x.numel()} words, need {words}")
+    return x.data_ptr()
+
+
+def ntt_host(inp, out, N, limbs, count, tables: NttTables, ops, work, moduli=None, stream=None):
+    """he_ntt_host: transform host-resident polynomials through the device
+    (copy in, ops = NTT_OP_FORWARD / NTT_OP_INVERSE / both, copy out),
+    pipelined over chunks; `work` is device scratch."""
+    m = _moduli_arg(tables, limbs, moduli)
+    words = N * limbs * count
+    nbytes = work.numel() * work.element_size()
+    _check(load().he_ntt_host(_host_ptr(inp, words), _host_ptr(out, words), N, limbs, count, _hp(m),
+                              tables.handle, ops, _ptr(work), nbytes, _stream(stream)))
 
 
 def ntt_fwd_naive(poly, N, limbs, count, tables: NttTables, moduli=None, stream=None):

@@ -65,8 +65,11 @@ def test_invalid_arguments_rejected_on_host():
     # null output handle, no moduli
     assert lib.he_ntt_tables_create(4096, 1, qp, None) == he.HE_EINVAL
     assert lib.he_ntt_tables_create(4096, 0, qp, ctypes.byref(h)) == he.HE_EINVAL
-    # null tables on a transform
+    # null tables on a transform, on a host-buffer transform
     assert lib.he_ntt_fwd(None, 4096, 1, 1, qp, None, None) == he.HE_EINVAL
+    host = np.zeros(4096, dtype=np.uint64)
+    assert lib.he_ntt_host(host.ctypes.data, host.ctypes.data, 4096, 1, 1, qp, None, 1, None, 1 << 20,
+                           None) == he.HE_EINVAL
     # contexts: too many primes, duplicates, small primes
     assert lib.he_context_create(4096, 0, qp, int(q[0]), ctypes.byref(h)) == he.HE_EINVAL
     assert lib.he_context_create(4096, 1, qp, int(q[0]), ctypes.byref(h)) == he.HE_EINVAL
