@@ -24,7 +24,7 @@ __device__ __forceinline__ void ntt_limb(u64 *smem, u32 m, u32 rbase, u64 *data,
     u64 x[Sh::E];
     const u32 tid = threadIdx.x;
     if constexpr (!INV) {
-        auto ld = [&](u32 P) -> u64 { return __ldcs(reinterpret_cast<const unsigned long long *>(data + P)); };
+        auto ld = [&](int P) -> u64 { return __ldcs(reinterpret_cast<const unsigned long long *>(data + P)); };
         auto nost = [&](u32, u64) {};
         ntt_fwd_block<Sh>(smem, m, rbase, tw, pc, ld, nost, x);
         if (valid) {
@@ -40,7 +40,7 @@ __device__ __forceinline__ void ntt_limb(u64 *smem, u32 m, u32 rbase, u64 *data,
             x[e + 1] = v.y;
         }
         auto nold = [&](u32) -> u64 { return 0; };
-        auto st = [&](u32 P, u64 v) {
+        auto st = [&](int P, u64 v) {
             if (valid) __stcs(reinterpret_cast<unsigned long long *>(data + P), (unsigned long long)v);
         };
         ntt_inv_block<Sh, true>(smem, m, rbase, tw, pc, nold, st, x);
@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(256, 4) k_ntt_mixed(const MixedUnit *units, u3
     const u32 clusters = gridDim.x >> 3;
     bool first = true;
     for (u32 ui = blockIdx.x >> 3; ui < n_units; ui += clusters) {
-        if (!first) cluster_sync_all();
+        if (!first) cluster_sync_war();
         first = false;
         const MixedUnit un = units[ui];
         switch (un.log_n) {

@@ -34,11 +34,23 @@ struct PrimeConst {
     u32 h4;          // ceil(4p / 2^32): high-word threshold of the lazy reduction
 };
 
-__device__ __forceinline__ u64 reduce_once(u64 x, u64 m) { return x >= m ? x - m : x; }
+// x >= m ? x - m : x for x, m < 2^63 (every caller: moduli below 2^60 and
+// values below 16p). The sign of x - m decides, which saves the 64-bit
+// unsigned comparison (two compare instructions) of the plain form.
+__device__ __forceinline__ u64 reduce_once(u64 x, u64 m)
+{
+    const u64 r = x - m;
+    return (long long)r < 0 ? x : r;
+}
 
 __device__ __forceinline__ u64 add_mod(u64 a, u64 b, u64 p) { return reduce_once(a + b, p); }
 
-__device__ __forceinline__ u64 sub_mod(u64 a, u64 b, u64 p) { return a >= b ? a - b : a + p - b; }
+// a - b mod p for a, b < p < 2^62, by the sign of a - b.
+__device__ __forceinline__ u64 sub_mod(u64 a, u64 b, u64 p)
+{
+    const u64 r = a - b;
+    return (long long)r < 0 ? r + p : r;
+}
 
 // W * Y mod p in [0, 2p) for any Y < 2^64 (Shoup).
 __device__ __forceinline__ u64 mul_shoup_lazy(u64 y, u64 w, u64 w_sh, u64 p)

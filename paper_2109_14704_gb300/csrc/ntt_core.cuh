@@ -67,6 +67,17 @@ __device__ __forceinline__ void cluster_sync_all()
                  "barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
+// Cluster barrier for write-after-read only: every CTA has finished reading
+// shared memory that a peer is about to overwrite (or release by exiting).
+// Those reads have returned their values before the arrive is issued, so the
+// arrive needs no release ordering (and no memory fence before it); waits on
+// it still acquire.
+__device__ __forceinline__ void cluster_sync_war()
+{
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;\n\t"
+                 "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ u32 smem_u32(const void *p) { return (u32)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ u32 map_to_rank(u32 addr, u32 rank)
@@ -88,7 +99,11 @@ __device__ __forceinline__ u64 ld_cluster(u32 addr)
     return v;
 }
 
-__device__ __forceinline__ ulonglong2 ld_tw(const ulonglong2 *tw, u32 idx) { return __ldg(tw + idx); }
+// Positions and twiddle indices are signed ints (all below 2^17): a signed
+// sum cannot wrap, so the compiler may split base + constant and fold the
+// constant into the load's immediate offset, where a u32 sum would need its
+// own 64-bit address computation per access.
+__device__ __forceinline__ ulonglong2 ld_tw(const ulonglong2 *tw, int idx) { return __ldg(tw + idx); }
 
 template <int LOG_B_, int LOG_C_, int LOG_E_ = 4>
 struct NttShape {
@@ -132,12 +147,12 @@ struct RoundOf {
 
 // Block-local position of element u of subgroup i of this thread in a round.
 template <class Rd>
-__device__ __forceinline__ u32 round_pos(u32 tid, int i, int u)
+__device__ __forceinline__ int round_pos(u32 tid, int i, int u)
 {
-    u32 sg = tid * Rd::SUB + (u32)i;
-    u32 k = sg & (Rd::TL - 1);
-    u32 g = sg >> Rd::LOG_TL;
-    return (g << (Rd::LOG_TL + Rd::R)) + k + (u32)u * Rd::TL;
+    const int sg = (int)tid * Rd::SUB + i;
+    const int k = sg & ((int)Rd::TL - 1);
+    const int g = sg >> Rd::LOG_TL;
+    return g * (1 << (Rd::LOG_TL + Rd::R)) + k + u * (int)Rd::TL;
 }
 
 // Group base of subgroup i in a round: the index, at the round's first stage,
@@ -160,7 +175,7 @@ template <class Sh>
 __device__ __forceinline__ void ntt_barrier()
 {
     if constexpr (Sh::LOG_C > 0)
-        cluster_sync_all();
+        cluster_sync_war();
     else
         __syncthreads();
 }
@@ -213,7 +228,7 @@ __device__ __forceinline__ void fwd_stage(u64 (&x)[Sh::E], u32 tid, u32 m, const
         const u32 G = round_group_base<Sh, Rd>(tid, i, m);
 #pragma unroll
         for (int grp = 0; grp < (1 << q); grp++) {
-            const ulonglong2 w = ld_tw(tw, (1u << S) + (G << q) + (u32)grp);
+            const ulonglong2 w = ld_tw(tw, (1 << S) + (int)G * (1 << q) + grp);
 #pragma unroll
             for (int v = 0; v < half; v++) {
                 const int u = grp * 2 * half + v;
@@ -259,27 +274,27 @@ __device__ __forceinline__ void fwd_cross(u64 *s, u32 tid, u32 m, u32 rbase, con
 {
     constexpr u32 C = Sh::C;
     constexpr int COLS = Sh::E / (int)C;
-    ulonglong2 wt[C];
-#pragma unroll
-    for (u32 i = 1; i < C; i++) wt[i] = ld_tw(tw, i);
     const u32 s_base = smem_u32(s);
 #pragma unroll
     for (int c = 0; c < COLS; c++) {
-        const u32 j = m * (Sh::B / C) + (u32)c * Sh::T + tid;
+        const int j = (int)(m * (Sh::B / C)) + c * (int)Sh::T + (int)tid;
         u64 v[C];
 #pragma unroll
-        for (u32 t = 0; t < C; t++) v[t] = load(t * Sh::B + j);
+        for (u32 t = 0; t < C; t++) v[t] = load((int)t * (int)Sh::B + j);
 #pragma unroll
         for (int S = 0; S < Sh::LOG_C; S++) {
             const u32 half = C >> (S + 1);
+            ulonglong2 ws[C / 2];   // this stage's twiddles only: fewer live registers
+#pragma unroll
+            for (int g = 0; g < (1 << S); g++) ws[g] = ld_tw(tw, (1 << S) + g);
 #pragma unroll
             for (u32 t = 0; t < C; t++) {
                 if (t & half) continue;
-                const u32 idx = (1u << S) + (t >> (Sh::LOG_C - S));
-                ct_butterfly(v[t], v[t + half], wt[idx].x, wt[idx].y, pc);
+                const ulonglong2 w = ws[t >> (Sh::LOG_C - S)];
+                ct_butterfly(v[t], v[t + half], w.x, w.y, pc);
             }
         }
-        const u32 a = s_base + swz<Sh::LOG_E>(j) * 8u;
+        const u32 a = s_base + swz<Sh::LOG_E>((u32)j) * 8u;
 #pragma unroll
         for (u32 t = 0; t < C; t++) st_cluster(map_to_rank(a, rbase + t), v[t]);
     }
@@ -315,17 +330,17 @@ __device__ __forceinline__ void ntt_fwd_block(u64 *s, u32 m, u32 rbase, const ul
         for (int u = 0; u < (1 << RL::R); u++) {
             const u64 v = reduce_from_fwd_range(x[i * (1 << RL::R) + u], pc);
             x[i * (1 << RL::R) + u] = v;
-            store(m * Sh::B + round_pos<RL>(tid, i, u), v);
+            store((int)(m * Sh::B) + round_pos<RL>(tid, i, u), v);
         }
 }
 
 // Position (within the limb) of element e of x[] after ntt_fwd_block, and of
 // the input element e expected by ntt_inv_block with HAVE_X.
 template <class Sh>
-__device__ __forceinline__ u32 last_pos(u32 m, u32 tid, int e)
+__device__ __forceinline__ int last_pos(u32 m, u32 tid, int e)
 {
     using RL = RoundOf<Sh, Sh::NROUND - 1>;
-    return m * Sh::B + round_pos<RL>(tid, e >> RL::R, e & ((1 << RL::R) - 1));
+    return (int)(m * Sh::B) + round_pos<RL>(tid, e >> RL::R, e & ((1 << RL::R) - 1));
 }
 
 // ---------------------------------------------------------------- inverse
@@ -359,7 +374,7 @@ __device__ __forceinline__ void inv_stage(u64 (&x)[Sh::E], u32 tid, u32 m, const
                     gs_last(x[i * (1 << Rd::R) + u], x[i * (1 << Rd::R) + u + half], pc);
                 }
             } else {
-                const ulonglong2 w = ld_tw(tw, (1u << S) + (G << q) + (u32)grp);
+                const ulonglong2 w = ld_tw(tw, (1 << S) + (int)G * (1 << q) + grp);
 #pragma unroll
                 for (int v = 0; v < half; v++) {
                     const int u = grp * 2 * half + v;
@@ -425,14 +440,11 @@ __device__ __forceinline__ void ntt_inv_block(u64 *s, u32 m, u32 rbase, const ul
         cluster_sync_all();
         constexpr u32 C = Sh::C;
         constexpr int COLS = Sh::E / (int)C;
-        ulonglong2 wt[C];
-#pragma unroll
-        for (u32 i = 2; i < C; i++) wt[i] = ld_tw(tw, i);
         const u32 s_base = smem_u32(s);
 #pragma unroll
         for (int c = 0; c < COLS; c++) {
-            const u32 j = m * (Sh::B / C) + (u32)c * Sh::T + tid;
-            const u32 a = s_base + swz<Sh::LOG_E>(j) * 8u;
+            const int j = (int)(m * (Sh::B / C)) + c * (int)Sh::T + (int)tid;
+            const u32 a = s_base + swz<Sh::LOG_E>((u32)j) * 8u;
             u64 v[C];
 #pragma unroll
             for (u32 t = 0; t < C; t++) v[t] = ld_cluster(map_to_rank(a, rbase + t));
@@ -440,21 +452,26 @@ __device__ __forceinline__ void ntt_inv_block(u64 *s, u32 m, u32 rbase, const ul
             for (int SS = 0; SS < Sh::LOG_C; SS++) {
                 const int S = Sh::LOG_C - 1 - SS;
                 const u32 half = C >> (S + 1);
+                ulonglong2 ws[C / 2];   // this stage's twiddles only
+                if (S > 0) {
+#pragma unroll
+                    for (int g = 0; g < (1 << S); g++) ws[g] = ld_tw(tw, (1 << S) + g);
+                }
 #pragma unroll
                 for (u32 t = 0; t < C; t++) {
                     if (t & half) continue;
                     if (S == 0) {
                         gs_last(v[t], v[t + half], pc);
                     } else {
-                        const u32 idx = (1u << S) + (t >> (Sh::LOG_C - S));
-                        gs_butterfly(v[t], v[t + half], wt[idx].x, wt[idx].y, pc);
+                        const ulonglong2 w = ws[t >> (Sh::LOG_C - S)];
+                        gs_butterfly(v[t], v[t + half], w.x, w.y, pc);
                     }
                 }
             }
 #pragma unroll
-            for (u32 t = 0; t < C; t++) store(t * Sh::B + j, v[t]);
+            for (u32 t = 0; t < C; t++) store((int)t * (int)Sh::B + j, v[t]);
         }
-        cluster_sync_all();  // peers may still read this CTA's shared memory
+        cluster_sync_war();  // peers may still read this CTA's shared memory
     }
 }
 
