@@ -271,6 +271,11 @@ __device__ __forceinline__ u64 centred_mod(u64 y, u64 half_m, u64 m_mod_q, const
     return y > half_m ? sub_mod(r, m_mod_q, pc.p) : r;
 }
 
+// a - x + 12p: congruent to a - x mod p and positive for a < 2^63 - 12p and
+// x < 12p (a lazy forward-transform output, see ntt_fwd_block with CANON =
+// false); below 2^64 for a < 2p, so it can go straight into mul_shoup.
+__device__ __forceinline__ u64 lazy_sub(u64 a, u64 x, u64 twelve_p) { return a + twelve_p - x; }
+
 // Read-only load (the kernel never writes what it reads through this).
 __device__ __forceinline__ u64 rd(const u64 *p) { return __ldg(reinterpret_cast<const unsigned long long *>(p)); }
 
@@ -346,13 +351,13 @@ k_ks_modup(EvalArgs a)
             // digit: when q_j <= 8t the digit c2_j < q_j goes in as it is.
             if (a.ctx.pc[j].p <= (pc.four_p << 1)) {
                 auto ld = [&](u32 P) -> u64 { return __ldg(reinterpret_cast<const unsigned long long *>(src + P)); };
-                ntt_fwd_block<Sh>(smem, m, 0, twf, pc, ld, st, x);
+                ntt_fwd_block<Sh, false>(smem, m, 0, twf, pc, ld, st, x);
             } else {
                 auto ld = [&](u32 P) -> u64 {
                     return barrett_reduce(0, __ldg(reinterpret_cast<const unsigned long long *>(src + P)), pc.p,
                                           pc.mu, pc.bits);
                 };
-                ntt_fwd_block<Sh>(smem, m, 0, twf, pc, ld, st, x);
+                ntt_fwd_block<Sh, false>(smem, m, 0, twf, pc, ld, st, x);
             }
         }
         // multiply-accumulate with the key: lazy products in [0, 4p),
@@ -415,13 +420,14 @@ k_ks_moddown(EvalArgs a)
     u64 x[Sh::E];
     auto ld = [&](u32 P) -> u64 { return centred_mod(rd(y + P), half_P, cst[2], pc); };
     auto st = [&](u32, u64) {};
-    ntt_fwd_block<Sh>(smem, m, 0, a.ctx.tw_fwd + (size_t)i * Sh::N, pc, ld, st, x);
+    ntt_fwd_block<Sh, false>(smem, m, 0, a.ctx.tw_fwd + (size_t)i * Sh::N, pc, ld, st, x);
     const u64 *accp = a.accq + (((size_t)c * 2 + k) * n + i) * Sh::N;
     u64 *out = a.out + (((size_t)c * 2 + k) * n + i) * Sh::N;
+    const u64 twelve_p = 3 * pc.four_p;
 #pragma unroll
     for (int e = 0; e < Sh::E; e++) {
         const u32 P = last_pos<Sh>(m, tid, e);
-        const u64 v = mul_shoup(sub_mod(rd(accp + P), x[e], pc.p), cst[0], cst[1], pc.p);
+        const u64 v = mul_shoup(lazy_sub(rd(accp + P), x[e], twelve_p), cst[0], cst[1], pc.p);
         out[P] = add_mod(ds.d(k, i, Sh::LOG_N, P, pc), v, pc.p);
     }
 }
@@ -465,13 +471,14 @@ k_rs(EvalArgs a)
     u64 x[Sh::E];
     auto ld = [&](u32 P) -> u64 { return centred_mod(rd(y + P), half_l, cst[2], pc); };
     auto st = [&](u32, u64) {};
-    ntt_fwd_block<Sh>(smem, m, 0, a.ctx.tw_fwd + (size_t)i * Sh::N, pc, ld, st, x);
+    ntt_fwd_block<Sh, false>(smem, m, 0, a.ctx.tw_fwd + (size_t)i * Sh::N, pc, ld, st, x);
     const u64 *src = a.ct2 + (((size_t)c * 2 + k) * n + i) * Sh::N;
     u64 *out = a.out + (((size_t)c * 2 + k) * l + i) * Sh::N;
+    const u64 twelve_p = 3 * pc.four_p;
 #pragma unroll
     for (int e = 0; e < Sh::E; e++) {
         const u32 P = last_pos<Sh>(m, tid, e);
-        out[P] = mul_shoup(sub_mod(rd(src + P), x[e], pc.p), cst[0], cst[1], pc.p);
+        out[P] = mul_shoup(lazy_sub(rd(src + P), x[e], twelve_p), cst[0], cst[1], pc.p);
     }
 }
 
@@ -497,12 +504,13 @@ k_mrr_last(EvalArgs a)
     u64 x[Sh::E];
     auto ld = [&](u32 P) -> u64 { return centred_mod(rd(y + P), half_P, cst[2], pc); };
     auto nost = [&](u32, u64) {};
-    ntt_fwd_block<Sh>(smem, m, 0, a.ctx.tw_fwd + (size_t)l * Sh::N, pc, ld, nost, x);
+    ntt_fwd_block<Sh, false>(smem, m, 0, a.ctx.tw_fwd + (size_t)l * Sh::N, pc, ld, nost, x);
     const u64 *accp = a.accq + (((size_t)c * 2 + k) * n + l) * Sh::N;
+    const u64 twelve_p = 3 * pc.four_p;
 #pragma unroll
     for (int e = 0; e < Sh::E; e++) {
         const u32 P = last_pos<Sh>(m, tid, e);
-        const u64 v = mul_shoup(sub_mod(rd(accp + P), x[e], pc.p), cst[0], cst[1], pc.p);
+        const u64 v = mul_shoup(lazy_sub(rd(accp + P), x[e], twelve_p), cst[0], cst[1], pc.p);
         x[e] = add_mod(ds.d(k, l, Sh::LOG_N, P, pc), v, pc.p);
     }
     u64 *dst = a.lift2 + ((size_t)c * 2 + k) * Sh::N;
@@ -535,23 +543,24 @@ k_mrr_rest(EvalArgs a)
     u64 x[Sh::E], z[Sh::E];
     auto nost = [&](u32, u64) {};
     auto ld1 = [&](u32 P) -> u64 { return centred_mod(rd(y + P), half_P, cP[2], pc); };
-    ntt_fwd_block<Sh>(smem, m, 0, twf, pc, ld1, nost, x);
+    ntt_fwd_block<Sh, false>(smem, m, 0, twf, pc, ld1, nost, x);
     const u64 *accp = a.accq + (((size_t)c * 2 + k) * n + i) * Sh::N;
+    const u64 twelve_p = 3 * pc.four_p;
 #pragma unroll
     for (int e = 0; e < Sh::E; e++) {
         const u32 P = last_pos<Sh>(m, tid, e);
-        const u64 v = mul_shoup(sub_mod(rd(accp + P), x[e], pc.p), cP[0], cP[1], pc.p);
+        const u64 v = mul_shoup(lazy_sub(rd(accp + P), x[e], twelve_p), cP[0], cP[1], pc.p);
         z[e] = add_mod(ds.d(k, i, Sh::LOG_N, P, pc), v, pc.p);
     }
     ntt_barrier<Sh>();
     const u64 *y2 = a.lift2 + ((size_t)c * 2 + k) * Sh::N;
     auto ld2 = [&](u32 P) -> u64 { return centred_mod(rd(y2 + P), half_l, cl[2], pc); };
-    ntt_fwd_block<Sh>(smem, m, 0, twf, pc, ld2, nost, x);
+    ntt_fwd_block<Sh, false>(smem, m, 0, twf, pc, ld2, nost, x);
     u64 *out = a.out + (((size_t)c * 2 + k) * l + i) * Sh::N;
 #pragma unroll
     for (int e = 0; e < Sh::E; e++) {
         const u32 P = last_pos<Sh>(m, tid, e);
-        out[P] = mul_shoup(sub_mod(z[e], x[e], pc.p), cl[0], cl[1], pc.p);
+        out[P] = mul_shoup(lazy_sub(z[e], x[e], twelve_p), cl[0], cl[1], pc.p);
     }
 }
 

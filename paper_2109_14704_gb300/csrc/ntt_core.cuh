@@ -306,8 +306,10 @@ __device__ __forceinline__ void fwd_cross(u64 *s, u32 tid, u32 m, u32 rbase, con
 // load(P) gives input position P in [0, N) (values below 8p); store(P, v)
 // receives the canonical output at bit-reversed evaluation index P. After
 // the call the canonical values also remain in x[] in the last round's order
-// (see last_pos).
-template <class Sh, class Load, class Store>
+// (see last_pos). With CANON = false the final reduction is skipped: x[] and
+// store receive values in [0, 8p + 2^32), below 12p for p >= 2^30, for
+// callers that feed them straight into a Shoup product (any 64-bit input).
+template <class Sh, bool CANON = true, class Load, class Store>
 __device__ __forceinline__ void ntt_fwd_block(u64 *s, u32 m, u32 rbase, const ulonglong2 *tw,
                                               const PrimeConst &pc, Load load, Store store, u64 (&x)[Sh::E])
 {
@@ -328,7 +330,7 @@ __device__ __forceinline__ void ntt_fwd_block(u64 *s, u32 m, u32 rbase, const ul
     for (int i = 0; i < RL::SUB; i++)
 #pragma unroll
         for (int u = 0; u < (1 << RL::R); u++) {
-            const u64 v = reduce_from_fwd_range(x[i * (1 << RL::R) + u], pc);
+            const u64 v = CANON ? reduce_from_fwd_range(x[i * (1 << RL::R) + u], pc) : x[i * (1 << RL::R) + u];
             x[i * (1 << RL::R) + u] = v;
             store((int)(m * Sh::B) + round_pos<RL>(tid, i, u), v);
         }
