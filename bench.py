@@ -655,7 +655,8 @@ def profile_case(args):
     """A small case of one kernel family: `ntt` transforms args.instances x 8
     limbs at N = 2^15 (64 instances = 128 MiB, above the L2 size) forward
     then inverse, `mrr` runs one MulLinRS batch of args.instances pairs on
-    the CKKS workload, `probe` the butterfly probe. Each runs `--steps` times."""
+    the CKKS workload (--shape: log2 words per thread of its kernels),
+    `probe` the butterfly probe. Each runs `--steps` times."""
     import numpy as np
     import torch
 
@@ -690,6 +691,8 @@ def profile_case(args):
         ca, cb = mk(), mk()
         out = torch.empty((count, 2, L, MRR_N), dtype=torch.int64, device=dev)
         scratch = torch.empty(ctx.mrr_scratch_bytes(L, count) // 8, dtype=torch.int64, device=dev)
+        if args.shape:   # words per thread of the evaluation kernels, as log2
+            ctx.set_eval_shape(int(args.shape))
         for _ in range(args.steps):
             he.mul_relin_rescale(out, ca, cb, count, key, ctx, L, scratch)
     else:

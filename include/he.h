@@ -179,7 +179,16 @@ he_status he_ct_mul(uint64_t *out3, const uint64_t *ct_a, const uint64_t *ct_b,
 
 /* Relin (Sec. II-A): ct_out2 = (c0, c1) + round(P^-1 c[2] evk) mod q_l, with
  * c[2] split into its RNS digits [c[2]]_{q_j} in [0, q_j) and the division by
- * P rounded half up. ct_in3 is [3][l+1][N], ct_out2 is [2][l+1][N]. */
+ * P rounded half up. ct_in3 is [3][l+1][N], ct_out2 is [2][l+1][N].
+ *
+ * Scratch (device, 16-byte aligned, contents irrelevant) of key switching,
+ * with n = l + 1 limbs: at least (3 n + 2) N words (Relin) or
+ * (3 n + 4) N words per pair (MulLinRS); then the mod-up runs as one fused
+ * kernel per (ciphertext, target prime). With room for (n + 1) n N more
+ * words per ciphertext of a group of up to 64 the mod-up is expanded: each
+ * digit-to-target transform runs as its own cluster at the plain
+ * transform's size, and the key products as an elementwise pass -- faster,
+ * same result. The *_scratch_bytes functions return the expanded size. */
 size_t he_relin_scratch_bytes(const he_context *ctx, uint32_t level);
 he_status he_relin(uint64_t *ct_out2, const uint64_t *ct_in3, const he_relin_key *key,
                    const he_context *ctx, uint32_t level, void *scratch, size_t scratch_bytes,
@@ -210,8 +219,9 @@ he_status he_mul_relin_rescale(uint64_t *ct_out, const uint64_t *ct_a, const uin
  * taking its scratch from a buffer of HE_NOALLOC_SCRATCH_BYTES compiled into
  * the library, held on every GPU that loads the library until the process
  * exits. It never allocates. Requests needing more scratch than that
- * ((3 (level + 1) + 4) * N * 8 bytes per pair) return HE_EINVAL with a
- * message. The first call on each device resolves the buffer's address
+ * ((3 (level + 1) + 4) * N * 8 bytes per pair, the fused mod-up's minimum)
+ * return HE_EINVAL with a message; the expanded mod-up runs when the
+ * buffer also holds its group buffer. The first call on each device resolves the buffer's address
  * (cudaGetSymbolAddress, with that device current), so make that first call
  * before any stream capture. All calls share the buffer: calls that may
  * overlap on the GPU race and must be ordered by the caller (e.g. one

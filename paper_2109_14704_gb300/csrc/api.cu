@@ -378,6 +378,20 @@ extern "C" he_status he_ntt_set_shape(uint32_t N, uint32_t direction, uint32_t l
     return HE_OK;
 }
 
+// One launch of a batch of limb transforms in the shape set for the degree.
+static he_status ntt_launch(const he::NttLaunch &a, int log_n, bool inv, cudaStream_t stream)
+{
+    const he::DegreeOps *ops = he::degree_ops(log_n);
+    const int lb = g_shape_b[inv][log_n].load(), le = g_shape_e[inv][log_n].load();
+    if (g_shape_persistent[inv][log_n].load()) {
+        const u32 clusters = std::min<u32>(a.items, (u32)std::max(ops->max_clusters(lb, le, inv), 1));
+        HE_CUDA(ops->ntt_persistent(a, lb, le, inv, clusters, stream));
+    } else {
+        HE_CUDA(ops->ntt(a, lb, le, inv, stream));
+    }
+    return HE_OK;
+}
+
 static he_status ntt_common(uint64_t *poly, uint32_t N, uint32_t limbs, uint32_t count,
                             const uint64_t *moduli_host, const he_ntt_tables *tw, he_stream_t stream, bool inv)
 {
@@ -385,16 +399,7 @@ static he_status ntt_common(uint64_t *poly, uint32_t N, uint32_t limbs, uint32_t
     if (he_status s = check_poly_args(poly, N, limbs, moduli_host, tw, &log_n)) return s;
     if ((u64)limbs * count == 0) return HE_OK;
     if ((u64)limbs * count * (N / 4096 + 1) > 0x7fffffffull) return fail(HE_EINVAL, "batch too large");
-    const he::DegreeOps *ops = he::degree_ops(log_n);
-    const int lb = g_shape_b[inv][log_n].load(), le = g_shape_e[inv][log_n].load();
-    const he::NttLaunch a = uniform_launch(poly, limbs, count, tw);
-    if (g_shape_persistent[inv][log_n].load()) {
-        const u32 clusters = std::min<u32>(a.items, (u32)std::max(ops->max_clusters(lb, le, inv), 1));
-        HE_CUDA(ops->ntt_persistent(a, lb, le, inv, clusters, (cudaStream_t)stream));
-    } else {
-        HE_CUDA(ops->ntt(a, lb, le, inv, (cudaStream_t)stream));
-    }
-    return HE_OK;
+    return ntt_launch(uniform_launch(poly, limbs, count, tw), log_n, inv, (cudaStream_t)stream);
 }
 
 extern "C" he_status he_ntt_fwd(uint64_t *poly, uint32_t N, uint32_t limbs, uint32_t count,
@@ -657,14 +662,18 @@ extern "C" he_status he_ct_mul(uint64_t *out3, const uint64_t *ct_a, const uint6
     return HE_OK;
 }
 
-// Scratch of key switching and rescale, in words per ciphertext.
+// Scratch of key switching and rescale, in words per ciphertext (the
+// minimum, with the fused mod-up), plus the expanded mod-up's buffer for a
+// group of ciphertexts.
 static size_t relin_words(const he_context *c, u32 n) { return (size_t)(3 * n + 2) * c->N; }
 static size_t rescale_words(const he_context *c) { return (size_t)2 * c->N; }
 static size_t mrr_words(const he_context *c, u32 n) { return (size_t)(3 * n + 4) * c->N; }
+static const u32 kModupGroup = 64;  // ciphertexts per expanded mod-up group (fewer, larger launches)
+static size_t modup_x_words(const he_context *c, u32 n, u32 group) { return (size_t)group * (n + 1) * n * c->N; }
 
 extern "C" size_t he_relin_scratch_bytes(const he_context *ctx, uint32_t level)
 {
-    return ctx ? relin_words(ctx, level + 1) * 8 : 0;
+    return ctx ? (relin_words(ctx, level + 1) + modup_x_words(ctx, level + 1, 1)) * 8 : 0;
 }
 
 extern "C" size_t he_rescale_scratch_bytes(const he_context *ctx, uint32_t level)
@@ -675,7 +684,8 @@ extern "C" size_t he_rescale_scratch_bytes(const he_context *ctx, uint32_t level
 
 extern "C" size_t he_mul_relin_rescale_scratch_bytes(const he_context *ctx, uint32_t level, uint32_t count)
 {
-    return ctx ? mrr_words(ctx, level + 1) * 8 * count : 0;
+    if (!ctx || !count) return 0;
+    return (mrr_words(ctx, level + 1) * count + modup_x_words(ctx, level + 1, std::min(count, kModupGroup))) * 8;
 }
 
 static he_status run_eval(const he_context *ctx, he::EvalKernel k, const he::EvalArgs &a, u32 items,
@@ -684,6 +694,43 @@ static he_status run_eval(const he_context *ctx, he::EvalKernel k, const he::Eva
     if (!items) return HE_OK;
     HE_CUDA(he::degree_ops(ctx->log_n)->eval(k, a, items, ctx->eval_log_e.load(), s));
     return HE_OK;
+}
+
+// Mod-up of key switching for `count` ciphertexts (a.c2 holds their
+// coefficient-domain digits): accq and plift as k_ks_modup leaves them.
+// With room for the expanded buffer (x_words at xbuf, at least one
+// ciphertext's (n + 1) n N words) the transforms run as independent plain-
+// size launches (k_ks_expand), the key products as an elementwise pass
+// (k_ks_mac) and the special prime's accumulators go through the inverse
+// transform in place; the buffer takes groups of up to kModupGroup
+// ciphertexts. Otherwise the fused k_ks_modup runs.
+static he_status ks_modup(const he_context *ctx, he::EvalArgs &a, u32 count, u64 *xbuf, size_t x_words,
+                          cudaStream_t s)
+{
+    const u32 n = a.n;
+    const size_t per = (size_t)(n + 1) * n * ctx->N;
+    const u32 group = (u32)std::min<size_t>({(size_t)kModupGroup, (size_t)count, xbuf ? x_words / per : 0});
+    if (group == 0) return run_eval(ctx, he::EK_KS_MODUP, a, count * (n + 1), s);
+    a.mx = xbuf;
+    for (u32 c0 = 0; c0 < count; c0 += group) {
+        const u32 gs = std::min(group, count - c0);
+        a.c_first = c0;
+        if (he_status r = run_eval(ctx, he::EK_KS_EXPAND, a, gs * (n + 1) * n, s)) return r;
+        const u64 chunks = (gs + he::MAC_CTS - 1) / he::MAC_CTS;
+        he::k_ks_mac<<<stream_grid(chunks * (n + 1) * (ctx->N / 2), 256), 256, 0, s>>>(a, gs);
+        HE_CUDA(cudaGetLastError());
+    }
+    a.mx = nullptr;
+    a.c_first = 0;
+    he::NttLaunch L = {};
+    L.base = a.plift;
+    L.limbs = 1;
+    L.first_prime = ctx->n_data;
+    L.items = 2 * count;
+    L.tw_fwd = ctx->tables->d_fwd;
+    L.tw_inv = ctx->tables->d_inv;
+    L.pc = ctx->tables->d_pc;
+    return ntt_launch(L, ctx->log_n, true, s);
 }
 
 extern "C" he_status he_relin(uint64_t *ct_out2, const uint64_t *ct_in3, const he_relin_key *key,
@@ -708,8 +755,10 @@ extern "C" he_status he_relin(uint64_t *ct_out2, const uint64_t *ct_in3, const h
     a.count = 1;
     a.ctx = dev_ctx(ctx);
     cudaStream_t s = (cudaStream_t)stream;
+    u64 *xbuf = (u64 *)scratch + relin_words(ctx, n);
+    const size_t x_words = scratch_bytes / 8 - relin_words(ctx, n);
     if (he_status r = run_eval(ctx, he::EK_KS_DIGITS, a, n, s)) return r;
-    if (he_status r = run_eval(ctx, he::EK_KS_MODUP, a, n + 1, s)) return r;
+    if (he_status r = ks_modup(ctx, a, 1, xbuf, x_words, s)) return r;
     return run_eval(ctx, he::EK_KS_MODDOWN, a, 2 * n, s);
 }
 
@@ -760,10 +809,13 @@ extern "C" he_status he_mul_relin_rescale(uint64_t *ct_out, const uint64_t *ct_a
     a.count = count;
     a.ctx = dev_ctx(ctx);
     cudaStream_t s = (cudaStream_t)stream;
+    u64 *xbuf = (u64 *)scratch + mrr_words(ctx, n) * count;
+    const size_t x_words = scratch_bytes / 8 - mrr_words(ctx, n) * count;
     if (he_status r = run_eval(ctx, he::EK_KS_DIGITS, a, count * n, s)) return r;
-    if (he_status r = run_eval(ctx, he::EK_KS_MODUP, a, count * (n + 1), s)) return r;
+    if (he_status r = ks_modup(ctx, a, count, xbuf, x_words, s)) return r;
     if (he_status r = run_eval(ctx, he::EK_MRR_LAST, a, count * 2, s)) return r;
-    return run_eval(ctx, he::EK_MRR_REST, a, count * 2 * level, s);
+    if (he_status r = run_eval(ctx, he::EK_MRR_REST_Z, a, count * 2 * level, s)) return r;
+    return run_eval(ctx, he::EK_MRR_REST_OUT, a, count * 2 * level, s);
 }
 
 // ------------------------------------------------------------- measurement

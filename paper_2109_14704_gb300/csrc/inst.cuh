@@ -104,11 +104,13 @@ struct ShapeOps {
     }
             HE_EVAL_CASE(EK_KS_DIGITS, k_ks_digits, sm1)
             HE_EVAL_CASE(EK_KS_MODUP, k_ks_modup, sm3)
+            HE_EVAL_CASE(EK_KS_EXPAND, k_ks_expand, sm1)
             HE_EVAL_CASE(EK_KS_MODDOWN, k_ks_moddown, sm1)
             HE_EVAL_CASE(EK_RS_LIFT, k_rs_lift, sm1)
             HE_EVAL_CASE(EK_RS, k_rs, sm1)
             HE_EVAL_CASE(EK_MRR_LAST, k_mrr_last, sm1)
-            HE_EVAL_CASE(EK_MRR_REST, k_mrr_rest, sm1)
+            HE_EVAL_CASE(EK_MRR_REST_Z, k_mrr_rest_z, sm1)
+            HE_EVAL_CASE(EK_MRR_REST_OUT, k_mrr_rest_out, sm1)
 #undef HE_EVAL_CASE
         default:
             return cudaErrorInvalidValue;

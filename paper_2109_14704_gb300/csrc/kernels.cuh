@@ -255,13 +255,17 @@ __global__ void k_tensor(u64 *out3, const u64 *ct_a, const u64 *ct_b, u32 log_n,
 //                 acc_k[t] = sum_j NTT_t(c2_j mod t) * evk[j][k][t]  (n^2 NTT)
 //                 (for t = q_j the NTT-domain c[2]_j is used as is); on P the
 //                 accumulators are brought back by INTT_P and kept as the
-//                 coefficient-domain residues y_k = [x_k]_P          (2 INTT)
-//   k_ks_moddown  out_k[i] = d_k[i] + (acc_k[q_i] - NTT(r_k mod q_i)) P^-1,
+//                 coefficient-domain residues y_k = [x_k]_P          (2 INTT);
+//                 on the data primes the stored accumulator already holds
+//                 d_k P + acc_k, so that the mod-down needs no d_k:
+//   k_ks_moddown  out_k[i] = d_k[i] + (acc_k[q_i] - NTT(r_k mod q_i)) P^-1
+//                          = (stored acc - NTT(r_k mod q_i)) P^-1,
 //                 r_k the centred lift of y_k                        (2n NTT)
 // RS (Sec. II-A): k_rs_lift brings c_k[q_l] to the coefficient domain
 // (2 INTT), k_rs combines (c_k[q_i] - NTT(r mod q_i)) q_l^-1 (2(n-1) NTT).
 // MulLinRS fuses Mul into the loads and the mod-down of limb q_l with RS's
-// INTT (k_mrr_last), and mod-down with RS for the other limbs (k_mrr_rest).
+// INTT (k_mrr_last), and mod-down with RS for the other limbs (k_mrr_rest_z,
+// k_mrr_rest_out).
 
 // Centred residue of y in [0, m) (|r| <= (m-1)/2) reduced mod q:
 // y mod q, or y mod q - m mod q when y > (m-1)/2. Needs y < 2 q^2.
@@ -275,6 +279,37 @@ __device__ __forceinline__ u64 centred_mod(u64 y, u64 half_m, u64 m_mod_q, const
 // x < 12p (a lazy forward-transform output, see ntt_fwd_block with CANON =
 // false); below 2^64 for a < 2p, so it can go straight into mul_shoup.
 __device__ __forceinline__ u64 lazy_sub(u64 a, u64 x, u64 twelve_p) { return a + twelve_p - x; }
+
+// Epilogue of a lazy forward transform (ntt_fwd_block with CANON = false):
+//   r(e) = (src[P] - x[e]) C mod p,  P = last_pos(e),  C' = Shoup(C),
+// for every word the thread holds, into x. Positions e and e + 1 of the last
+// round are consecutive and 16-byte aligned, so src moves as 16-byte pairs,
+// all of them loaded before the caller stores anything (src may be the
+// output: with alternating loads and stores each store would evict lines
+// the next loads need).
+template <class Sh>
+__device__ __forceinline__ void sub_scale_pairs(u64 (&x)[Sh::E], const u64 *src, u64 C, u64 C_sh,
+                                                const PrimeConst &pc, u32 m, u32 tid)
+{
+    const u64 twelve_p = 3 * pc.four_p;
+    ulonglong2 v[Sh::E / 2];
+#pragma unroll
+    for (int e = 0; e < Sh::E; e += 2) v[e / 2] = *reinterpret_cast<const ulonglong2 *>(src + last_pos<Sh>(m, tid, e));
+#pragma unroll
+    for (int e = 0; e < Sh::E; e += 2) {
+        x[e] = mul_shoup(lazy_sub(v[e / 2].x, x[e], twelve_p), C, C_sh, pc.p);
+        x[e + 1] = mul_shoup(lazy_sub(v[e / 2].y, x[e + 1], twelve_p), C, C_sh, pc.p);
+    }
+}
+
+// x[] to dst at the thread's last-round positions, as 16-byte pairs.
+template <class Sh>
+__device__ __forceinline__ void store_pairs(u64 *dst, const u64 (&x)[Sh::E], u32 m, u32 tid)
+{
+#pragma unroll
+    for (int e = 0; e < Sh::E; e += 2)
+        *reinterpret_cast<ulonglong2 *>(dst + last_pos<Sh>(m, tid, e)) = make_ulonglong2(x[e], x[e + 1]);
+}
 
 // Read-only load (the kernel never writes what it reads through this).
 __device__ __forceinline__ u64 rd(const u64 *p) { return __ldg(reinterpret_cast<const unsigned long long *>(p)); }
@@ -292,6 +327,26 @@ struct DSource {
         if (k == 1) return mad2_mod(rd(ct_a + off), rd(ct_b + per + off), rd(ct_a + per + off), rd(ct_b + off), pc);
         return mul_mod(rd(ct_a + per + off), rd(ct_b + per + off), pc);
     }
+    // d_k at the two positions P, P + 1 (P even), from 16-byte loads.
+    __device__ __forceinline__ ulonglong2 d2(int k, u32 limb, u32 log_n, u32 P, const PrimeConst &pc) const
+    {
+        const size_t off = ((size_t)limb << log_n) + P;
+        auto ld = [](const u64 *q) { return __ldg(reinterpret_cast<const ulonglong2 *>(q)); };
+        if (ct3) return ld(ct3 + k * per + off);
+        ulonglong2 r;
+        if (k == 1) {
+            const ulonglong2 a0 = ld(ct_a + off), a1 = ld(ct_a + per + off);
+            const ulonglong2 b0 = ld(ct_b + off), b1 = ld(ct_b + per + off);
+            r.x = mad2_mod(a0.x, b1.x, a1.x, b0.x, pc);
+            r.y = mad2_mod(a0.y, b1.y, a1.y, b0.y, pc);
+            return r;
+        }
+        const size_t o = (k == 0) ? off : per + off;
+        const ulonglong2 a = ld(ct_a + o), b = ld(ct_b + o);
+        r.x = mul_mod(a.x, b.x, pc);
+        r.y = mul_mod(a.y, b.y, pc);
+        return r;
+    }
 };
 
 __device__ __forceinline__ DSource dsource(const EvalArgs &a, u32 c)
@@ -305,7 +360,7 @@ __device__ __forceinline__ DSource dsource(const EvalArgs &a, u32 c)
 }
 
 template <int LOG_B, int LOG_C, int LOG_E>
-__global__ void __launch_bounds__(NttShape<LOG_B, LOG_C, LOG_E>::T, NttShape<LOG_B, LOG_C, LOG_E>::EVAL_MIN_CTAS)
+__global__ void __launch_bounds__(NttShape<LOG_B, LOG_C, LOG_E>::T, NttShape<LOG_B, LOG_C, LOG_E>::MIN_CTAS)
 k_ks_digits(EvalArgs a)
 {
     using Sh = NttShape<LOG_B, LOG_C, LOG_E>;
@@ -316,10 +371,18 @@ k_ks_digits(EvalArgs a)
     const PrimeConst pc = a.ctx.pc[j];
     const DSource ds = dsource(a, c);
     u64 *out = a.c2 + ((size_t)c * a.n + j) * Sh::N;
+    const u32 tid = threadIdx.x;
     u64 x[Sh::E];
-    auto ld = [&](u32 P) -> u64 { return ds.d(2, j, Sh::LOG_N, P, pc); };
+    // d2 at the thread's inverse-input positions (consecutive pairs)
+#pragma unroll
+    for (int e = 0; e < Sh::E; e += 2) {
+        const ulonglong2 v = ds.d2(2, j, Sh::LOG_N, (u32)last_pos<Sh>(m, tid, e), pc);
+        x[e] = v.x;
+        x[e + 1] = v.y;
+    }
+    auto nold = [&](u32) -> u64 { return 0; };
     auto st = [&](u32 P, u64 v) { out[P] = v; };
-    ntt_inv_block<Sh, false>(smem, m, 0, a.ctx.tw_inv + (size_t)j * Sh::N, pc, ld, st, x);
+    ntt_inv_block<Sh, true>(smem, m, 0, a.ctx.tw_inv + (size_t)j * Sh::N, pc, nold, st, x);
 }
 
 template <int LOG_B, int LOG_C, int LOG_E>
@@ -375,13 +438,16 @@ k_ks_modup(EvalArgs a)
         }
     }
     if (t < n) {
+        const u64 P_mod_q = a.ctx.cst[3 * t + 2];
 #pragma unroll
         for (int k = 0; k < 2; k++) {
             u64 *dst = a.accq + (((size_t)c * 2 + k) * n + t) * Sh::N;
 #pragma unroll
-            for (int e = 0; e < Sh::E; e++)
-                dst[last_pos<Sh>(m, tid, e)] =
-                    reduce_once(reduce_once(acc[(k * Sh::E + e) * Sh::T + tid], pc.two_p), pc.p);
+            for (int e = 0; e < Sh::E; e++) {
+                const int P = last_pos<Sh>(m, tid, e);
+                const u64 s = reduce_once(reduce_once(acc[(k * Sh::E + e) * Sh::T + tid], pc.two_p), pc.p);
+                dst[P] = add_mod(s, mul_mod(ds.d(k, t, Sh::LOG_N, (u32)P, pc), P_mod_q, pc), pc.p);
+            }
         }
     } else {
         // special prime: y_k = INTT_P(acc_k) (inputs in [0, 4p)), kept in the
@@ -399,6 +465,136 @@ k_ks_modup(EvalArgs a)
     }
 }
 
+// Expanded mod-up, first half: one transform per cluster,
+//   X[g][t][j] = NTT_t(c2_j mod t)  for each digit j != t, target t in
+//   {q_0..q_l, P}, ciphertext c = c_first + g of the group,
+// left in the lazy range [0, 12t) (it only feeds Shoup products). The same
+// transforms as k_ks_modup, but as independent launches of the plain
+// transform's size and register budget instead of a sequence inside one
+// accumulating cluster; k_ks_mac then accumulates them with the key.
+// Clusters of the diagonal (j = t) exit at once: there the digit is already
+// in the NTT domain.
+template <int LOG_B, int LOG_C, int LOG_E>
+__global__ void __launch_bounds__(NttShape<LOG_B, LOG_C, LOG_E>::T, NttShape<LOG_B, LOG_C, LOG_E>::MIN_CTAS)
+k_ks_expand(EvalArgs a)
+{
+    using Sh = NttShape<LOG_B, LOG_C, LOG_E>;
+    extern __shared__ __align__(16) u64 smem[];
+    const u32 tid = threadIdx.x;
+    const u32 m = (LOG_C > 0) ? cluster_ctarank() : 0u;
+    const u32 item = blockIdx.x >> LOG_C;
+    const u32 n = a.n;
+    const u32 j = item % n, t = (item / n) % (n + 1), g = item / (n * (n + 1));
+    if (j == t) return;
+    const u32 tp = (t == n) ? a.ctx.n_data : t;
+    const PrimeConst pc = a.ctx.pc[tp];
+    const u64 *src = a.c2 + ((size_t)(a.c_first + g) * n + j) * Sh::N;
+    u64 *dst = a.mx + (size_t)item * Sh::N;
+    const ulonglong2 *twf = a.ctx.tw_fwd + (size_t)tp * Sh::N;
+    u64 x[Sh::E];
+    auto nost = [&](u32, u64) {};
+    // any input below 8t congruent to the digit will do: when q_j <= 8t the
+    // digit c2_j < q_j goes in as it is
+    if (a.ctx.pc[j].p <= (pc.four_p << 1)) {
+        auto ld = [&](int P) -> u64 { return rd(src + P); };
+        ntt_fwd_block<Sh, false>(smem, m, 0, twf, pc, ld, nost, x);
+    } else {
+        auto ld = [&](int P) -> u64 { return barrett_reduce(0, rd(src + P), pc.p, pc.mu, pc.bits); };
+        ntt_fwd_block<Sh, false>(smem, m, 0, twf, pc, ld, nost, x);
+    }
+#pragma unroll
+    for (int e = 0; e < Sh::E; e += 2)
+        *reinterpret_cast<ulonglong2 *>(dst + last_pos<Sh>(m, tid, e)) = make_ulonglong2(x[e], x[e + 1]);
+}
+
+#ifdef HE_MISC_KERNELS
+// Expanded mod-up, second half (elementwise):
+//   acc_k[t] = sum_j X[g][t][j] * evk[j][k][t]   (j = t: the NTT-domain
+//   digit d2_t itself), lazy products in [0, 4t), sums kept in [0, 4t);
+// d_k P + acc_k, canonical, into accq for data targets (as k_ks_modup),
+// acc_k left in [0, 4P) in plift for the special prime (the inverse
+// transform that follows accepts that range).
+// A thread takes two positions of one target for MAC_CTS ciphertexts of the
+// group, so each key word it loads serves MAC_CTS products; two ciphertexts
+// under a 64-register bound (four blocks of 256 per SM) measured fastest
+// (one: fewer key reuses; four: too few warps to cover the loads).
+constexpr u32 MAC_CTS = 2;
+
+__global__ void __launch_bounds__(256, 4) k_ks_mac(EvalArgs a, u32 groups)
+{
+    const u32 n = a.n, N = a.ctx.N;
+    u32 log_n = 0;
+    while ((1u << log_n) < N) log_n++;
+    const u32 chunks = (groups + MAC_CTS - 1) / MAC_CTS;
+    const size_t total = (size_t)chunks * (n + 1) * (N / 2);
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
+        const u32 P = (u32)(q % (N / 2)) * 2;
+        const u32 t = (u32)((q / (N / 2)) % (n + 1));
+        const u32 g0 = (u32)(q / ((size_t)(N / 2) * (n + 1))) * MAC_CTS;
+        const u32 ng = min(MAC_CTS, groups - g0);
+        const u32 tp = (t == n) ? a.ctx.n_data : t;
+        const PrimeConst pc = a.ctx.pc[tp];
+        u64 acc[MAC_CTS][2][2];
+        for (u32 j = 0; j < n; j++) {
+            ulonglong2 w[2][2];
+#pragma unroll
+            for (int k = 0; k < 2; k++) {
+                const ulonglong2 *key = a.evk + (((size_t)j * 2 + k) * (a.ctx.n_data + 1) + tp) * N + P;
+                w[k][0] = __ldg(key);
+                w[k][1] = __ldg(key + 1);
+            }
+#pragma unroll
+            for (u32 gi = 0; gi < MAC_CTS; gi++) {
+                if (gi >= ng) break;
+                const u32 g = g0 + gi;
+                u64 x0, x1;
+                if (j == t) {
+                    const ulonglong2 v = dsource(a, a.c_first + g).d2(2, j, log_n, P, pc);
+                    x0 = v.x;
+                    x1 = v.y;
+                } else {
+                    const ulonglong2 v =
+                        __ldg(reinterpret_cast<const ulonglong2 *>(a.mx + (((size_t)g * (n + 1) + t) * n + j) * N + P));
+                    x0 = v.x;
+                    x1 = v.y;
+                }
+#pragma unroll
+                for (int k = 0; k < 2; k++) {
+                    const u64 p0 = mul_shoup_lazy4_asm(x0, w[k][0].x, w[k][0].y, pc.neg_p);
+                    const u64 p1 = mul_shoup_lazy4_asm(x1, w[k][1].x, w[k][1].y, pc.neg_p);
+                    acc[gi][k][0] = j == 0 ? p0 : reduce_once(acc[gi][k][0] + p0, pc.four_p);
+                    acc[gi][k][1] = j == 0 ? p1 : reduce_once(acc[gi][k][1] + p1, pc.four_p);
+                }
+            }
+        }
+#pragma unroll
+        for (u32 gi = 0; gi < MAC_CTS; gi++) {
+            if (gi >= ng) break;
+            const u32 c = a.c_first + g0 + gi;
+            const DSource ds = dsource(a, c);
+#pragma unroll
+            for (int k = 0; k < 2; k++) {
+                ulonglong2 o;
+                if (t < n) {
+                    // stored as d_k P + acc_k (see the mod-down)
+                    const u64 P_mod_q = a.ctx.cst[3 * t + 2];
+                    const u64 s0 = reduce_once(reduce_once(acc[gi][k][0], pc.two_p), pc.p);
+                    const u64 s1 = reduce_once(reduce_once(acc[gi][k][1], pc.two_p), pc.p);
+                    const ulonglong2 dv = ds.d2(k, t, log_n, P, pc);
+                    o.x = add_mod(s0, mul_mod(dv.x, P_mod_q, pc), pc.p);
+                    o.y = add_mod(s1, mul_mod(dv.y, P_mod_q, pc), pc.p);
+                    *reinterpret_cast<ulonglong2 *>(a.accq + (((size_t)c * 2 + k) * n + t) * N + P) = o;
+                } else {
+                    o.x = acc[gi][k][0];
+                    o.y = acc[gi][k][1];
+                    *reinterpret_cast<ulonglong2 *>(a.plift + ((size_t)c * 2 + k) * N + P) = o;
+                }
+            }
+        }
+    }
+}
+#endif  // HE_MISC_KERNELS
+
 // Relin mod-down (no rescale): out[c][k][i] = d_k[i] + (acc - NTT(r)) P^-1.
 template <int LOG_B, int LOG_C, int LOG_E>
 __global__ void __launch_bounds__(NttShape<LOG_B, LOG_C, LOG_E>::T, NttShape<LOG_B, LOG_C, LOG_E>::EVAL_MIN_CTAS)
@@ -415,7 +611,6 @@ k_ks_moddown(EvalArgs a)
     const PrimeConst pP = a.ctx.pc[a.ctx.n_data];
     const u64 *cst = a.ctx.cst + 3 * i;         // P^-1, Shoup, P mod q_i
     const u64 half_P = (pP.p - 1) / 2;
-    const DSource ds = dsource(a, c);
     const u64 *y = a.plift + ((size_t)c * 2 + k) * Sh::N;
     u64 x[Sh::E];
     auto ld = [&](u32 P) -> u64 { return centred_mod(rd(y + P), half_P, cst[2], pc); };
@@ -423,13 +618,8 @@ k_ks_moddown(EvalArgs a)
     ntt_fwd_block<Sh, false>(smem, m, 0, a.ctx.tw_fwd + (size_t)i * Sh::N, pc, ld, st, x);
     const u64 *accp = a.accq + (((size_t)c * 2 + k) * n + i) * Sh::N;
     u64 *out = a.out + (((size_t)c * 2 + k) * n + i) * Sh::N;
-    const u64 twelve_p = 3 * pc.four_p;
-#pragma unroll
-    for (int e = 0; e < Sh::E; e++) {
-        const u32 P = last_pos<Sh>(m, tid, e);
-        const u64 v = mul_shoup(lazy_sub(rd(accp + P), x[e], twelve_p), cst[0], cst[1], pc.p);
-        out[P] = add_mod(ds.d(k, i, Sh::LOG_N, P, pc), v, pc.p);
-    }
+    sub_scale_pairs<Sh>(x, accp, cst[0], cst[1], pc, m, tid);   // acc holds d P
+    store_pairs<Sh>(out, x, m, tid);
 }
 
 // RS, first half: y_k = INTT_{q_l}(c_k[q_l]) -> lift2 (coefficient domain).
@@ -474,12 +664,8 @@ k_rs(EvalArgs a)
     ntt_fwd_block<Sh, false>(smem, m, 0, a.ctx.tw_fwd + (size_t)i * Sh::N, pc, ld, st, x);
     const u64 *src = a.ct2 + (((size_t)c * 2 + k) * n + i) * Sh::N;
     u64 *out = a.out + (((size_t)c * 2 + k) * l + i) * Sh::N;
-    const u64 twelve_p = 3 * pc.four_p;
-#pragma unroll
-    for (int e = 0; e < Sh::E; e++) {
-        const u32 P = last_pos<Sh>(m, tid, e);
-        out[P] = mul_shoup(lazy_sub(rd(src + P), x[e], twelve_p), cst[0], cst[1], pc.p);
-    }
+    sub_scale_pairs<Sh>(x, src, cst[0], cst[1], pc, m, tid);
+    store_pairs<Sh>(out, x, m, tid);
 }
 
 // MulLinRS, limb q_l: relin output c_k[q_l] = d_k[l] + (acc - NTT(r)) P^-1,
@@ -499,30 +685,32 @@ k_mrr_last(EvalArgs a)
     const PrimeConst pP = a.ctx.pc[a.ctx.n_data];
     const u64 *cst = a.ctx.cst + 3 * l;
     const u64 half_P = (pP.p - 1) / 2;
-    const DSource ds = dsource(a, c);
     const u64 *y = a.plift + ((size_t)c * 2 + k) * Sh::N;
     u64 x[Sh::E];
     auto ld = [&](u32 P) -> u64 { return centred_mod(rd(y + P), half_P, cst[2], pc); };
     auto nost = [&](u32, u64) {};
     ntt_fwd_block<Sh, false>(smem, m, 0, a.ctx.tw_fwd + (size_t)l * Sh::N, pc, ld, nost, x);
     const u64 *accp = a.accq + (((size_t)c * 2 + k) * n + l) * Sh::N;
-    const u64 twelve_p = 3 * pc.four_p;
-#pragma unroll
-    for (int e = 0; e < Sh::E; e++) {
-        const u32 P = last_pos<Sh>(m, tid, e);
-        const u64 v = mul_shoup(lazy_sub(rd(accp + P), x[e], twelve_p), cst[0], cst[1], pc.p);
-        x[e] = add_mod(ds.d(k, l, Sh::LOG_N, P, pc), v, pc.p);
-    }
+    sub_scale_pairs<Sh>(x, accp, cst[0], cst[1], pc, m, tid);   // acc holds d P
     u64 *dst = a.lift2 + ((size_t)c * 2 + k) * Sh::N;
     auto st = [&](u32 P, u64 v) { dst[P] = v; };
     auto nold = [&](u32) -> u64 { return 0; };
     ntt_inv_block<Sh, true>(smem, m, 0, a.ctx.tw_inv + (size_t)l * Sh::N, pc, nold, st, x);
 }
 
-// MulLinRS, limbs i < l: mod-down by P then rescale by q_l, two NTTs.
+// MulLinRS, limbs i < l: mod-down by P, then rescale by q_l, as two launches
+// of one transform each (plain transform size and register budget; one
+// fused kernel holding the first result across the second transform needs
+// twice the registers):
+//   k_mrr_rest_z:   z_k[i] = d_k[i] + (acc_k[i] - NTT_i([y_k]_P)) P^-1
+//                          = (stored acc - NTT_i([y_k]_P)) P^-1 (the mod-up
+//                   stores d_k P + acc_k), written over the accumulator (each
+//                   thread rewrites only the positions it read);
+//   k_mrr_rest_out: out[c][k][i] = (z_k[i] - NTT_i([y2_k]_{q_l})) q_l^-1.
+// Both transforms are left lazy (their outputs only enter Shoup products).
 template <int LOG_B, int LOG_C, int LOG_E>
-__global__ void __launch_bounds__(NttShape<LOG_B, LOG_C, LOG_E>::T, NttShape<LOG_B, LOG_C, LOG_E>::EVAL_MIN_CTAS)
-k_mrr_rest(EvalArgs a)
+__global__ void __launch_bounds__(NttShape<LOG_B, LOG_C, LOG_E>::T, NttShape<LOG_B, LOG_C, LOG_E>::MIN_CTAS)
+k_mrr_rest_z(EvalArgs a)
 {
     using Sh = NttShape<LOG_B, LOG_C, LOG_E>;
     extern __shared__ __align__(16) u64 smem[];
@@ -532,36 +720,43 @@ k_mrr_rest(EvalArgs a)
     const u32 n = a.n, l = n - 1;
     const u32 c = item / (2 * l), k = (item / l) % 2, i = item % l;
     const PrimeConst pc = a.ctx.pc[i];
-    const PrimeConst pP = a.ctx.pc[a.ctx.n_data];
     const u64 *cP = a.ctx.cst + 3 * i;
-    const u64 *cl = a.ctx.cst + 3 * a.ctx.n_data + 3 * ((size_t)l * a.ctx.n_data + i);
-    const u64 half_P = (pP.p - 1) / 2;
-    const u64 half_l = (a.ctx.pc[l].p - 1) / 2;
-    const DSource ds = dsource(a, c);
-    const ulonglong2 *twf = a.ctx.tw_fwd + (size_t)i * Sh::N;
+    const u64 half_P = (a.ctx.pc[a.ctx.n_data].p - 1) / 2;
+    const u64 P_mod_q = cP[2];
     const u64 *y = a.plift + ((size_t)c * 2 + k) * Sh::N;
-    u64 x[Sh::E], z[Sh::E];
+    u64 x[Sh::E];
     auto nost = [&](u32, u64) {};
-    auto ld1 = [&](u32 P) -> u64 { return centred_mod(rd(y + P), half_P, cP[2], pc); };
-    ntt_fwd_block<Sh, false>(smem, m, 0, twf, pc, ld1, nost, x);
-    const u64 *accp = a.accq + (((size_t)c * 2 + k) * n + i) * Sh::N;
-    const u64 twelve_p = 3 * pc.four_p;
-#pragma unroll
-    for (int e = 0; e < Sh::E; e++) {
-        const u32 P = last_pos<Sh>(m, tid, e);
-        const u64 v = mul_shoup(lazy_sub(rd(accp + P), x[e], twelve_p), cP[0], cP[1], pc.p);
-        z[e] = add_mod(ds.d(k, i, Sh::LOG_N, P, pc), v, pc.p);
-    }
-    ntt_barrier<Sh>();
+    auto ld = [&](int P) -> u64 { return centred_mod(rd(y + P), half_P, P_mod_q, pc); };
+    ntt_fwd_block<Sh, false>(smem, m, 0, a.ctx.tw_fwd + (size_t)i * Sh::N, pc, ld, nost, x);
+    u64 *accp = a.accq + (((size_t)c * 2 + k) * n + i) * Sh::N;
+    sub_scale_pairs<Sh>(x, accp, cP[0], cP[1], pc, m, tid);
+    store_pairs<Sh>(accp, x, m, tid);
+}
+
+template <int LOG_B, int LOG_C, int LOG_E>
+__global__ void __launch_bounds__(NttShape<LOG_B, LOG_C, LOG_E>::T, NttShape<LOG_B, LOG_C, LOG_E>::MIN_CTAS)
+k_mrr_rest_out(EvalArgs a)
+{
+    using Sh = NttShape<LOG_B, LOG_C, LOG_E>;
+    extern __shared__ __align__(16) u64 smem[];
+    const u32 tid = threadIdx.x;
+    const u32 m = (LOG_C > 0) ? cluster_ctarank() : 0u;
+    const u32 item = blockIdx.x >> LOG_C;
+    const u32 n = a.n, l = n - 1;
+    const u32 c = item / (2 * l), k = (item / l) % 2, i = item % l;
+    const PrimeConst pc = a.ctx.pc[i];
+    const u64 *cl = a.ctx.cst + 3 * a.ctx.n_data + 3 * ((size_t)l * a.ctx.n_data + i);
+    const u64 half_l = (a.ctx.pc[l].p - 1) / 2;
+    const u64 ql_mod_q = cl[2];
     const u64 *y2 = a.lift2 + ((size_t)c * 2 + k) * Sh::N;
-    auto ld2 = [&](u32 P) -> u64 { return centred_mod(rd(y2 + P), half_l, cl[2], pc); };
-    ntt_fwd_block<Sh, false>(smem, m, 0, twf, pc, ld2, nost, x);
+    u64 x[Sh::E];
+    auto nost = [&](u32, u64) {};
+    auto ld = [&](int P) -> u64 { return centred_mod(rd(y2 + P), half_l, ql_mod_q, pc); };
+    ntt_fwd_block<Sh, false>(smem, m, 0, a.ctx.tw_fwd + (size_t)i * Sh::N, pc, ld, nost, x);
+    const u64 *zp = a.accq + (((size_t)c * 2 + k) * n + i) * Sh::N;
     u64 *out = a.out + (((size_t)c * 2 + k) * l + i) * Sh::N;
-#pragma unroll
-    for (int e = 0; e < Sh::E; e++) {
-        const u32 P = last_pos<Sh>(m, tid, e);
-        out[P] = mul_shoup(lazy_sub(z[e], x[e], twelve_p), cl[0], cl[1], pc.p);
-    }
+    sub_scale_pairs<Sh>(x, zp, cl[0], cl[1], pc, m, tid);
+    store_pairs<Sh>(out, x, m, tid);
 }
 
 }  // namespace he

@@ -69,19 +69,24 @@ struct EvalArgs {
     u64 *plift;                 // scratch [count][2][N]
     u64 *lift2;                 // scratch [count][2][N]
     const ulonglong2 *evk;      // [n_data][2][n_data + 1][N] (value, Shoup)
+    u64 *mx;                    // expanded mod-up scratch [group][n + 1][n][N]
     u32 n;                      // limbs at the current level
     u32 count;
+    u32 c_first;                // first ciphertext of the expanded mod-up group
+    u32 pad;
     DevCtx ctx;
 };
 
 enum EvalKernel {
     EK_KS_DIGITS = 0,
     EK_KS_MODUP,
+    EK_KS_EXPAND,
     EK_KS_MODDOWN,
     EK_RS_LIFT,
     EK_RS,
     EK_MRR_LAST,
-    EK_MRR_REST,
+    EK_MRR_REST_Z,
+    EK_MRR_REST_OUT,
     EK_COUNT
 };
 

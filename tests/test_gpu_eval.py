@@ -22,6 +22,16 @@ CHAINS = {
 }
 
 
+def _relin_min_bytes(N, level):
+    """The fused mod-up's minimum scratch, (3 n + 2) N words."""
+    return (3 * (level + 1) + 2) * N * 8
+
+
+def _mrr_min_bytes(N, level, count):
+    """The fused mod-up's minimum MulLinRS scratch, (3 n + 4) N words a pair."""
+    return (3 * (level + 1) + 4) * N * 8 * count
+
+
 def _setup(name, seed):
     N, bits, pbits = CHAINS[name]
     data, P = he.chain_primes(N, bits, pbits)
@@ -44,16 +54,18 @@ def test_ct_mul(name, level):
     assert np.array_equal(host(out), oracle.tensor(ca, cb, qs))
 
 
+@pytest.mark.parametrize("modup", ["expanded", "fused"])
 @pytest.mark.parametrize("log_e", [4, 3])
 @pytest.mark.parametrize("name,level", [("ckks16k", 6), ("ckks16k", 2), ("matrix8k", 2), ("small4k", 0),
                                         ("small4k", 3)])
-def test_relin(name, level, log_e):
+def test_relin(name, level, log_e, modup):
     N, data, P, ctx, evk, key, r = _setup(name, 20 + level)
     ctx.set_eval_shape(log_e)
     qs = data[:level + 1]
     c3 = np.stack([r.uniform_limbs(qs, N) for _ in range(3)])
     out = empty(2, level + 1, N)
-    scratch = empty(ctx.relin_scratch_bytes(level) // 8)
+    nbytes = ctx.relin_scratch_bytes(level) if modup == "expanded" else _relin_min_bytes(N, level)
+    scratch = empty(nbytes // 8)
     he.relin(out, dev(c3), key, ctx, level, scratch)
     assert np.array_equal(host(out), oracle.relin(c3, evk, data, P, level))
 
@@ -71,18 +83,39 @@ def test_rescale(name, level, log_e):
     assert np.array_equal(host(out), oracle.rescale(c, data, level))
 
 
+@pytest.mark.parametrize("modup", ["expanded", "fused"])
 @pytest.mark.parametrize("log_e", [4, 3])
 @pytest.mark.parametrize("name,level,count", [("ckks16k", 6, 3), ("ckks16k", 2, 2), ("matrix8k", 2, 5),
                                               ("small4k", 1, 4), ("small4k", 3, 1)])
-def test_mul_relin_rescale_batch(name, level, count, log_e):
+def test_mul_relin_rescale_batch(name, level, count, log_e, modup):
     N, data, P, ctx, evk, key, r = _setup(name, 40 + level + count)
     ctx.set_eval_shape(log_e)
     qs = data[:level + 1]
     ca = np.stack([np.stack([r.uniform_limbs(qs, N) for _ in range(2)]) for _ in range(count)])
     cb = np.stack([np.stack([r.uniform_limbs(qs, N) for _ in range(2)]) for _ in range(count)])
     out = empty(count, 2, level, N)
-    scratch = empty(ctx.mrr_scratch_bytes(level, count) // 8)
+    nbytes = ctx.mrr_scratch_bytes(level, count) if modup == "expanded" else _mrr_min_bytes(N, level, count)
+    scratch = empty(nbytes // 8)
     he.mul_relin_rescale(out, dev(ca), dev(cb), count, key, ctx, level, scratch)
+    got = host(out)
+    for c in range(count):
+        assert np.array_equal(got[c], oracle.mul_relin_rescale(ca[c], cb[c], evk, data, P, level)), c
+
+
+@pytest.mark.parametrize("extra_polys", [11, 12, 36, 96])
+def test_expanded_modup_groups(extra_polys):
+    """11 pairs at level 2 (n = 3 limbs) with `extra_polys` x N words of
+    scratch beyond the fused minimum: 11 holds no mod-up expansion
+    ((n + 1) n = 12 per pair), so the fused mod-up runs; 12, 36 and 96 hold
+    1, 3 and 8 (ragged last group). Same limbs as the oracle."""
+    N, data, P, ctx, evk, key, r = _setup("small4k", 60 + extra_polys)
+    level, count = 2, 11
+    qs = data[:level + 1]
+    ca = np.stack([np.stack([r.uniform_limbs(qs, N) for _ in range(2)]) for _ in range(count)])
+    cb = np.stack([np.stack([r.uniform_limbs(qs, N) for _ in range(2)]) for _ in range(count)])
+    out = empty(count, 2, level, N)
+    nbytes = _mrr_min_bytes(N, level, count) + extra_polys * N * 8 + 8 * 5
+    he.mul_relin_rescale(out, dev(ca), dev(cb), count, key, ctx, level, empty(nbytes // 8))
     got = host(out)
     for c in range(count):
         assert np.array_equal(got[c], oracle.mul_relin_rescale(ca[c], cb[c], evk, data, P, level)), c
