@@ -558,8 +558,14 @@ def bench_serving(args):
     launch (one slot, one stream)."""
     from paper_2109_14704_gb300 import serving
 
+    import torch
+
     out = {"workload": "Poisson 2000 req/s, N in {8192,16384,32768}, levels 2-16, budget 64 GB"}
     for name, kw in (("batched", dict(slots=16, streams=4)), ("plain", dict(slots=1, streams=1))):
+        # every server starts from an empty allocator cache (the previous
+        # phases' freed blocks would otherwise count against device memory)
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
         srv = serving.Server(pool_per_bucket=1, seed=5, **kw)
         srv.run(srv.make_requests(300, rate=2000.0, seed=55))              # warm-up
         srv.completed.clear()
@@ -571,7 +577,10 @@ def bench_serving(args):
         sat = srv.run(srv.make_requests(args.serve_requests, rate=1e6, seed=6))
         out[name]["saturated_throughput_per_s"] = sat["throughput_per_s"]
         out[name]["saturated_mean_batch"] = sat["mean_batch"]
+        out[name]["expand_group"] = srv.expand_group
         del srv
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
     return out
 
 

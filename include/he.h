@@ -205,6 +205,11 @@ he_status he_rescale(uint64_t *ct_out, const uint64_t *ct_in, const he_context *
  * [count][2][l][N]. The two roundings (by P, then by q_l) stay separate, so
  * the result equals he_rescale(he_relin(he_ct_mul(a, b))). */
 size_t he_mul_relin_rescale_scratch_bytes(const he_context *ctx, uint32_t level, uint32_t count);
+/* Scratch bytes for `count` pairs with the mod-up expanded in groups of at
+ * most expand_group ciphertexts (0: the fused mod-up's minimum); the plain
+ * query above uses groups of 64. Smaller groups trade speed for memory. */
+size_t he_mul_relin_rescale_scratch_bytes_ex(const he_context *ctx, uint32_t level, uint32_t count,
+                                             uint32_t expand_group);
 he_status he_mul_relin_rescale(uint64_t *ct_out, const uint64_t *ct_a, const uint64_t *ct_b,
                                uint32_t count, const he_relin_key *key, const he_context *ctx,
                                uint32_t level, void *scratch, size_t scratch_bytes,

@@ -682,10 +682,17 @@ extern "C" size_t he_rescale_scratch_bytes(const he_context *ctx, uint32_t level
     return ctx ? rescale_words(ctx) * 8 : 0;
 }
 
-extern "C" size_t he_mul_relin_rescale_scratch_bytes(const he_context *ctx, uint32_t level, uint32_t count)
+extern "C" size_t he_mul_relin_rescale_scratch_bytes_ex(const he_context *ctx, uint32_t level, uint32_t count,
+                                                        uint32_t expand_group)
 {
     if (!ctx || !count) return 0;
-    return (mrr_words(ctx, level + 1) * count + modup_x_words(ctx, level + 1, std::min(count, kModupGroup))) * 8;
+    const u32 group = std::min({count, kModupGroup, expand_group});
+    return (mrr_words(ctx, level + 1) * count + modup_x_words(ctx, level + 1, group)) * 8;
+}
+
+extern "C" size_t he_mul_relin_rescale_scratch_bytes(const he_context *ctx, uint32_t level, uint32_t count)
+{
+    return he_mul_relin_rescale_scratch_bytes_ex(ctx, level, count, kModupGroup);
 }
 
 static he_status run_eval(const he_context *ctx, he::EvalKernel k, const he::EvalArgs &a, u32 items,

@@ -68,6 +68,8 @@ _SIGS = {
     "he_rescale_scratch_bytes": (ctypes.c_size_t, [_vp, ctypes.c_uint32]),
     "he_rescale": (ctypes.c_int32, [_vp, _vp, _vp, ctypes.c_uint32, _vp, ctypes.c_size_t, _vp]),
     "he_mul_relin_rescale_scratch_bytes": (ctypes.c_size_t, [_vp, ctypes.c_uint32, ctypes.c_uint32]),
+    "he_mul_relin_rescale_scratch_bytes_ex": (ctypes.c_size_t, [_vp, ctypes.c_uint32, ctypes.c_uint32,
+                                                                ctypes.c_uint32]),
     "he_mul_relin_rescale": (ctypes.c_int32, [_vp, _vp, _vp, ctypes.c_uint32, _vp, _vp, ctypes.c_uint32, _vp,
                                               ctypes.c_size_t, _vp]),
     "he_ntt_plan_create": (ctypes.c_int32, [ctypes.POINTER(PolyDesc), ctypes.c_uint32, ctypes.POINTER(NttShape),
@@ -125,8 +127,11 @@ def _check(status: int):
         raise HeError(status, last_error())
 
 
-def _ptr(x):
-    """Device pointer of a torch tensor (or an int address, or None)."""
+def _ptr(x, words: int | None = None):
+    """Device pointer of a torch tensor (or an int address, or None). With
+    `words`, the tensor must hold at least that many 64-bit words: the C ABI
+    takes bare pointers, so the binding is where a short buffer is caught
+    (an int address is passed through unchecked)."""
     if x is None:
         return None
     if isinstance(x, int):
@@ -137,6 +142,8 @@ def _ptr(x):
         raise ValueError("expected a contiguous tensor")
     if x.element_size() != 8:
         raise ValueError("expected 64-bit words (int64 or uint64)")
+    if words is not None and x.numel() < words:
+        raise ValueError(f"device tensor holds {x.numel()} words, the call needs {words}")
     return x.data_ptr()
 
 
@@ -233,12 +240,12 @@ def _moduli_arg(tables: NttTables, limbs: int, moduli):
 
 def ntt_fwd(poly, N, limbs, count, tables: NttTables, moduli=None, stream=None):
     m = _moduli_arg(tables, limbs, moduli)
-    _check(load().he_ntt_fwd(_ptr(poly), N, limbs, count, _hp(m), tables.handle, _stream(stream)))
+    _check(load().he_ntt_fwd(_ptr(poly, N * limbs * count), N, limbs, count, _hp(m), tables.handle, _stream(stream)))
 
 
 def ntt_inv(poly, N, limbs, count, tables: NttTables, moduli=None, stream=None):
     m = _moduli_arg(tables, limbs, moduli)
-    _check(load().he_ntt_inv(_ptr(poly), N, limbs, count, _hp(m), tables.handle, _stream(stream)))
+    _check(load().he_ntt_inv(_ptr(poly, N * limbs * count), N, limbs, count, _hp(m), tables.handle, _stream(stream)))
 
 
 NTT_OP_FORWARD, NTT_OP_INVERSE = 1, 2
@@ -277,17 +284,18 @@ def ntt_host(inp, out, N, limbs, count, tables: NttTables, ops, work, moduli=Non
 
 def ntt_fwd_naive(poly, N, limbs, count, tables: NttTables, moduli=None, stream=None):
     m = _moduli_arg(tables, limbs, moduli)
-    _check(load().he_ntt_fwd_naive(_ptr(poly), N, limbs, count, _hp(m), tables.handle, _stream(stream)))
+    _check(load().he_ntt_fwd_naive(_ptr(poly, N * limbs * count), N, limbs, count, _hp(m), tables.handle, _stream(stream)))
 
 
 def ntt_inv_naive(poly, N, limbs, count, tables: NttTables, moduli=None, stream=None):
     m = _moduli_arg(tables, limbs, moduli)
-    _check(load().he_ntt_inv_naive(_ptr(poly), N, limbs, count, _hp(m), tables.handle, _stream(stream)))
+    _check(load().he_ntt_inv_naive(_ptr(poly, N * limbs * count), N, limbs, count, _hp(m), tables.handle, _stream(stream)))
 
 
 def dyadic_mul(out, a, b, N, limbs, count, tables: NttTables, moduli=None, stream=None):
     m = _moduli_arg(tables, limbs, moduli)
-    _check(load().he_dyadic_mul(_ptr(out), _ptr(a), _ptr(b), N, limbs, count, _hp(m), tables.handle,
+    w = N * limbs * count
+    _check(load().he_dyadic_mul(_ptr(out, w), _ptr(a, w), _ptr(b, w), N, limbs, count, _hp(m), tables.handle,
                                 _stream(stream)))
 
 
@@ -318,8 +326,12 @@ class Context:
     def rescale_scratch_bytes(self, level: int) -> int:
         return int(load().he_rescale_scratch_bytes(self.handle, level))
 
-    def mrr_scratch_bytes(self, level: int, count: int) -> int:
-        return int(load().he_mul_relin_rescale_scratch_bytes(self.handle, level, count))
+    def mrr_scratch_bytes(self, level: int, count: int, expand_group: int | None = None) -> int:
+        """Scratch bytes of mul_relin_rescale; expand_group bounds the
+        expanded mod-up's group (0: the fused minimum, None: the default)."""
+        if expand_group is None:
+            return int(load().he_mul_relin_rescale_scratch_bytes(self.handle, level, count))
+        return int(load().he_mul_relin_rescale_scratch_bytes_ex(self.handle, level, count, expand_group))
 
     def close(self):
         if getattr(self, "handle", None):
@@ -359,23 +371,28 @@ class RelinKey:
 
 
 def ct_mul(out3, ct_a, ct_b, ctx: Context, level: int, stream=None):
-    _check(load().he_ct_mul(_ptr(out3), _ptr(ct_a), _ptr(ct_b), ctx.handle, level, _stream(stream)))
+    w = (level + 1) * ctx.N
+    _check(load().he_ct_mul(_ptr(out3, 3 * w), _ptr(ct_a, 2 * w), _ptr(ct_b, 2 * w), ctx.handle, level,
+                            _stream(stream)))
 
 
 def relin(ct_out2, ct_in3, key: RelinKey, ctx: Context, level: int, scratch, stream=None):
-    _check(load().he_relin(_ptr(ct_out2), _ptr(ct_in3), key.handle, ctx.handle, level, _ptr(scratch),
+    w = (level + 1) * ctx.N
+    _check(load().he_relin(_ptr(ct_out2, 2 * w), _ptr(ct_in3, 3 * w), key.handle, ctx.handle, level, _ptr(scratch),
                            scratch.numel() * 8, _stream(stream)))
 
 
 def rescale(ct_out, ct_in, ctx: Context, level: int, scratch, stream=None):
-    _check(load().he_rescale(_ptr(ct_out), _ptr(ct_in), ctx.handle, level, _ptr(scratch), scratch.numel() * 8,
+    _check(load().he_rescale(_ptr(ct_out, 2 * level * ctx.N), _ptr(ct_in, 2 * (level + 1) * ctx.N), ctx.handle,
+                             level, _ptr(scratch), scratch.numel() * 8,
                              _stream(stream)))
 
 
 def mul_relin_rescale(ct_out, ct_a, ct_b, count: int, key: RelinKey, ctx: Context, level: int, scratch,
                       stream=None):
-    _check(load().he_mul_relin_rescale(_ptr(ct_out), _ptr(ct_a), _ptr(ct_b), count, key.handle, ctx.handle, level,
-                                       _ptr(scratch), scratch.numel() * 8, _stream(stream)))
+    w_in, w_out = count * 2 * (level + 1) * ctx.N, count * 2 * level * ctx.N
+    _check(load().he_mul_relin_rescale(_ptr(ct_out, w_out), _ptr(ct_a, w_in), _ptr(ct_b, w_in), count, key.handle,
+                                       ctx.handle, level, _ptr(scratch), scratch.numel() * 8, _stream(stream)))
 
 
 class NttPlan:
@@ -386,7 +403,7 @@ class NttPlan:
         arr = (PolyDesc * max(len(polys), 1))()
         self._keep = []
         for i, (data, tables, N, limbs, first) in enumerate(polys):
-            arr[i].data = _ptr(data)
+            arr[i].data = _ptr(data, N * limbs)
             arr[i].tables = tables.handle.value
             arr[i].N = N
             arr[i].limbs = limbs
@@ -439,11 +456,13 @@ def mul_relin_rescale_noalloc(ct_out, ct_a, ct_b, count: int, key: RelinKey, ctx
     device memory at call time (stream capture, allocator-free serving paths,
     externally budgeted memory): the library's built-in buffer is used.
     Calls that can overlap on the GPU share that buffer and must be ordered."""
-    _check(load().he_mul_relin_rescale_noalloc(_ptr(ct_out), _ptr(ct_a), _ptr(ct_b), count, key.handle, ctx.handle,
-                                               level, _stream(stream)))
+    w_in, w_out = count * 2 * (level + 1) * ctx.N, count * 2 * level * ctx.N
+    _check(load().he_mul_relin_rescale_noalloc(_ptr(ct_out, w_out), _ptr(ct_a, w_in), _ptr(ct_b, w_in), count,
+                                               key.handle, ctx.handle, level, _stream(stream)))
 
 
 def butterfly_apply(x, y, w, w_shoup, p: int, inverse: bool = False, stream=None):
     """Apply the transform butterfly elementwise (device arrays, in place)."""
-    _check(load().he_butterfly_apply(_ptr(x), _ptr(y), _ptr(w), _ptr(w_shoup), x.numel(), p, int(inverse),
+    n = x.numel()
+    _check(load().he_butterfly_apply(_ptr(x), _ptr(y, n), _ptr(w, n), _ptr(w_shoup, n), n, p, int(inverse),
                                      _stream(stream)))

@@ -25,7 +25,9 @@ buffers come from a memory cache that reuses any free buffer large enough
 """
 from __future__ import annotations
 
+import bisect
 import collections
+import math
 import statistics
 import time
 from dataclasses import dataclass, field
@@ -37,28 +39,50 @@ from .synth import Rng
 
 
 class DeviceMemoryCache:
-    """Device buffer pool: allocate reuses any free buffer with capacity at
-    least the request (smallest such first), else allocates; free returns a
-    buffer to the pool. `reserved` (bytes held, free or in use) is what the
-    admission ledger counts; free buffers can be evicted to make room."""
+    """Device buffer pool: allocate reuses the smallest free buffer with
+    capacity at least the request, else allocates; free returns a buffer to
+    the pool. `reserved` (bytes held, free or in use) is what the admission
+    ledger counts; free buffers can be evicted to make room.
 
-    def __init__(self, device):
+    Free buffers stay sorted by capacity, so a pick is a binary search (the
+    serving loop runs on one host thread and may hold thousands of buffers).
+    With size_classes, new buffers are rounded up to the next of the sizes
+    2^(k/4) words (at most 19 % slack), so that a buffer freed by one
+    (N, level) bucket serves its neighbours instead of each bucket growing
+    its own."""
+
+    def __init__(self, device, size_classes: bool = False):
         import torch
         self.torch = torch
         self.device = device
-        self.free_list: list = []          # (capacity_words, tensor)
+        self.size_classes = size_classes
+        self._free: list = []              # sorted (capacity_words, seq, tensor)
+        self._seq = 0
         self.reserved = 0                  # bytes held by the cache (free + in use)
         self.in_use = 0
         self.hits = 0
         self.misses = 0
         self.evicted = 0
 
+    @property
+    def free_list(self):
+        return [(cap, t) for cap, _, t in self._free]
+
+    def _capacity(self, words: int) -> int:
+        if not self.size_classes or words <= 256:
+            return words
+        k = math.ceil(4 * math.log2(words))
+        while 2 ** ((k - 1) / 4) >= words:     # guard the float rounding
+            k -= 1
+        return int(math.ceil(2 ** (k / 4) / 256)) * 256
+
     def _pick(self, words, taken):
-        best = None
-        for i, (cap, _) in enumerate(self.free_list):
-            if i not in taken and cap >= words and (best is None or cap < self.free_list[best][0]):
-                best = i
-        return best
+        """Index into the free list of the smallest buffer of >= words
+        words that is not in `taken`, or None."""
+        i = bisect.bisect_left(self._free, (words, -1))
+        while i < len(self._free) and i in taken:
+            i += 1
+        return i if i < len(self._free) else None
 
     def growth(self, words_list) -> int:
         """Bytes of new memory that allocating all of words_list would add."""
@@ -66,29 +90,27 @@ class DeviceMemoryCache:
         for w in words_list:
             i = self._pick(w, taken)
             if i is None:
-                grow += w * 8
+                grow += self._capacity(w) * 8
             else:
                 taken.add(i)
         return grow
 
     def allocate_within(self, words_list, limit_bytes: int, base_bytes: int = 0):
         """Allocate every request of words_list so that base_bytes + reserved
-        stays within limit_bytes, evicting free buffers when that makes room;
-        None (and nothing allocated) if it cannot."""
+        stays within limit_bytes, evicting free buffers (largest first) when
+        that makes room; None (and nothing allocated) if it cannot."""
         while base_bytes + self.reserved + self.growth(words_list) > limit_bytes:
-            if not self.free_list:
-                return None
-            # evict the largest free buffer not needed by this request
             taken = set()
             for w in words_list:
                 i = self._pick(w, taken)
                 if i is not None:
                     taken.add(i)
-            spare = [i for i in range(len(self.free_list)) if i not in taken]
-            if not spare:
+            j = len(self._free) - 1
+            while j >= 0 and j in taken:
+                j -= 1
+            if j < 0:
                 return None
-            j = max(spare, key=lambda i: self.free_list[i][0])
-            cap, _ = self.free_list.pop(j)
+            cap, _, _ = self._free.pop(j)
             self.reserved -= cap * 8
             self.evicted += 1
         return [self.allocate(w) for w in words_list]
@@ -96,11 +118,11 @@ class DeviceMemoryCache:
     def allocate(self, words: int):
         best = self._pick(words, set())
         if best is not None:
-            cap, t = self.free_list.pop(best)
+            cap, _, t = self._free.pop(best)
             self.hits += 1
         else:
-            t = self.torch.empty(words, dtype=self.torch.int64, device=self.device)
-            cap = words
+            cap = self._capacity(words)
+            t = self.torch.empty(cap, dtype=self.torch.int64, device=self.device)
             self.reserved += cap * 8
             self.misses += 1
         self.in_use += cap * 8
@@ -108,7 +130,8 @@ class DeviceMemoryCache:
 
     def free(self, cap: int, t):
         self.in_use -= cap * 8
-        self.free_list.append((cap, t))
+        self._seq += 1
+        bisect.insort(self._free, (cap, self._seq, t))
 
 
 @dataclass
@@ -139,7 +162,7 @@ class Server:
     """MulLinRS server over degrees `degrees` and levels [min_level, max_level]."""
 
     def __init__(self, degrees=(8192, 16384, 32768), min_level=2, max_level=16, budget_bytes=64 << 30,
-                 slots=16, streams=4, max_wait_s=0.002, pool_per_bucket=2, seed=5, device=None):
+                 slots=16, streams=4, max_wait_s=0.002, pool_per_bucket=2, seed=5, device=None, expand_group=4):
         import torch
         self.torch = torch
         self.device = device or torch.device("cuda", torch.cuda.current_device())
@@ -150,7 +173,10 @@ class Server:
         self.max_wait = max_wait_s
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(streams)]
         self.busy = {i: None for i in range(streams)}
-        self.cache = DeviceMemoryCache(self.device)
+        self.cache = DeviceMemoryCache(self.device, size_classes=True)
+        # key-switching mod-up expanded in groups of at most this many
+        # ciphertexts (bounds a batch's scratch; 0 = the fused minimum)
+        self.expand_group = expand_group
         self.rng = Rng(seed)
         self.ctx, self.key, self.moduli = {}, {}, {}
         self.static_bytes = 0
@@ -187,7 +213,8 @@ class Server:
     def _batch_words(self, N, lvl, cap):
         n = lvl + 1
         ct_in = 2 * n * N
-        return [cap * ct_in, cap * ct_in, cap * 2 * lvl * N, self.ctx[N].mrr_scratch_bytes(lvl, cap) // 8]
+        return [cap * ct_in, cap * ct_in, cap * 2 * lvl * N,
+                self.ctx[N].mrr_scratch_bytes(lvl, cap, self.expand_group) // 8]
 
     def _open_batch(self, key, now):
         N, lvl = key
@@ -336,7 +363,8 @@ class Server:
         N, lvl = req.N, req.level
         src = self.pool[(N, lvl)][req.src].to(self.device)
         out = torch.empty(2 * lvl * N, dtype=torch.int64, device=self.device)
-        scratch = torch.empty(self.ctx[N].mrr_scratch_bytes(lvl, 1) // 8, dtype=torch.int64, device=self.device)
+        scratch = torch.empty(self.ctx[N].mrr_scratch_bytes(lvl, 1, self.expand_group) // 8, dtype=torch.int64,
+                              device=self.device)
         he.mul_relin_rescale(out, src[0].contiguous(), src[1].contiguous(), 1, self.key[N], self.ctx[N], lvl, scratch)
         torch.cuda.synchronize()
         return out.cpu()

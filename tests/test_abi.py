@@ -101,3 +101,16 @@ def test_error_type():
     with pytest.raises(he.HeError) as e:
         he.primes_generate(61, 8192, 1)
     assert e.value.status == he.HE_EINVAL
+
+
+def test_binding_rejects_short_device_buffers():
+    """The C ABI takes bare pointers; the binding checks every tensor against
+    the words the call will touch before anything is launched."""
+    import types
+    fake = types.SimpleNamespace(is_cuda=True, is_contiguous=lambda: True, element_size=lambda: 8,
+                                 numel=lambda: 99, data_ptr=lambda: 4096)
+    assert he._ptr(fake) == 4096
+    assert he._ptr(fake, 99) == 4096
+    with pytest.raises(ValueError, match="needs 100"):
+        he._ptr(fake, 100)
+    assert he._ptr(12345, 1 << 40) == 12345      # raw addresses pass unchecked

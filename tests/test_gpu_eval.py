@@ -95,6 +95,7 @@ def test_mul_relin_rescale_batch(name, level, count, log_e, modup):
     cb = np.stack([np.stack([r.uniform_limbs(qs, N) for _ in range(2)]) for _ in range(count)])
     out = empty(count, 2, level, N)
     nbytes = ctx.mrr_scratch_bytes(level, count) if modup == "expanded" else _mrr_min_bytes(N, level, count)
+    assert _mrr_min_bytes(N, level, count) == ctx.mrr_scratch_bytes(level, count, 0)
     scratch = empty(nbytes // 8)
     he.mul_relin_rescale(out, dev(ca), dev(cb), count, key, ctx, level, scratch)
     got = host(out)

@@ -42,3 +42,26 @@ def test_allocate_within_budget_evicts_free_buffers():
     before = (c.reserved, c.in_use)
     assert c.allocate_within([100], limit_bytes=300 * 8) is None
     assert (c.reserved, c.in_use) == before
+
+
+def test_size_classes_round_up_and_serve_neighbours():
+    c = DeviceMemoryCache(torch.device("cpu"), size_classes=True)
+    for words in (1000, 4096, 5000, 123457, 1 << 20):
+        cap = c._capacity(words)
+        # the next quarter-octave size (rounded to 256 words): at most 19 % slack
+        assert words <= cap <= words * 2 ** 0.25 + 256 and cap % 256 == 0
+    assert c._capacity(100) == 100            # small requests stay exact
+    a = c.allocate(5000)
+    c.free(*a)
+    b = c.allocate(5100)                      # a neighbouring size reuses it
+    assert b[0] == a[0] and c.hits == 1 and c.misses == 1
+
+
+def test_many_free_buffers_pick_smallest_sufficient():
+    c = DeviceMemoryCache(torch.device("cpu"))
+    bufs = [c.allocate(w) for w in range(1000, 3000, 7)]
+    for b in reversed(bufs):
+        c.free(*b)
+    cap, _ = c.allocate(2000)
+    assert cap == min(w for w in range(1000, 3000, 7) if w >= 2000)
+    assert [x for x, _ in c.free_list] == sorted(x for x, _ in c.free_list)
