@@ -520,7 +520,9 @@ def bench_uneven(args, stream, barrier):
 
 def bench_matrix(args, stream, barrier):
     """Element-wise product of two 32 x 32 matrices of ciphertexts: 1024
-    MulLinRS at N = 8192, data primes 60/40/40, special prime 60, one call."""
+    MulLinRS at N = 8192, data primes 60/40/40, special prime 60, one call;
+    and the encrypted matrix product C += A B (32x32x32 and the paper's
+    100x100x1 and 10x9x8) at the same parameters."""
     import numpy as np
     import torch
 
@@ -546,22 +548,55 @@ def bench_matrix(args, stream, barrier):
         he.mul_relin_rescale(out, A, B, count, key, ctx, L, scratch, stream=stream)
 
     ms = _time_steps(step, args.steps, args.warmup, stream, barrier)
-    return {"workload": "32x32 element-wise, N=8192, primes 60/40/40 + 60, 1024 MulLinRS per step",
-            "ms_per_step": ms, "mul_relin_rescale_per_s": count / (ms / 1e3),
-            "eval_log_thread_words": tune["log_thread_words"]}
+    res = {"workload": "32x32 element-wise, N=8192, primes 60/40/40 + 60, 1024 MulLinRS per step",
+           "ms_per_step": ms, "mul_relin_rescale_per_s": count / (ms / 1e3),
+           "eval_log_thread_words": tune["log_thread_words"]}
+    del A, B, out, scratch
+    # the encrypted matrix product C += A B (matMul_mxnxk): tensors
+    # accumulated over k, one relin + rescale per output, add into C
+    res["matmul"] = {}
+    for (m, k, n) in ((32, 32, 32), (100, 100, 1), (10, 9, 8)):
+        Am = torch.from_numpy(np.stack([np.stack([r.uniform_limbs(data, N) for _ in range(2)])
+                                        for _ in range(m * k)]).view(np.int64)).cuda()
+        Bm = torch.from_numpy(np.stack([np.stack([r.uniform_limbs(data, N) for _ in range(2)])
+                                        for _ in range(k * n)]).view(np.int64)).cuda()
+        Cm = torch.from_numpy(np.stack([np.stack([r.uniform_limbs(data[:L], N) for _ in range(2)])
+                                        for _ in range(m * n)]).view(np.int64)).cuda()
+        T = torch.empty((m * n, 3, L + 1, N), dtype=torch.int64, device="cuda")
+        R = torch.empty((m * n, 2, L, N), dtype=torch.int64, device="cuda")
+        sc = torch.empty(ctx.mrr_scratch_bytes(L, m * n) // 8, dtype=torch.int64, device="cuda")
+
+        def t_step():
+            he.ct_matmul_tensor(T, Am, Bm, m, k, n, ctx, L, stream=stream)
+
+        def mm_step():
+            t_step()
+            he.relin_rescale(R, T, m * n, key, ctx, L, sc, stream=stream)
+            he.ct_add(Cm, Cm, R, m * n, 2, ctx, L - 1, stream=stream)
+
+        ms_t = _time_steps(t_step, max(3, args.steps // 2), 2, stream, barrier)
+        ms_mm = _time_steps(mm_step, max(3, args.steps // 2), 2, stream, barrier)
+        res["matmul"][f"{m}x{k}x{n}"] = {
+            "ms_per_matmul": ms_mm, "ms_tensor": ms_t, "tensor_products": m * k * n,
+            "relin_rescale_outputs": m * n,
+            "tensor_products_per_s": m * k * n / (ms_t / 1e3)}
+        del Am, Bm, Cm, T, R, sc
+    return res
 
 
 def bench_serving(args):
     """Poisson arrivals at 2000 requests/s of MulLinRS jobs, N in {8192,
     16384, 32768}, levels 2-16, keys resident, 64 GB admission budget: the
     continuous-batching server versus the same server with one request per
-    launch (one slot, one stream)."""
+    launch (one slot, one stream). Each server reserves its buffer pool at
+    start-up (prewarm) and runs its loop without collector pauses."""
     from paper_2109_14704_gb300 import serving
 
     import torch
 
     out = {"workload": "Poisson 2000 req/s, N in {8192,16384,32768}, levels 2-16, budget 64 GB"}
-    for name, kw in (("batched", dict(slots=16, streams=4)), ("plain", dict(slots=1, streams=1))):
+    for name, kw in (("batched", dict(slots=16, streams=4, prewarm_batches=8)),
+                     ("plain", dict(slots=1, streams=1, prewarm_batches=4))):
         # every server starts from an empty allocator cache (the previous
         # phases' freed blocks would otherwise count against device memory)
         torch.cuda.synchronize()

@@ -200,7 +200,7 @@ size_t he_rescale_scratch_bytes(const he_context *ctx, uint32_t level);
 he_status he_rescale(uint64_t *ct_out, const uint64_t *ct_in, const he_context *ctx,
                      uint32_t level, void *scratch, size_t scratch_bytes, he_stream_t stream);
 
-/* MulLinRS (Sec. V-C): Mul, Relin and RS of `count` ciphertext pairs in one
+/* MulLinRS (Sec. IV-C): Mul, Relin and RS of `count` ciphertext pairs in one
  * fused sequence of launches. ct_a, ct_b are [count][2][l+1][N]; ct_out is
  * [count][2][l][N]. The two roundings (by P, then by q_l) stay separate, so
  * the result equals he_rescale(he_relin(he_ct_mul(a, b))). */
@@ -214,6 +214,48 @@ he_status he_mul_relin_rescale(uint64_t *ct_out, const uint64_t *ct_a, const uin
                                uint32_t count, const he_relin_key *key, const he_context *ctx,
                                uint32_t level, void *scratch, size_t scratch_bytes,
                                he_stream_t stream);
+
+/* ---- the other routines of Sec. IV-C and the matrix product of Sec. IV-E ---------- */
+
+/* SqrLinRS: the square of each ciphertext (tensor (a0^2, 2 a0 a1, a1^2)),
+ * relinearized and rescaled; equals he_mul_relin_rescale(a, a). ct_a is
+ * [count][2][l+1][N], ct_out [count][2][l][N]; scratch as MulLinRS. */
+he_status he_sqr_relin_rescale(uint64_t *ct_out, const uint64_t *ct_a, uint32_t count,
+                               const he_relin_key *key, const he_context *ctx, uint32_t level,
+                               void *scratch, size_t scratch_bytes, he_stream_t stream);
+
+/* MulLin: Mul then Relin of `count` pairs, no rescale: ct_out
+ * [count][2][l+1][N] equals he_relin(he_ct_mul(a, b)). Scratch: at least
+ * (3 n + 2) N words per pair; he_mul_relin_scratch_bytes also makes room
+ * for the expanded mod-up (groups of up to 64). */
+size_t he_mul_relin_scratch_bytes(const he_context *ctx, uint32_t level, uint32_t count);
+he_status he_mul_relin(uint64_t *ct_out, const uint64_t *ct_a, const uint64_t *ct_b, uint32_t count,
+                       const he_relin_key *key, const he_context *ctx, uint32_t level, void *scratch,
+                       size_t scratch_bytes, he_stream_t stream);
+
+/* Relin then RS of `count` three-component ciphertexts ct3
+ * [count][3][l+1][N] (for instance tensors accumulated over a matrix
+ * product, relinearized once per output), into [count][2][l][N]; equals
+ * he_rescale(he_relin(ct3)). Scratch as MulLinRS. */
+he_status he_relin_rescale(uint64_t *ct_out, const uint64_t *ct3, uint32_t count, const he_relin_key *key,
+                           const he_context *ctx, uint32_t level, void *scratch, size_t scratch_bytes,
+                           he_stream_t stream);
+
+/* Add (Sec. II-A): ct_out = ct_a + ct_b mod q_i, `count` ciphertexts of
+ * `components` (2 or 3) components at level l ([count][components][l+1][N]).
+ * ct_out may equal ct_a or ct_b. */
+he_status he_ct_add(uint64_t *ct_out, const uint64_t *ct_a, const uint64_t *ct_b, uint32_t count,
+                    uint32_t components, const he_context *ctx, uint32_t level, he_stream_t stream);
+
+/* Tensor part of the encrypted matrix product C += A B (Sec. IV-E,
+ * matMul_mxnxk): for the m x k matrix A and the k x n matrix B of level-l
+ * ciphertexts (row-major, each [2][l+1][N]), t_out[i][j] (row-major m x n,
+ * each [3][l+1][N]) = sum over l' of the tensor of A[i][l'] and B[l'][j]
+ * (Sec. II-A Mul, accumulated before relinearization). he_relin_rescale of
+ * t_out followed by he_ct_add into C completes C += A B with one key switch
+ * per output (lazy relinearization). m, n, k >= 1. */
+he_status he_ct_matmul_tensor(uint64_t *t_out, const uint64_t *a, const uint64_t *b, uint32_t m, uint32_t k,
+                              uint32_t n, const he_context *ctx, uint32_t level, he_stream_t stream);
 
 /* Allocation-free MulLinRS. The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory when they need the

@@ -195,10 +195,38 @@ def rescale(ct: np.ndarray, moduli, level: int) -> np.ndarray:
 
 
 def mul_relin_rescale(ct_a, ct_b, evk, moduli, P, level) -> np.ndarray:
-    """MulLinRS: tensor, relinearize, rescale (Sec. V-C routines)."""
+    """MulLinRS: tensor, relinearize, rescale (Sec. IV-C routines)."""
     ct3 = tensor(ct_a, ct_b, list(moduli)[:level + 1])
     ct2 = relin(ct3, evk, moduli, P, level)
     return rescale(ct2, moduli, level)
+
+
+def add(ct_a: np.ndarray, ct_b: np.ndarray, moduli) -> np.ndarray:
+    """Add (Sec. II-A): componentwise (a + b) mod q_l on [c][n][N] residues
+    (any number of components c; moduli q_0..q_{n-1})."""
+    a, b = _u64(ct_a), _u64(ct_b)
+    qs = np.array([int(q) for q in list(moduli)[:a.shape[-2]]], dtype=np.uint64)[:, None]
+    return (a + b) % qs
+
+
+def matmul_tensor(A, B, moduli) -> np.ndarray:
+    """Tensor part of the encrypted matrix product C += A B (Sec. IV-E
+    matMul_mxnxk): A is [m][k] and B [k][n] two-component ciphertexts
+    ([2][n_limbs][N] each); returns [m][n][3][n_limbs][N] with
+    T[i][j] = sum over l of the Mul tensor (Sec. II-A) of A[i][l] and B[l][j],
+    summed limb by limb mod q."""
+    A, B = _u64(A), _u64(B)
+    m, k, n = A.shape[0], A.shape[1], B.shape[1]
+    assert B.shape[0] == k
+    qs = list(moduli)[:A.shape[-2]]
+    out = np.empty((m, n, 3) + A.shape[-2:], dtype=np.uint64)
+    for i in range(m):
+        for j in range(n):
+            acc = tensor(A[i, 0], B[0, j], qs)
+            for l in range(1, k):
+                acc = add(acc, tensor(A[i, l], B[l, j], qs), qs)
+            out[i, j] = acc
+    return out
 
 
 # ---- multi-threaded drivers for the timed CPU baseline -------------------------

@@ -5,7 +5,7 @@ library built for that degree (he_ntt_shapes: words per CTA, i.e. how many
 stages run across the CTAs of a cluster versus inside one CTA's shared
 memory, and words per thread, i.e. radix-8 or radix-16 register rounds --
 the paper tuned the same knobs by hand: radix, SLM threshold and register
-slots, Sec. III-B, Sec. V-A), each launched either as one cluster per limb
+slots, Sec. III-B, Sec. IV-A), each launched either as one cluster per limb
 or as a persistent grid walking the limbs, and keeps the fastest for each
 direction. Each candidate is first checked once: its
 forward output must equal the default shape's output bit for bit and its

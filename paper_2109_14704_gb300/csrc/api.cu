@@ -789,40 +789,125 @@ extern "C" he_status he_rescale(uint64_t *ct_out, const uint64_t *ct_in, const h
     return run_eval(ctx, he::EK_RS, a, 2 * level, s);
 }
 
-extern "C" he_status he_mul_relin_rescale(uint64_t *ct_out, const uint64_t *ct_a, const uint64_t *ct_b,
-                                          uint32_t count, const he_relin_key *key, const he_context *ctx,
-                                          uint32_t level, void *scratch, size_t scratch_bytes, he_stream_t stream)
+// Key switching of `count` ciphertexts whose third component is given either
+// as the tensor of a pair (ct_a, ct_b: Mul fused into the loads) or as a
+// three-component input ct3, then (rescale = true) RS by q_l (MulLinRS
+// kernels) or (rescale = false) the mod-down only (MulLin / Relin).
+static he_status key_switch_common(uint64_t *ct_out, const uint64_t *ct_a, const uint64_t *ct_b, const uint64_t *ct3,
+                                   uint32_t count, const he_relin_key *key, const he_context *ctx, uint32_t level,
+                                   void *scratch, size_t scratch_bytes, he_stream_t stream, bool rescale)
 {
-    if (he_status s = check_level(ctx, level, true)) return s;
+    if (he_status s = check_level(ctx, level, rescale)) return s;
     if (!key || key->ctx != ctx) return fail(HE_EINVAL, "relin key is NULL or belongs to another context");
     if (he_status s = check_ptr(ct_out, "ct_out")) return s;
-    if (he_status s = check_ptr(ct_a, "ct_a")) return s;
-    if (he_status s = check_ptr(ct_b, "ct_b")) return s;
+    if (ct3) {
+        if (he_status s = check_ptr(ct3, "ct3")) return s;
+    } else {
+        if (he_status s = check_ptr(ct_a, "ct_a")) return s;
+        if (he_status s = check_ptr(ct_b, "ct_b")) return s;
+    }
     if (count == 0) return HE_OK;
     if (he_status s = check_ptr(scratch, "scratch")) return s;
     const u32 n = level + 1;
-    if (scratch_bytes < mrr_words(ctx, n) * 8 * count) return fail(HE_EINVAL, "scratch too small");
+    const size_t base_words = (rescale ? mrr_words(ctx, n) : relin_words(ctx, n)) * count;
+    if (scratch_bytes < base_words * 8) return fail(HE_EINVAL, "scratch too small");
     if ((u64)count * 2 * n * (ctx->N / 4096 + 1) > 0x7fffffffull) return fail(HE_EINVAL, "batch too large");
     he::EvalArgs a = {};
-    a.ct_a = ct_a;
-    a.ct_b = ct_b;
+    a.ct_a = ct3 ? nullptr : ct_a;
+    a.ct_b = ct3 ? nullptr : ct_b;
+    a.ct3 = ct3;
     a.out = ct_out;
     a.c2 = (u64 *)scratch;
     a.accq = a.c2 + (size_t)count * n * ctx->N;
     a.plift = a.accq + (size_t)count * 2 * n * ctx->N;
-    a.lift2 = a.plift + (size_t)count * 2 * ctx->N;
+    a.lift2 = rescale ? a.plift + (size_t)count * 2 * ctx->N : nullptr;
     a.evk = key->d_evk;
     a.n = n;
     a.count = count;
     a.ctx = dev_ctx(ctx);
     cudaStream_t s = (cudaStream_t)stream;
-    u64 *xbuf = (u64 *)scratch + mrr_words(ctx, n) * count;
-    const size_t x_words = scratch_bytes / 8 - mrr_words(ctx, n) * count;
+    u64 *xbuf = (u64 *)scratch + base_words;
+    const size_t x_words = scratch_bytes / 8 - base_words;
     if (he_status r = run_eval(ctx, he::EK_KS_DIGITS, a, count * n, s)) return r;
     if (he_status r = ks_modup(ctx, a, count, xbuf, x_words, s)) return r;
+    if (!rescale) return run_eval(ctx, he::EK_KS_MODDOWN, a, count * 2 * n, s);
     if (he_status r = run_eval(ctx, he::EK_MRR_LAST, a, count * 2, s)) return r;
     if (he_status r = run_eval(ctx, he::EK_MRR_REST_Z, a, count * 2 * level, s)) return r;
     return run_eval(ctx, he::EK_MRR_REST_OUT, a, count * 2 * level, s);
+}
+
+extern "C" he_status he_mul_relin_rescale(uint64_t *ct_out, const uint64_t *ct_a, const uint64_t *ct_b,
+                                          uint32_t count, const he_relin_key *key, const he_context *ctx,
+                                          uint32_t level, void *scratch, size_t scratch_bytes, he_stream_t stream)
+{
+    return key_switch_common(ct_out, ct_a, ct_b, nullptr, count, key, ctx, level, scratch, scratch_bytes, stream,
+                             true);
+}
+
+extern "C" he_status he_sqr_relin_rescale(uint64_t *ct_out, const uint64_t *ct_a, uint32_t count,
+                                          const he_relin_key *key, const he_context *ctx, uint32_t level,
+                                          void *scratch, size_t scratch_bytes, he_stream_t stream)
+{
+    return key_switch_common(ct_out, ct_a, ct_a, nullptr, count, key, ctx, level, scratch, scratch_bytes, stream,
+                             true);
+}
+
+extern "C" he_status he_relin_rescale(uint64_t *ct_out, const uint64_t *ct3, uint32_t count,
+                                      const he_relin_key *key, const he_context *ctx, uint32_t level, void *scratch,
+                                      size_t scratch_bytes, he_stream_t stream)
+{
+    if (!ct3) return fail(HE_EINVAL, "ct3 is NULL");
+    return key_switch_common(ct_out, nullptr, nullptr, ct3, count, key, ctx, level, scratch, scratch_bytes, stream,
+                             true);
+}
+
+extern "C" size_t he_mul_relin_scratch_bytes(const he_context *ctx, uint32_t level, uint32_t count)
+{
+    if (!ctx || !count) return 0;
+    return (relin_words(ctx, level + 1) * count + modup_x_words(ctx, level + 1, std::min(count, kModupGroup))) * 8;
+}
+
+extern "C" he_status he_mul_relin(uint64_t *ct_out, const uint64_t *ct_a, const uint64_t *ct_b, uint32_t count,
+                                  const he_relin_key *key, const he_context *ctx, uint32_t level, void *scratch,
+                                  size_t scratch_bytes, he_stream_t stream)
+{
+    return key_switch_common(ct_out, ct_a, ct_b, nullptr, count, key, ctx, level, scratch, scratch_bytes, stream,
+                             false);
+}
+
+extern "C" he_status he_ct_add(uint64_t *ct_out, const uint64_t *ct_a, const uint64_t *ct_b, uint32_t count,
+                               uint32_t components, const he_context *ctx, uint32_t level, he_stream_t stream)
+{
+    if (he_status s = check_level(ctx, level, false)) return s;
+    if (components != 2 && components != 3) return fail(HE_EINVAL, "components must be 2 or 3, got %u", components);
+    if (he_status s = check_ptr(ct_out, "ct_out")) return s;
+    if (he_status s = check_ptr(ct_a, "ct_a")) return s;
+    if (he_status s = check_ptr(ct_b, "ct_b")) return s;
+    if (count == 0) return HE_OK;
+    const u32 n = level + 1;
+    const u64 words = (u64)count * components * n * ctx->N;
+    he::k_ct_add<<<stream_grid(words / 2, 256), 256, 0, (cudaStream_t)stream>>>(
+        ct_out, ct_a, ct_b, words, (u32)ctx->log_n, n, ctx->tables->d_pc);
+    HE_CUDA(cudaGetLastError());
+    return HE_OK;
+}
+
+extern "C" he_status he_ct_matmul_tensor(uint64_t *t_out, const uint64_t *a, const uint64_t *b, uint32_t m,
+                                         uint32_t k, uint32_t n, const he_context *ctx, uint32_t level,
+                                         he_stream_t stream)
+{
+    if (he_status s = check_level(ctx, level, false)) return s;
+    if (he_status s = check_ptr(t_out, "t_out")) return s;
+    if (he_status s = check_ptr(a, "a")) return s;
+    if (he_status s = check_ptr(b, "b")) return s;
+    if (m == 0 || k == 0 || n == 0) return fail(HE_EINVAL, "matrix dimensions must be positive");
+    if ((u64)m * n * 3 * (level + 1) * ctx->N >= (1ull << 40)) return fail(HE_EINVAL, "matrix product too large");
+    const u32 limbs = level + 1;
+    const u64 threads = (u64)m * ((n + he::MM_TJ - 1) / he::MM_TJ) * limbs * (ctx->N / 2);
+    he::k_ct_matmul_tensor<<<stream_grid(threads, 256), 256, 0, (cudaStream_t)stream>>>(
+        t_out, a, b, m, k, n, (u32)ctx->log_n, limbs, ctx->tables->d_pc);
+    HE_CUDA(cudaGetLastError());
+    return HE_OK;
 }
 
 // ------------------------------------------------------------- measurement

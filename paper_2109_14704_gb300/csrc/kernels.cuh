@@ -244,6 +244,136 @@ __global__ void k_tensor(u64 *out3, const u64 *ct_a, const u64 *ct_b, u32 log_n,
     }
 }
 
+// ct_out = ct_a + ct_b mod q per limb, `words` words of ciphertexts with n
+// limbs of 2^log_n words (any number of components), two words per thread.
+__global__ void k_ct_add(u64 *out, const u64 *a, const u64 *b, u64 words, u32 log_n, u32 n, const PrimeConst *pcs)
+{
+    for (u64 g = (u64)blockIdx.x * blockDim.x + threadIdx.x; 2 * g < words; g += (u64)gridDim.x * blockDim.x) {
+        const u64 e = 2 * g;
+        const PrimeConst pc = pcs[(u32)((e >> log_n) % n)];
+        const ulonglong2 x = *reinterpret_cast<const ulonglong2 *>(a + e);
+        const ulonglong2 y = *reinterpret_cast<const ulonglong2 *>(b + e);
+        *reinterpret_cast<ulonglong2 *>(out + e) = make_ulonglong2(add_mod(x.x, y.x, pc.p), add_mod(x.y, y.y, pc.p));
+    }
+}
+
+// ============================================ encrypted matrix product ======
+// Tensor part of C += A B (Sec. IV-E matMul_mxnxk; Sec. II-A Mul): for each
+// limb and position, T[i][j] = sum_l (a0 b0, a0 b1 + a1 b0, a1 b1) over the
+// pairs (A[i][l], B[l][j]) mod q. For q >= 2^32 the 128-bit products are
+// summed without reduction (a0 b1 + a1 b0 included: the fused
+// multiply-add of Sec. III-A-1 carried over the whole sum) and reduced once
+// per 32 terms; smaller moduli reduce every term (Barrett, one reduction for
+// a0 b1 + a1 b0). A thread owns one limb, two positions, row i and MM_TJ
+// consecutive output columns, so each A word it loads serves MM_TJ products;
+// consecutive threads take consecutive positions (coalesced 16-byte loads).
+constexpr u32 MM_TJ = 2;
+
+// (h, lo) += a b as a 128-bit sum.
+__device__ __forceinline__ void mac128(u64 &h, u64 &lo, u64 a, u64 b)
+{
+    const u64 pl = a * b, ph = __umul64hi(a, b);
+    lo += pl;
+    h += ph + (lo < pl ? 1 : 0);
+}
+
+__global__ void k_ct_matmul_tensor(u64 *t, const u64 *a, const u64 *b, u32 m, u32 k, u32 n, u32 log_n, u32 limbs,
+                                   const PrimeConst *pcs)
+{
+    const u32 half = 1u << (log_n - 1);
+    const u32 jt_count = (n + MM_TJ - 1) / MM_TJ;
+    const size_t poly = (size_t)limbs << log_n;             // words per component
+    const u64 total = (u64)m * jt_count * limbs * half;
+    for (u64 q = (u64)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (u64)gridDim.x * blockDim.x) {
+        const u32 P = (u32)(q % half) * 2;
+        const u32 limb = (u32)((q / half) % limbs);
+        const u32 jt = (u32)((q / ((u64)half * limbs)) % jt_count);
+        const u32 i = (u32)(q / ((u64)half * limbs * jt_count));
+        const PrimeConst pc = pcs[limb];
+        const size_t off = ((size_t)limb << log_n) + P;
+        u64 acc[MM_TJ][3][2];
+#pragma unroll
+        for (u32 jj = 0; jj < MM_TJ; jj++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) acc[jj][c][0] = acc[jj][c][1] = 0;
+        if (pc.p >= (1ull << 32)) {
+            // lazy: 128-bit sums of up to 64 products (< 2^126), reduced per
+            // chunk of 32 terms: hi mod p, then hi 2^64 + lo = hi c64 + lo
+            const u64 c64 = barrett_reduce(1, 0, pc.p, pc.mu, pc.bits);   // 2^64 mod p
+            for (u32 l0 = 0; l0 < k; l0 += 32) {
+                u64 h[MM_TJ][3][2], lo[MM_TJ][3][2];
+#pragma unroll
+                for (u32 jj = 0; jj < MM_TJ; jj++)
+#pragma unroll
+                    for (int c = 0; c < 3; c++) h[jj][c][0] = h[jj][c][1] = lo[jj][c][0] = lo[jj][c][1] = 0;
+                const u32 l1 = min(k, l0 + 32);
+                for (u32 l = l0; l < l1; l++) {
+                    const u64 *ap = a + ((size_t)i * k + l) * 2 * poly + off;
+                    const ulonglong2 a0 = __ldg(reinterpret_cast<const ulonglong2 *>(ap));
+                    const ulonglong2 a1 = __ldg(reinterpret_cast<const ulonglong2 *>(ap + poly));
+#pragma unroll
+                    for (u32 jj = 0; jj < MM_TJ; jj++) {
+                        const u32 j = jt * MM_TJ + jj;
+                        if (j >= n) break;
+                        const u64 *bp = b + ((size_t)l * n + j) * 2 * poly + off;
+                        const ulonglong2 b0 = __ldg(reinterpret_cast<const ulonglong2 *>(bp));
+                        const ulonglong2 b1 = __ldg(reinterpret_cast<const ulonglong2 *>(bp + poly));
+                        mac128(h[jj][0][0], lo[jj][0][0], a0.x, b0.x);
+                        mac128(h[jj][0][1], lo[jj][0][1], a0.y, b0.y);
+                        mac128(h[jj][1][0], lo[jj][1][0], a0.x, b1.x);
+                        mac128(h[jj][1][0], lo[jj][1][0], a1.x, b0.x);
+                        mac128(h[jj][1][1], lo[jj][1][1], a0.y, b1.y);
+                        mac128(h[jj][1][1], lo[jj][1][1], a1.y, b0.y);
+                        mac128(h[jj][2][0], lo[jj][2][0], a1.x, b1.x);
+                        mac128(h[jj][2][1], lo[jj][2][1], a1.y, b1.y);
+                    }
+                }
+#pragma unroll
+                for (u32 jj = 0; jj < MM_TJ; jj++)
+#pragma unroll
+                    for (int c = 0; c < 3; c++)
+#pragma unroll
+                        for (int x = 0; x < 2; x++) {
+                            const u64 r1 = barrett_reduce(0, h[jj][c][x], pc.p, pc.mu, pc.bits);
+                            u64 zh, zl;
+                            mul_wide(r1, c64, zh, zl);
+                            zl += lo[jj][c][x];
+                            zh += (zl < lo[jj][c][x]) ? 1 : 0;
+                            acc[jj][c][x] = add_mod(acc[jj][c][x], barrett_reduce(zh, zl, pc.p, pc.mu, pc.bits), pc.p);
+                        }
+            }
+        } else
+        for (u32 l = 0; l < k; l++) {
+            const u64 *ap = a + ((size_t)i * k + l) * 2 * poly + off;
+            const ulonglong2 a0 = __ldg(reinterpret_cast<const ulonglong2 *>(ap));
+            const ulonglong2 a1 = __ldg(reinterpret_cast<const ulonglong2 *>(ap + poly));
+#pragma unroll
+            for (u32 jj = 0; jj < MM_TJ; jj++) {
+                const u32 j = jt * MM_TJ + jj;
+                if (j >= n) break;
+                const u64 *bp = b + ((size_t)l * n + j) * 2 * poly + off;
+                const ulonglong2 b0 = __ldg(reinterpret_cast<const ulonglong2 *>(bp));
+                const ulonglong2 b1 = __ldg(reinterpret_cast<const ulonglong2 *>(bp + poly));
+                acc[jj][0][0] = add_mod(acc[jj][0][0], mul_mod(a0.x, b0.x, pc), pc.p);
+                acc[jj][0][1] = add_mod(acc[jj][0][1], mul_mod(a0.y, b0.y, pc), pc.p);
+                acc[jj][1][0] = add_mod(acc[jj][1][0], mad2_mod(a0.x, b1.x, a1.x, b0.x, pc), pc.p);
+                acc[jj][1][1] = add_mod(acc[jj][1][1], mad2_mod(a0.y, b1.y, a1.y, b0.y, pc), pc.p);
+                acc[jj][2][0] = add_mod(acc[jj][2][0], mul_mod(a1.x, b1.x, pc), pc.p);
+                acc[jj][2][1] = add_mod(acc[jj][2][1], mul_mod(a1.y, b1.y, pc), pc.p);
+            }
+        }
+#pragma unroll
+        for (u32 jj = 0; jj < MM_TJ; jj++) {
+            const u32 j = jt * MM_TJ + jj;
+            if (j >= n) break;
+            u64 *tp = t + ((size_t)i * n + j) * 3 * poly + off;
+#pragma unroll
+            for (int c = 0; c < 3; c++)
+                *reinterpret_cast<ulonglong2 *>(tp + c * poly) = make_ulonglong2(acc[jj][c][0], acc[jj][c][1]);
+        }
+    }
+}
+
 #endif  // HE_MISC_KERNELS
 
 // ============================================== key switching and rescale ==

@@ -86,6 +86,16 @@ _SIGS = {
                                           ctypes.c_uint32]),
     "he_butterfly_probe": (ctypes.c_int32, [_vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, _vp]),
     "he_butterfly_apply": (ctypes.c_int32, [_vp, _vp, _vp, _vp, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32, _vp]),
+    "he_sqr_relin_rescale": (ctypes.c_int32, [_vp, _vp, ctypes.c_uint32, _vp, _vp, ctypes.c_uint32, _vp,
+                                              ctypes.c_size_t, _vp]),
+    "he_mul_relin_scratch_bytes": (ctypes.c_size_t, [_vp, ctypes.c_uint32, ctypes.c_uint32]),
+    "he_mul_relin": (ctypes.c_int32, [_vp, _vp, _vp, ctypes.c_uint32, _vp, _vp, ctypes.c_uint32, _vp,
+                                      ctypes.c_size_t, _vp]),
+    "he_relin_rescale": (ctypes.c_int32, [_vp, _vp, ctypes.c_uint32, _vp, _vp, ctypes.c_uint32, _vp,
+                                          ctypes.c_size_t, _vp]),
+    "he_ct_add": (ctypes.c_int32, [_vp, _vp, _vp, ctypes.c_uint32, ctypes.c_uint32, _vp, ctypes.c_uint32, _vp]),
+    "he_ct_matmul_tensor": (ctypes.c_int32, [_vp, _vp, _vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                             _vp, ctypes.c_uint32, _vp]),
     "he_mul_relin_rescale_noalloc": (ctypes.c_int32, [_vp, _vp, _vp, ctypes.c_uint32, _vp, _vp, ctypes.c_uint32,
                                                       _vp]),
 }
@@ -326,6 +336,9 @@ class Context:
     def rescale_scratch_bytes(self, level: int) -> int:
         return int(load().he_rescale_scratch_bytes(self.handle, level))
 
+    def mul_relin_scratch_bytes(self, level: int, count: int) -> int:
+        return int(load().he_mul_relin_scratch_bytes(self.handle, level, count))
+
     def mrr_scratch_bytes(self, level: int, count: int, expand_group: int | None = None) -> int:
         """Scratch bytes of mul_relin_rescale; expand_group bounds the
         expanded mod-up's group (0: the fused minimum, None: the default)."""
@@ -393,6 +406,41 @@ def mul_relin_rescale(ct_out, ct_a, ct_b, count: int, key: RelinKey, ctx: Contex
     w_in, w_out = count * 2 * (level + 1) * ctx.N, count * 2 * level * ctx.N
     _check(load().he_mul_relin_rescale(_ptr(ct_out, w_out), _ptr(ct_a, w_in), _ptr(ct_b, w_in), count, key.handle,
                                        ctx.handle, level, _ptr(scratch), scratch.numel() * 8, _stream(stream)))
+
+
+def sqr_relin_rescale(ct_out, ct_a, count: int, key: RelinKey, ctx: Context, level: int, scratch, stream=None):
+    """SqrLinRS: he_mul_relin_rescale(a, a) (Sec. IV-C routine set)."""
+    w_in, w_out = count * 2 * (level + 1) * ctx.N, count * 2 * level * ctx.N
+    _check(load().he_sqr_relin_rescale(_ptr(ct_out, w_out), _ptr(ct_a, w_in), count, key.handle, ctx.handle, level,
+                                       _ptr(scratch), scratch.numel() * 8, _stream(stream)))
+
+
+def mul_relin(ct_out, ct_a, ct_b, count: int, key: RelinKey, ctx: Context, level: int, scratch, stream=None):
+    """MulLin: Mul then Relin of `count` pairs, no rescale."""
+    w = count * 2 * (level + 1) * ctx.N
+    _check(load().he_mul_relin(_ptr(ct_out, w), _ptr(ct_a, w), _ptr(ct_b, w), count, key.handle, ctx.handle, level,
+                               _ptr(scratch), scratch.numel() * 8, _stream(stream)))
+
+
+def relin_rescale(ct_out, ct3, count: int, key: RelinKey, ctx: Context, level: int, scratch, stream=None):
+    """Relin then RS of `count` three-component ciphertexts."""
+    _check(load().he_relin_rescale(_ptr(ct_out, count * 2 * level * ctx.N), _ptr(ct3, count * 3 * (level + 1) * ctx.N),
+                                   count, key.handle, ctx.handle, level, _ptr(scratch), scratch.numel() * 8,
+                                   _stream(stream)))
+
+
+def ct_add(ct_out, ct_a, ct_b, count: int, components: int, ctx: Context, level: int, stream=None):
+    """Add: ct_out = ct_a + ct_b mod q_i (2- or 3-component ciphertexts)."""
+    w = count * components * (level + 1) * ctx.N
+    _check(load().he_ct_add(_ptr(ct_out, w), _ptr(ct_a, w), _ptr(ct_b, w), count, components, ctx.handle, level,
+                            _stream(stream)))
+
+
+def ct_matmul_tensor(t_out, a, b, m: int, k: int, n: int, ctx: Context, level: int, stream=None):
+    """Tensor part of C += A B over matrices of ciphertexts (row-major)."""
+    w = 2 * (level + 1) * ctx.N
+    _check(load().he_ct_matmul_tensor(_ptr(t_out, m * n * 3 * (level + 1) * ctx.N), _ptr(a, m * k * w),
+                                      _ptr(b, k * n * w), m, k, n, ctx.handle, level, _stream(stream)))
 
 
 class NttPlan:

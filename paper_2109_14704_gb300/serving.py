@@ -27,6 +27,7 @@ from __future__ import annotations
 
 import bisect
 import collections
+import gc
 import math
 import statistics
 import time
@@ -162,7 +163,8 @@ class Server:
     """MulLinRS server over degrees `degrees` and levels [min_level, max_level]."""
 
     def __init__(self, degrees=(8192, 16384, 32768), min_level=2, max_level=16, budget_bytes=64 << 30,
-                 slots=16, streams=4, max_wait_s=0.002, pool_per_bucket=2, seed=5, device=None, expand_group=4):
+                 slots=16, streams=4, max_wait_s=0.002, pool_per_bucket=2, seed=5, device=None, expand_group=4,
+                 prewarm_batches=0):
         import torch
         self.torch = torch
         self.device = device or torch.device("cuda", torch.cuda.current_device())
@@ -205,6 +207,26 @@ class Server:
         self.keep: dict = {}                   # rid -> result copy (host) for requests to check
         self.peak_ledger = 0
         self.batches_launched = 0
+        if prewarm_batches:
+            self.prewarm(prewarm_batches)
+
+    def prewarm(self, batches: int):
+        """Reserve the memory pool up front, as a server does at start-up:
+        `batches` buffer sets of the largest bucket (any smaller batch can
+        reuse them), allocated and returned to the cache, so that requests
+        seldom wait for the device allocator."""
+        N, lvl = max(self.degrees), self.max_level
+        words = self._batch_words(N, lvl, self.slots)
+        sets = []
+        for _ in range(batches):
+            got = self.cache.allocate_within(words, self.budget, self.static_bytes)
+            if got is None:
+                break
+            sets.append(got)
+        for got in sets:
+            for cap, t in got:
+                self.cache.free(cap, t)
+        self.peak_ledger = max(self.peak_ledger, self.ledger())
 
     # ---- ledger
     def ledger(self) -> int:
@@ -317,6 +339,18 @@ class Server:
         torch = self.torch
         self.keep = {rid: None for rid in keep_ids}
         pending = collections.deque(sorted(requests, key=lambda q: q.arrival))
+        # no collector pauses inside the serving loop (it runs on one host
+        # thread; a full collection of a large process takes milliseconds)
+        gc.collect()
+        gc_was_enabled = gc.isenabled()
+        gc.disable()
+        try:
+            return self._run(pending, torch)
+        finally:
+            if gc_was_enabled:
+                gc.enable()
+
+    def _run(self, pending, torch) -> dict:
         torch.cuda.synchronize()
         self.anchor = torch.cuda.Event(enable_timing=True)
         self.anchor.record(self.streams[0])

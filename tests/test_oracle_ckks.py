@@ -95,3 +95,47 @@ def test_mul_relin_rescale_round_trip(N, data_bits, tol):
     assert out.shape == (2, L, N)
     scale_out = scale * scale / data[L]
     assert _err(ckks.decrypt_decode(out, keys, scale_out), za * zb) < tol
+
+
+def test_add_brute_force_and_decryption():
+    """Add: residue by residue against Python integers, and decrypt(a + b) =
+    decrypt(a) + decrypt(b) on decoded slots."""
+    qs = [97, 113]
+    a = np.array([[[96, 5, 0], [112, 1, 50]]], dtype=np.uint64)
+    b = np.array([[[1, 96, 0], [112, 112, 63]]], dtype=np.uint64)
+    got = oracle.add(a, b, qs)
+    for l, q in enumerate(qs):
+        for x in range(3):
+            assert int(got[0, l, x]) == (int(a[0, l, x]) + int(b[0, l, x])) % q
+    N, scale = 1024, 2.0 ** 40
+    data, P = oracle.chain_primes(N, [60, 40, 40], 60)
+    r = Rng(11)
+    keys = ckks.keygen(N, data, P, r)
+    za, zb = r.complex_slots(N // 2), r.complex_slots(N // 2)
+    ca = ckks.encrypt(ckks.encode_real(za, N, scale), keys, r)
+    cb = ckks.encrypt(ckks.encode_real(zb, N, scale), keys, r)
+    assert _err(ckks.decrypt_decode(oracle.add(ca, cb, data), keys, scale), za + zb) < 1e-6
+
+
+def test_matmul_tensor_decrypts_to_slot_matrix_product():
+    """T = sum_l A_il (x) B_lj decrypts (with 1, s, s^2) to the slot-wise
+    matrix product sum_l z(A_il) z(B_lj): exact numpy arithmetic on the
+    plaintext slots, independent of the oracle's ring code."""
+    N, scale = 1024, 2.0 ** 40          # product scale 2^80 under the 180-bit chain
+    data, P = oracle.chain_primes(N, [60, 60, 60], 60)
+    r = Rng(12)
+    keys = ckks.keygen(N, data, P, r)
+    m, k, n = 2, 3, 2
+    zA = np.array([[r.complex_slots(N // 2) for _ in range(k)] for _ in range(m)])
+    zB = np.array([[r.complex_slots(N // 2) for _ in range(n)] for _ in range(k)])
+    A = np.stack([np.stack([ckks.encrypt(ckks.encode_real(zA[i, l], N, scale), keys, r) for l in range(k)])
+                  for i in range(m)])
+    B = np.stack([np.stack([ckks.encrypt(ckks.encode_real(zB[l, j], N, scale), keys, r) for j in range(n)])
+                  for l in range(k)])
+    T = oracle.matmul_tensor(A, B, data)
+    assert T.shape == (m, n, 3, len(data), N)
+    for i in range(m):
+        for j in range(n):
+            z = ckks.decrypt_decode(T[i, j], keys, scale * scale)
+            exact = sum(zA[i, l] * zB[l, j] for l in range(k))
+            assert _err(z, exact) < 1e-5
