@@ -73,7 +73,7 @@ def _args():
                     help="NTT instances of --profile-case ntt, ciphertext pairs of --profile-case mrr")
     ap.add_argument("--shape", default="",
                     help="log_block,log_thread_words[,persistent] for --profile-case ntt (or fwd/inv)")
-    ap.add_argument("--skip", default="", help="comma list of sub-benchmarks to skip: uneven,matrix,serving")
+    ap.add_argument("--skip", default="", help="comma list of sub-benchmarks to skip: uneven,matrix,routines,serving")
     ap.add_argument("--serve-requests", type=int, default=4000)
     ap.add_argument("--no-tune-cache", action="store_true", help="always re-run the autotuner")
     a = ap.parse_args()
@@ -309,6 +309,7 @@ def run_ours(args, rank, world, local):
 
     uneven = bench_uneven(args, stream, barrier) if "uneven" not in args.skip else None
     matrix = bench_matrix(args, stream, barrier) if "matrix" not in args.skip else None
+    routines = bench_routines(args, stream, barrier) if "routines" not in args.skip else None
 
     # end to end through host buffers: one he_ntt_host call per step (copy in,
     # forward, inverse, copy out, pipelined over chunks of 32 polynomials)
@@ -394,6 +395,7 @@ def run_ours(args, rank, world, local):
                                     for c in tune["candidates"]]},
         "uneven_batch": uneven,
         "matrix_mul_relin_rescale": matrix,
+        "routines": routines,
         "serving": serve,
         "mul_relin_rescale": {
             "workload": "N=16384, data primes 60+6x50, special 60, 64 ciphertext pairs, level 6 -> 5",
@@ -581,6 +583,45 @@ def bench_matrix(args, stream, barrier):
             "relin_rescale_outputs": m * n,
             "tensor_products_per_s": m * k * n / (ms_t / 1e3)}
         del Am, Bm, Cm, T, R, sc
+    return res
+
+
+def bench_routines(args, stream, barrier):
+    """The paper's five-routine set at its size (Sec. IV-C: N = 32K, 8 RNS
+    limbs; here data primes 60 + 7 x 50, special prime 60, level 7), batches
+    of 16 ciphertexts: MulLin, MulLinRS, SqrLinRS, Rotate (k = 1)."""
+    import numpy as np
+    import torch
+
+    from paper_2109_14704_gb300 import he
+    from paper_2109_14704_gb300.synth import Rng
+
+    N, count = 32768, 16
+    data, P = he.chain_primes(N, [60] + [50] * 7, 60)
+    ctx = he.Context(N, data, P)
+    L = len(data) - 1
+    r = Rng(8)
+    evk = np.stack([np.stack([r.uniform_limbs(data + [P], N) for _ in range(2)]) for _ in range(len(data))])
+    key = he.RelinKey(ctx, evk)          # also serves as a (pseudo-random) Galois key for timing
+    mk = lambda: torch.from_numpy(np.stack([np.stack([r.uniform_limbs(data, N) for _ in range(2)])
+                                            for _ in range(count)]).view(np.int64)).cuda()
+    A, B = mk(), mk()
+    out_l = torch.empty((count, 2, L + 1, N), dtype=torch.int64, device="cuda")
+    out_r = torch.empty((count, 2, L, N), dtype=torch.int64, device="cuda")
+    sc = torch.empty(max(ctx.mrr_scratch_bytes(L, count), ctx.rotate_scratch_bytes(L, count)) // 8,
+                     dtype=torch.int64, device="cuda")
+    g = pow(5, 1, 2 * N)
+    ops = {
+        "mul_lin": lambda: he.mul_relin(out_l, A, B, count, key, ctx, L, sc, stream=stream),
+        "mul_lin_rs": lambda: he.mul_relin_rescale(out_r, A, B, count, key, ctx, L, sc, stream=stream),
+        "sqr_lin_rs": lambda: he.sqr_relin_rescale(out_r, A, count, key, ctx, L, sc, stream=stream),
+        "rotate": lambda: he.rotate(out_l, A, count, g, key, ctx, L, sc, stream=stream),
+    }
+    res = {"workload": f"N=32768, {len(data)} data primes (60 + 7 x 50) + 60-bit special, level {L}, "
+                       f"batches of {count} ciphertexts"}
+    for name, fn in ops.items():
+        ms = _time_steps(fn, max(3, args.steps // 2), 2, stream, barrier)
+        res[name] = {"ms_per_batch": ms, "per_s": count / (ms / 1e3)}
     return res
 
 

@@ -247,6 +247,28 @@ he_status he_relin_rescale(uint64_t *ct_out, const uint64_t *ct3, uint32_t count
 he_status he_ct_add(uint64_t *ct_out, const uint64_t *ct_a, const uint64_t *ct_b, uint32_t count,
                     uint32_t components, const he_context *ctx, uint32_t level, he_stream_t stream);
 
+/* The automorphism X -> X^galois_elt (odd, below 2N) applied to each of
+ * `components` components of `count` level-l ciphertexts in the NTT domain
+ * ([count][components][l+1][N]); a permutation of every limb's evaluations.
+ * Not in place. */
+he_status he_ct_automorph(uint64_t *ct_out, const uint64_t *ct_in, uint32_t count, uint32_t components,
+                          uint32_t galois_elt, const he_context *ctx, uint32_t level, he_stream_t stream);
+
+/* Rotate (Sec. IV-C routine set): for each of `count` level-l ciphertexts
+ * ([count][2][l+1][N] in and out), (sigma(c0), sigma(c1)) with
+ * sigma: X -> X^galois_elt, then sigma(c1) key-switched back to s with the
+ * Galois key, i.e. he_relin of (sigma(c0), 0, sigma(c1)). galois_elt = 5^k
+ * mod 2N rotates the slots by k (slot j at zeta^(5^j)); 2N - 1 conjugates.
+ * The Galois key has the relinearization key's layout and is uploaded with
+ * he_relin_key_upload: evk[j][0] + evk[j][1] s = e_j + [j = i] (P mod q_i)
+ * s(X^galois_elt) on limb q_i (no such term on P). Scratch:
+ * he_rotate_scratch_bytes (at least 3 n N + (3 n + 2) N words per
+ * ciphertext). */
+size_t he_rotate_scratch_bytes(const he_context *ctx, uint32_t level, uint32_t count);
+he_status he_rotate(uint64_t *ct_out, const uint64_t *ct_in, uint32_t count, uint32_t galois_elt,
+                    const he_relin_key *galois_key, const he_context *ctx, uint32_t level, void *scratch,
+                    size_t scratch_bytes, he_stream_t stream);
+
 /* Tensor part of the encrypted matrix product C += A B (Sec. IV-E,
  * matMul_mxnxk): for the m x k matrix A and the k x n matrix B of level-l
  * ciphertexts (row-major, each [2][l+1][N]), t_out[i][j] (row-major m x n,

@@ -209,6 +209,38 @@ def add(ct_a: np.ndarray, ct_b: np.ndarray, moduli) -> np.ndarray:
     return (a + b) % qs
 
 
+def automorphism(a: np.ndarray, g: int, moduli) -> np.ndarray:
+    """The ring automorphism a(X) -> a(X^g) of Z_q[X]/(X^N + 1) (g odd) on
+    coefficient-domain residues [limbs][N]: coefficient j moves to g j mod 2N,
+    negated when that exponent is N or more (X^N = -1). Behind Rotate
+    (Sec. IV-C): X -> X^(5^k) rotates the slots by k."""
+    a = _u64(a)
+    N = a.shape[-1]
+    assert g % 2 == 1
+    e = (np.arange(N, dtype=np.int64) * (g % (2 * N))) % (2 * N)
+    dest, neg = e % N, e >= N
+    qs = np.array([int(q) for q in list(moduli)[:a.shape[0]]], dtype=np.uint64)[:, None]
+    out = np.zeros_like(a)
+    out[:, dest] = np.where(neg[None, :], (qs - a) % qs, a)
+    return out
+
+
+def ntt_automorphism(a_ntt: np.ndarray, g: int, moduli) -> np.ndarray:
+    """The automorphism on NTT-domain residues, through the coefficient
+    domain (inverse transform, automorphism, forward transform)."""
+    return ntt_fwd(automorphism(ntt_inv(a_ntt, moduli), g, moduli), moduli)
+
+
+def rotate(ct: np.ndarray, g: int, gk: np.ndarray, moduli, P: int, level: int) -> np.ndarray:
+    """Rotate (Sec. IV-C): (sigma(c0), sigma(c1)) with sigma: X -> X^g, then
+    c1's key switched back to s with the Galois key gk (the relinearization
+    of (sigma(c0), 0, sigma(c1)))."""
+    ct = _u64(ct)
+    qs = list(moduli)[:level + 1]
+    c3 = np.stack([ntt_automorphism(ct[0], g, qs), np.zeros_like(ct[0]), ntt_automorphism(ct[1], g, qs)])
+    return relin(c3, gk, moduli, P, level)
+
+
 def matmul_tensor(A, B, moduli) -> np.ndarray:
     """Tensor part of the encrypted matrix product C += A B (Sec. IV-E
     matMul_mxnxk): A is [m][k] and B [k][n] two-component ciphertexts

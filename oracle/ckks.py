@@ -124,6 +124,17 @@ def keygen(N: int, data_moduli, P: int, rng) -> Keys:
     pk0 = np.stack([(np.uint64(q) - as_[l] + e[l]) % np.uint64(q) for l, q in enumerate(data_moduli)])
     pk = np.stack([_o.ntt_fwd(pk0, data_moduli), _o.ntt_fwd(a, data_moduli)])
 
+    evk = _switching_key(s_res, s2_res, data_moduli, int(P), rng)
+    return Keys(N, data_moduli, int(P), s, pk, evk)
+
+
+def _switching_key(s_res: np.ndarray, from_res: np.ndarray, data_moduli, P: int, rng) -> np.ndarray:
+    """Key switching from the secret `from` (residues on q_0..q_L, P) to s:
+    one RNS digit per data prime, evk[j] = (-a_j s + e_j + [t = j] (P mod q_t)
+    from, a_j) on the limbs t of {q_0..q_L, P}, in the NTT domain
+    ([L+1][2][L+2][N]). With from = s^2 it is the relinearization key."""
+    all_mod = list(data_moduli) + [P]
+    L1, N = len(data_moduli), s_res.shape[1]
     evk = np.empty((L1, 2, L1 + 1, N), dtype=np.uint64)
     for j in range(L1):
         aj = rng.uniform_limbs(all_mod, N)
@@ -134,11 +145,19 @@ def keygen(N: int, data_moduli, P: int, rng) -> Keys:
             qq = np.uint64(q)
             v = (qq - ajs[t] + ej[t]) % qq
             if t == j:
-                v = (v + _mulmod_vec(s2_res[t], int(P) % q, q)) % qq
+                v = (v + _mulmod_vec(from_res[t], P % q, q)) % qq
             k0[t] = v
         evk[j, 0] = _o.ntt_fwd(k0, all_mod)
         evk[j, 1] = _o.ntt_fwd(aj, all_mod)
-    return Keys(N, data_moduli, int(P), s, pk, evk)
+    return evk
+
+
+def galois_key(keys: "Keys", g: int, rng) -> np.ndarray:
+    """Rotation (Galois) key for the automorphism X -> X^g: the switching key
+    from s(X^g) to s, in the relinearization key's layout."""
+    all_mod = keys.data_moduli + [keys.P]
+    s_res = to_residues(keys.s, all_mod)
+    return _switching_key(s_res, _o.automorphism(s_res, g, all_mod), keys.data_moduli, keys.P, rng)
 
 
 def _mulmod_vec(x: np.ndarray, c: int, q: int) -> np.ndarray:

@@ -892,6 +892,66 @@ extern "C" he_status he_ct_add(uint64_t *ct_out, const uint64_t *ct_a, const uin
     return HE_OK;
 }
 
+static he_status check_galois(const he_context *ctx, uint32_t g)
+{
+    if (!(g & 1) || g >= 2 * ctx->N) return fail(HE_EINVAL, "Galois element %u is not odd and below 2N = %u", g, 2 * ctx->N);
+    return HE_OK;
+}
+
+extern "C" he_status he_ct_automorph(uint64_t *ct_out, const uint64_t *ct_in, uint32_t count, uint32_t components,
+                                     uint32_t galois_elt, const he_context *ctx, uint32_t level, he_stream_t stream)
+{
+    if (he_status s = check_level(ctx, level, false)) return s;
+    if (he_status s = check_galois(ctx, galois_elt)) return s;
+    if (he_status s = check_ptr(ct_out, "ct_out")) return s;
+    if (he_status s = check_ptr(ct_in, "ct_in")) return s;
+    if (ct_out == ct_in) return fail(HE_EINVAL, "the automorphism cannot work in place");
+    if (count == 0 || components == 0) return HE_OK;
+    const u64 words = (u64)count * components * (level + 1) * ctx->N;
+    he::k_ct_automorph<<<stream_grid(words, 256), 256, 0, (cudaStream_t)stream>>>(ct_out, ct_in, words,
+                                                                                  (u32)ctx->log_n, galois_elt);
+    HE_CUDA(cudaGetLastError());
+    return HE_OK;
+}
+
+// Rotate scratch: the three-component input (sigma(c0), 0, sigma(c1)) of the
+// key switch, then the key switch's own scratch (with the expanded mod-up).
+static size_t rotate_c3_words(const he_context *c, u32 n, u32 count) { return (size_t)3 * n * c->N * count; }
+
+extern "C" size_t he_rotate_scratch_bytes(const he_context *ctx, uint32_t level, uint32_t count)
+{
+    if (!ctx || !count) return 0;
+    return rotate_c3_words(ctx, level + 1, count) * 8 + he_mul_relin_scratch_bytes(ctx, level, count);
+}
+
+extern "C" he_status he_rotate(uint64_t *ct_out, const uint64_t *ct_in, uint32_t count, uint32_t galois_elt,
+                               const he_relin_key *galois_key, const he_context *ctx, uint32_t level, void *scratch,
+                               size_t scratch_bytes, he_stream_t stream)
+{
+    if (he_status s = check_level(ctx, level, false)) return s;
+    if (he_status s = check_galois(ctx, galois_elt)) return s;
+    if (he_status s = check_ptr(ct_out, "ct_out")) return s;
+    if (he_status s = check_ptr(ct_in, "ct_in")) return s;
+    if (count == 0) return HE_OK;
+    if (he_status s = check_ptr(scratch, "scratch")) return s;
+    const u32 n = level + 1;
+    const size_t c3_words = rotate_c3_words(ctx, n, count);
+    if (scratch_bytes < (c3_words + relin_words(ctx, n) * count) * 8) return fail(HE_EINVAL, "scratch too small");
+    u64 *c3 = (u64 *)scratch;
+    const size_t comp = (size_t)n * ctx->N;
+    cudaStream_t s = (cudaStream_t)stream;
+    // (sigma(c0), 0, sigma(c1)) per ciphertext
+    for (u32 c = 0; c < count; c++) {
+        if (he_status r = he_ct_automorph(c3 + (size_t)c * 3 * comp, ct_in + (size_t)c * 2 * comp, 1, 1, galois_elt,
+                                          ctx, level, stream)) return r;
+        HE_CUDA(cudaMemsetAsync(c3 + ((size_t)c * 3 + 1) * comp, 0, comp * 8, s));
+        if (he_status r = he_ct_automorph(c3 + ((size_t)c * 3 + 2) * comp, ct_in + ((size_t)c * 2 + 1) * comp, 1, 1,
+                                          galois_elt, ctx, level, stream)) return r;
+    }
+    return key_switch_common(ct_out, nullptr, nullptr, c3, count, galois_key, ctx, level, c3 + c3_words,
+                             scratch_bytes - c3_words * 8, stream, false);
+}
+
 extern "C" he_status he_ct_matmul_tensor(uint64_t *t_out, const uint64_t *a, const uint64_t *b, uint32_t m,
                                          uint32_t k, uint32_t n, const he_context *ctx, uint32_t level,
                                          he_stream_t stream)

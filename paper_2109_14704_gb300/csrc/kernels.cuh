@@ -257,6 +257,24 @@ __global__ void k_ct_add(u64 *out, const u64 *a, const u64 *b, u64 words, u32 lo
     }
 }
 
+// The automorphism X -> X^g (g odd) on NTT-domain polynomials of 2^log_n
+// words (any number of them, back to back). Output index i holds
+// a(psi^(2 brv(i) + 1)) (the order of he_ntt_fwd), so the image
+// sigma(a)(psi^(2 brv(i) + 1)) = a(psi^(g (2 brv(i) + 1))) is the input
+// word at index brv((g (2 brv(i) + 1) mod 2N - 1) / 2): a gather within
+// each polynomial, the same for every limb.
+__global__ void k_ct_automorph(u64 *out, const u64 *in, u64 words, u32 log_n, u32 g)
+{
+    const u32 N = 1u << log_n, mask2 = 2 * N - 1, sh = 32 - log_n;
+    for (u64 e = (u64)blockIdx.x * blockDim.x + threadIdx.x; e < words; e += (u64)gridDim.x * blockDim.x) {
+        const u32 i = (u32)e & (N - 1);
+        const u32 r = __brev(i) >> sh;
+        const u32 t = (u32)(((u64)g * (2 * r + 1)) & mask2);
+        const u32 src = __brev((t - 1) >> 1) >> sh;
+        out[e] = __ldg(reinterpret_cast<const unsigned long long *>(in + (e - i) + src));
+    }
+}
+
 // ============================================ encrypted matrix product ======
 // Tensor part of C += A B (Sec. IV-E matMul_mxnxk; Sec. II-A Mul): for each
 // limb and position, T[i][j] = sum_l (a0 b0, a0 b1 + a1 b0, a1 b1) over the

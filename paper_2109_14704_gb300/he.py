@@ -96,6 +96,11 @@ _SIGS = {
     "he_ct_add": (ctypes.c_int32, [_vp, _vp, _vp, ctypes.c_uint32, ctypes.c_uint32, _vp, ctypes.c_uint32, _vp]),
     "he_ct_matmul_tensor": (ctypes.c_int32, [_vp, _vp, _vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                                              _vp, ctypes.c_uint32, _vp]),
+    "he_ct_automorph": (ctypes.c_int32, [_vp, _vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, _vp,
+                                         ctypes.c_uint32, _vp]),
+    "he_rotate_scratch_bytes": (ctypes.c_size_t, [_vp, ctypes.c_uint32, ctypes.c_uint32]),
+    "he_rotate": (ctypes.c_int32, [_vp, _vp, ctypes.c_uint32, ctypes.c_uint32, _vp, _vp, ctypes.c_uint32, _vp,
+                                   ctypes.c_size_t, _vp]),
     "he_mul_relin_rescale_noalloc": (ctypes.c_int32, [_vp, _vp, _vp, ctypes.c_uint32, _vp, _vp, ctypes.c_uint32,
                                                       _vp]),
 }
@@ -336,6 +341,9 @@ class Context:
     def rescale_scratch_bytes(self, level: int) -> int:
         return int(load().he_rescale_scratch_bytes(self.handle, level))
 
+    def rotate_scratch_bytes(self, level: int, count: int) -> int:
+        return int(load().he_rotate_scratch_bytes(self.handle, level, count))
+
     def mul_relin_scratch_bytes(self, level: int, count: int) -> int:
         return int(load().he_mul_relin_scratch_bytes(self.handle, level, count))
 
@@ -441,6 +449,22 @@ def ct_matmul_tensor(t_out, a, b, m: int, k: int, n: int, ctx: Context, level: i
     w = 2 * (level + 1) * ctx.N
     _check(load().he_ct_matmul_tensor(_ptr(t_out, m * n * 3 * (level + 1) * ctx.N), _ptr(a, m * k * w),
                                       _ptr(b, k * n * w), m, k, n, ctx.handle, level, _stream(stream)))
+
+
+def ct_automorph(ct_out, ct_in, count: int, components: int, galois_elt: int, ctx: Context, level: int,
+                 stream=None):
+    """The automorphism X -> X^galois_elt on NTT-domain ciphertexts."""
+    w = count * components * (level + 1) * ctx.N
+    _check(load().he_ct_automorph(_ptr(ct_out, w), _ptr(ct_in, w), count, components, galois_elt, ctx.handle, level,
+                                  _stream(stream)))
+
+
+def rotate(ct_out, ct_in, count: int, galois_elt: int, galois_key: RelinKey, ctx: Context, level: int, scratch,
+           stream=None):
+    """Rotate: automorphism then key switch with the Galois key."""
+    w = count * 2 * (level + 1) * ctx.N
+    _check(load().he_rotate(_ptr(ct_out, w), _ptr(ct_in, w), count, galois_elt, galois_key.handle, ctx.handle, level,
+                            _ptr(scratch), scratch.numel() * 8, _stream(stream)))
 
 
 class NttPlan:

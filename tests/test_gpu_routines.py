@@ -156,3 +156,54 @@ def test_matmul_tensor_moduli_below_2_32():
     T = empty(m, n, 3, level + 1, N)
     he.ct_matmul_tensor(T, dev(A), dev(B), m, k, n, ctx, level)
     assert np.array_equal(host(T), oracle.matmul_tensor(A, B, data))
+
+
+@pytest.mark.parametrize("g_kind", ["rot1", "rot7", "conj"])
+def test_ct_automorph_matches_coefficient_domain(g_kind):
+    N, data, P, ctx, evk, key, r = _setup("small4k", 140)
+    level, count = 2, 2
+    qs = data[:level + 1]
+    g = {"rot1": 5, "rot7": pow(5, 7, 2 * N), "conj": 2 * N - 1}[g_kind]
+    ct = _cts(r, qs, N, count)
+    out = empty(count, 2, level + 1, N)
+    he.ct_automorph(out, dev(ct), count, 2, g, ctx, level)
+    got = host(out)
+    for c in range(count):
+        for k in range(2):
+            assert np.array_equal(got[c, k], oracle.ntt_automorphism(ct[c, k], g, qs)), (c, k)
+
+
+@pytest.mark.parametrize("fused", [False, True])
+def test_rotate_matches_oracle(fused):
+    N, data, P, ctx, evk, key, r = _setup("small4k", 150)
+    level, count, g = 3, 3, pow(5, 3, 2 * 4096)
+    qs = data[:level + 1]
+    ct = _cts(r, qs, N, count)
+    out = empty(count, 2, level + 1, N)
+    n = level + 1
+    nbytes = (3 * n + 3 * n + 2) * N * 8 * count if fused else ctx.rotate_scratch_bytes(level, count)
+    he.rotate(out, dev(ct), count, g, key, ctx, level, empty(nbytes // 8))   # evk serves as the Galois key
+    got = host(out)
+    for c in range(count):
+        assert np.array_equal(got[c], oracle.rotate(ct[c], g, evk, data, P, level)), c
+
+
+def test_rotate_real_encryption_rolls_slots():
+    N, bits, pbits = CHAINS["matrix8k"]
+    data, P = oracle.chain_primes(N, bits, pbits)
+    r = Rng(6)
+    keys = ckks.keygen(N, data, P, r)
+    k = 5
+    g = pow(5, k, 2 * N)
+    gk = ckks.galois_key(keys, g, r)
+    ctx = he.Context(N, data, P)
+    gkey = he.RelinKey(ctx, gk)
+    scale, L = 2.0 ** 40, len(data) - 1
+    z = r.complex_slots(N // 2)
+    ct = ckks.encrypt(ckks.encode_real(z, N, scale), keys, r)
+    out = empty(1, 2, L + 1, N)
+    he.rotate(out, dev(ct[None]), 1, g, gkey, ctx, L, empty(ctx.rotate_scratch_bytes(L, 1) // 8))
+    got = host(out)[0]
+    assert np.array_equal(got, oracle.rotate(ct, g, gk, data, P, L))
+    zr = ckks.decrypt_decode(got, keys, scale)
+    assert float(np.abs(zr - np.roll(z, -k)).max()) < 1e-5
