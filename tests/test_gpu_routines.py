@@ -207,3 +207,54 @@ def test_rotate_real_encryption_rolls_slots():
     assert np.array_equal(got, oracle.rotate(ct, g, gk, data, P, L))
     zr = ckks.decrypt_decode(got, keys, scale)
     assert float(np.abs(zr - np.roll(z, -k)).max()) < 1e-5
+
+
+def test_full_size_matrix_product_sampled():
+    """C += A B at 32 x 32 x 32, N = 8192, 60/40/40 + 60 (the benchmark's
+    launch configuration): three sampled outputs against the oracle."""
+    N, data, P, ctx, evk, key, r = _setup("matrix8k", 160)
+    m = k = n = 32
+    L = len(data) - 1
+    A = np.stack([_cts(r, data, N, k) for _ in range(m)])
+    B = np.stack([_cts(r, data, N, n) for _ in range(k)])
+    C = np.stack([_cts(r, data[:L], N, n) for _ in range(m)])
+    T = empty(m * n, 3, L + 1, N)
+    he.ct_matmul_tensor(T, dev(A), dev(B), m, k, n, ctx, L)
+    R = empty(m * n, 2, L, N)
+    he.relin_rescale(R, T, m * n, key, ctx, L, empty(ctx.mrr_scratch_bytes(L, m * n) // 8))
+    dC = dev(C)
+    he.ct_add(dC, dC, R, m * n, 2, ctx, L - 1)
+    got = host(dC).reshape(m, n, 2, L, N)
+    for (i, j) in ((0, 0), (13, 31), (31, 7)):
+        t = oracle.tensor(A[i, 0], B[0, j], data)
+        for l in range(1, k):
+            t = oracle.add(t, oracle.tensor(A[i, l], B[l, j], data), data)
+        ref = oracle.add(C[i, j], oracle.rescale(oracle.relin(t, evk, data, P, L), data, L), data[:L])
+        assert np.array_equal(got[i, j], ref), (i, j)
+
+
+def test_full_size_routines_sampled():
+    """The routine set at N = 32K, 8 limbs, batches of 16 (the benchmark's
+    configuration): two sampled ciphertexts per routine against the oracle."""
+    N = 32768
+    data, P = he.chain_primes(N, [60] + [50] * 7, 60)
+    ctx = he.Context(N, data, P)
+    r = Rng(170)
+    evk = np.stack([np.stack([r.uniform_limbs(data + [P], N) for _ in range(2)]) for _ in range(len(data))])
+    key = he.RelinKey(ctx, evk)
+    L, count = len(data) - 1, 16
+    A, B = _cts(r, data, N, count), _cts(r, data, N, count)
+    dA, dB = dev(A), dev(B)
+    sc = empty(max(ctx.mrr_scratch_bytes(L, count), ctx.rotate_scratch_bytes(L, count)) // 8)
+    out_l, out_r = empty(count, 2, L + 1, N), empty(count, 2, L, N)
+    g = pow(5, 1, 2 * N)
+    he.mul_relin(out_l, dA, dB, count, key, ctx, L, sc)
+    ml = host(out_l)
+    he.sqr_relin_rescale(out_r, dA, count, key, ctx, L, sc)
+    sq = host(out_r)
+    he.rotate(out_l, dA, count, g, key, ctx, L, sc)
+    rt = host(out_l)
+    for c in (0, 11):
+        assert np.array_equal(ml[c], oracle.relin(oracle.tensor(A[c], B[c], data), evk, data, P, L)), c
+        assert np.array_equal(sq[c], oracle.mul_relin_rescale(A[c], A[c], evk, data, P, L)), c
+        assert np.array_equal(rt[c], oracle.rotate(A[c], g, evk, data, P, L)), c
