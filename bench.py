@@ -176,6 +176,32 @@ def _time_steps(fn, steps, warmup, stream, barrier):
     return t0.elapsed_time(t1) / steps
 
 
+def _collectives(world: int, device):
+    """(barrier, max_over_ranks) over the initialised process group (any
+    backend; `device` holds the reduction tensor), or no-ops for one rank.
+    Replicas share nothing else: the timed step takes the slowest rank's
+    time and the job value counts every rank's work."""
+    if world <= 1:
+        return (lambda: None), (lambda x: x)
+    import torch
+    import torch.distributed as dist
+
+    def barrier():
+        dist.barrier()
+
+    def max_over_ranks(x):
+        t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    return barrier, max_over_ranks
+
+
+def job_value(world: int, units_per_rank: float, ms_max: float) -> float:
+    """Whole-job throughput: every rank's units over the slowest rank's time."""
+    return world * units_per_rank / (ms_max / 1e3)
+
+
 def run_ours(args, rank, world, local):
     import numpy as np
     import torch
@@ -188,20 +214,7 @@ def run_ours(args, rank, world, local):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
-
-        def barrier():
-            dist.barrier()
-
-        def max_over_ranks(x):
-            t = torch.tensor([x], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            return float(t.item())
-    else:
-        def barrier():
-            pass
-
-        def max_over_ranks(x):
-            return x
+    barrier, max_over_ranks = _collectives(world, dev)
 
     he.load()
     stream = torch.cuda.current_stream()
@@ -359,8 +372,8 @@ def run_ours(args, rank, world, local):
     frac_hbm = achieved_gbs / hbm_peak
     frac_alu = achieved_bfly / alu_peak
     bound_alu = frac_alu >= frac_hbm
-    value = world * 2 * limbs_total / (ms / 1e3)
-    e2e_value = world * 2 * limbs_total / (ms_e2e / 1e3)
+    value = job_value(world, 2 * limbs_total, ms)
+    e2e_value = job_value(world, 2 * limbs_total, ms_e2e)
     line = {
         "metric": METRIC,
         "value": value,
