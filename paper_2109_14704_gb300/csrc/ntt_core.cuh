@@ -11,9 +11,11 @@
 //   uses W = psi^brv(2^S + g) and pairs positions j and j + N / 2^(S+1).
 //   * The first log C stages pair positions in different CTAs. Each thread
 //     loads whole columns {t B + j : t < C} from global memory, runs the
-//     radix-C network in registers and scatters element t to CTA t through
-//     distributed shared memory (st.shared::cluster). This is the paper's
-//     "global memory" stage group, done without a second pass over HBM.
+//     radix-C network in registers and hands element t to CTA t through
+//     distributed shared memory: scattered with st.shared::cluster, or (16
+//     words per thread) kept locally for CTA t to read with
+//     ld.shared::cluster. This is the paper's "global memory" stage group,
+//     done without a second pass over HBM.
 //   * The remaining log B stages stay inside one CTA: rounds of up to LOG_E
 //     stages (radix E) in registers, exchanging through shared memory
 //     between rounds (the paper's SLM rounds, Sec. III-B; its best radix was
@@ -119,6 +121,13 @@ struct NttShape {
     static constexpr int NROUND = (LOG_B + LOG_E - 1) / LOG_E;
     static constexpr int LAST_R = LOG_B - LOG_E * (NROUND - 1);
     static constexpr u32 SMEM_BYTES = B * 8;
+    // Exchange of the forward transform's cross-CTA stages: push (each CTA
+    // stores its results into the owners' shared memory, one cluster
+    // barrier) or pull (each CTA keeps them, one cluster barrier, the owners
+    // read them remotely, and a second barrier before the block is reused,
+    // after the first register round). Pull measured 3 % faster with 16
+    // words per thread and 11 % slower with 8 (N = 2^15).
+    static constexpr bool FWD_PULL = LOG_E == 4;
     // CTAs per SM to aim for, from a register budget per thread: occupancy
     // pays for the transform (measured: radix-8 at 42 registers, three 512-
     // thread CTAs per SM, beats 64 registers by 8-9%; radix-16 at 64
@@ -251,6 +260,8 @@ __device__ __forceinline__ void fwd_round(u64 (&x)[Sh::E], u64 *s, u32 tid, u32 
 {
     using Rd = RoundOf<Sh, RI>;
     if constexpr (RI > 0) {
+        // pull form: the peers have pulled their words out of this block
+        if constexpr (RI == 1 && Sh::LOG_C > 0 && Sh::FWD_PULL) cluster_sync_war();
         round_store_smem<Sh, RoundOf<Sh, RI - 1>>(x, s, tid);
         __syncthreads();
         round_load_smem<Sh, Rd>(x, s, tid);
@@ -266,8 +277,9 @@ __device__ __forceinline__ void fwd_rounds(u64 (&x)[Sh::E], u64 *s, u32 tid, u32
 }
 
 // Cross-CTA stages of the forward transform: load columns, radix-C network,
-// scatter into the owning CTAs' shared memory (ranks rbase .. rbase + C - 1
-// of the cluster), cluster barrier.
+// then either scatter into the owning CTAs' shared memory (ranks rbase ..
+// rbase + C - 1 of the cluster) or keep the results for the owners to pull
+// (Sh::FWD_PULL), cluster barrier.
 template <class Sh, class Load>
 __device__ __forceinline__ void fwd_cross(u64 *s, u32 tid, u32 m, u32 rbase, const ulonglong2 *tw,
                                           const PrimeConst &pc, Load &load)
@@ -294,9 +306,17 @@ __device__ __forceinline__ void fwd_cross(u64 *s, u32 tid, u32 m, u32 rbase, con
                 ct_butterfly(v[t], v[t + half], w.x, w.y, pc);
             }
         }
-        const u32 a = s_base + swz<Sh::LOG_E>((u32)j) * 8u;
+        if constexpr (Sh::FWD_PULL) {
+            // kept in this CTA's block, word t of column offset o at
+            // t B / C + o, for the owner of the column's words to pull
+            const int o = c * (int)Sh::T + (int)tid;
 #pragma unroll
-        for (u32 t = 0; t < C; t++) st_cluster(map_to_rank(a, rbase + t), v[t]);
+            for (u32 t = 0; t < C; t++) s[((int)t << (Sh::LOG_B - Sh::LOG_C)) + o] = v[t];
+        } else {
+            const u32 a = s_base + swz<Sh::LOG_E>((u32)j) * 8u;
+#pragma unroll
+            for (u32 t = 0; t < C; t++) st_cluster(map_to_rank(a, rbase + t), v[t]);
+        }
     }
     cluster_sync_all();
 }
@@ -317,7 +337,21 @@ __device__ __forceinline__ void ntt_fwd_block(u64 *s, u32 m, u32 rbase, const ul
     using R0 = RoundOf<Sh, 0>;
     if constexpr (Sh::LOG_C > 0) {
         fwd_cross<Sh>(s, tid, m, rbase, tw, pc, load);
-        round_load_smem<Sh, R0>(x, s, tid);
+        if constexpr (Sh::FWD_PULL) {
+            constexpr int LOG_W = Sh::LOG_B - Sh::LOG_C;
+            const u32 s_base = smem_u32(s);
+#pragma unroll
+            for (int i = 0; i < R0::SUB; i++)
+#pragma unroll
+                for (int u = 0; u < (1 << R0::R); u++) {
+                    const int P = round_pos<R0>(tid, i, u);
+                    const u32 slot = (m << LOG_W) + ((u32)P & ((1u << LOG_W) - 1));
+                    x[i * (1 << R0::R) + u] = ld_cluster(map_to_rank(s_base + slot * 8u, rbase + ((u32)P >> LOG_W)));
+                }
+            if constexpr (Sh::NROUND == 1) cluster_sync_war();   // peers pulled from this block
+        } else {
+            round_load_smem<Sh, R0>(x, s, tid);
+        }
     } else {
 #pragma unroll
         for (int i = 0; i < R0::SUB; i++)
