@@ -28,6 +28,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -46,9 +47,9 @@ MRR_BITS = [60] + [50] * 6
 MRR_COUNT = 64
 METRIC = "NTT limbs/s at N=2^15 + HE mul-relin-rescale/s, batched vs plain; p99 latency"
 # DRAM bytes (read + write) of one forward launch of the 1024 x 8 x 2^15
-# batch in the radix-8 shape below: an ncu capture of the same kernel on 256
-# instances (542019328 B read, 484354560 B written) scaled by 4.
-FWD_TRAFFIC = {"shape": [12, 3, 0], "bytes": 4 * (542019328 + 484354560)}
+# batch in the radix-16 shape below: an ncu capture of the same kernel on 256
+# instances (541124352 B read, 481917696 B written) scaled by 4.
+FWD_TRAFFIC = {"shape": [12, 4, 0], "bytes": 4 * (541124352 + 481917696)}
 # The production forward butterfly keeps the IMAD (fmaheavy) pipe busy for
 # 0.2536 cycles per butterfly per SM: ncu on the register-resident probe
 # (1216 x 256 threads x 16 x 1024 butterflies) counts that pipe 94.2 % active
@@ -73,7 +74,7 @@ def _args():
                     help="NTT instances of --profile-case ntt, ciphertext pairs of --profile-case mrr")
     ap.add_argument("--shape", default="",
                     help="log_block,log_thread_words[,persistent] for --profile-case ntt (or fwd/inv)")
-    ap.add_argument("--skip", default="", help="comma list of sub-benchmarks to skip: uneven,matrix,routines,serving")
+    ap.add_argument("--skip", default="", help="comma list of sub-benchmarks to skip: uneven,matrix,routines,encode,serving")
     ap.add_argument("--serve-requests", type=int, default=4000)
     ap.add_argument("--no-tune-cache", action="store_true", help="always re-run the autotuner")
     a = ap.parse_args()
@@ -323,6 +324,7 @@ def run_ours(args, rank, world, local):
     uneven = bench_uneven(args, stream, barrier) if "uneven" not in args.skip else None
     matrix = bench_matrix(args, stream, barrier) if "matrix" not in args.skip else None
     routines = bench_routines(args, stream, barrier) if "routines" not in args.skip else None
+    encode = bench_encode(args, stream, barrier) if "encode" not in args.skip else None
 
     # end to end through host buffers: one he_ntt_host call per step (copy in,
     # forward, inverse, copy out, pipelined over chunks of 32 polynomials)
@@ -409,6 +411,7 @@ def run_ours(args, rank, world, local):
         "uneven_batch": uneven,
         "matrix_mul_relin_rescale": matrix,
         "routines": routines,
+        "encode_decode": encode,
         "serving": serve,
         "mul_relin_rescale": {
             "workload": "N=16384, data primes 60+6x50, special 60, 64 ciphertext pairs, level 6 -> 5",
@@ -636,6 +639,65 @@ def bench_routines(args, stream, barrier):
         ms = _time_steps(fn, max(3, args.steps // 2), 2, stream, barrier)
         res[name] = {"ms_per_batch": ms, "per_s": count / (ms / 1e3)}
     return res
+
+
+def bench_encode(args, stream, barrier):
+    """Device Encode / Decode (Sec. II-A) at the routine-set size: N = 2^15,
+    level 7 (8 limbs: 60 + 7 x 50 bits), batches of 64 messages of 16384
+    complex slots (scale 2^40). The components that the library exposes are
+    timed alone: the CRT lift of decoding, and the NTTs of the same limbs;
+    the FP64 probe gives the rate that bounds the slot FFT."""
+    import numpy as np
+    import torch
+
+    from paper_2109_14704_gb300 import he
+    from paper_2109_14704_gb300.synth import Rng
+
+    N, count, level, scale = 32768, 64, 7, 2.0 ** 40
+    n = N // 2
+    data, P = he.chain_primes(N, [60] + [50] * 7, 60)
+    ctx = he.Context(N, data, P)
+    enc = he.Encoder(ctx)
+    tables = he.NttTables(N, data)
+    r = Rng(9)
+    z = torch.from_numpy(np.stack([r.complex_slots(n) for _ in range(count)])).cuda()
+    zo = torch.empty_like(z)
+    pt = torch.empty((count, level + 1, N), dtype=torch.int64, device="cuda")
+    coef = torch.empty_like(pt)
+    m = torch.empty((count, N), dtype=torch.float64, device="cuda")
+    sc = torch.empty(max(enc.encode_scratch_bytes(count), enc.decode_scratch_bytes(level, count)) // 8,
+                     dtype=torch.int64, device="cuda")
+    steps = max(3, args.steps // 2)
+    ms_enc = _time_steps(lambda: enc.encode(pt, z, count, scale, level, sc, stream=stream), steps, 2, stream, barrier)
+    ms_dec = _time_steps(lambda: enc.decode(zo, pt, count, scale, level, sc, stream=stream), steps, 2, stream,
+                         barrier)
+    torch.cuda.synchronize()
+    err = float(((zo - z).abs().max() / z.abs().max()).item())
+    coef.copy_(pt)
+    ms_crt = _time_steps(lambda: enc.crt_compose(m, coef, count, level, stream=stream), steps, 2, stream, barrier)
+    ms_fwd = _time_steps(lambda: he.ntt_fwd(coef, N, level + 1, count, tables, stream=stream), steps, 2, stream,
+                         barrier)
+    ms_inv = _time_steps(lambda: he.ntt_inv(coef, N, level + 1, count, tables, stream=stream), steps, 2, stream,
+                         barrier)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    sink = torch.empty(sms * 8 * 256, dtype=torch.float64, device="cuda")
+    iters = 4096
+    ms_probe = _time_steps(lambda: he.fp64_probe(sink, sms * 8, 256, iters, stream=stream), 5, 2, stream, barrier)
+    fp64_peak = sms * 8 * 256 * iters * 16 / (ms_probe / 1e3) / 1e12
+    fft_flop = 5.0 * n * math.log2(n) * count
+    ms_fft_enc = ms_enc - ms_fwd
+    return {
+        "workload": f"N=32768, level {level} ({level + 1} limbs: 60 + 7 x 50 bits), {count} messages of {n} "
+                    "complex slots, scale 2^40",
+        "encode": {"ms_per_batch": ms_enc, "per_s": count / (ms_enc / 1e3)},
+        "decode": {"ms_per_batch": ms_dec, "per_s": count / (ms_dec / 1e3)},
+        "round_trip_max_rel_err": err,
+        "components_ms": {"ntt_fwd": ms_fwd, "ntt_inv": ms_inv, "crt_lift": ms_crt,
+                          "encode_minus_ntt": ms_fft_enc, "decode_minus_intt_crt": ms_dec - ms_inv - ms_crt},
+        "fp64": {"probe_tflops": fp64_peak,
+                 "encode_fft_tflops": fft_flop / (ms_fft_enc / 1e3) / 1e12,
+                 "fft_flop_per_batch": fft_flop},
+    }
 
 
 def bench_serving(args):

@@ -300,6 +300,59 @@ he_status he_mul_relin_rescale_noalloc(uint64_t *ct_out, const uint64_t *ct_a, c
                                        uint32_t count, const he_relin_key *key, const he_context *ctx,
                                        uint32_t level, he_stream_t stream);
 
+/* ---- encoding and decoding (Sec. II-A Encode / Decode) ------------------------ */
+
+/* Slot vectors are n = N/2 complex numbers, stored as interleaved FP64
+ * (re, im) pairs: slots[(c * n + j) * 2 + {0, 1}] for message c. Slot j is
+ * the value of the plaintext polynomial m at the root zeta^(5^j mod 2N),
+ * zeta = exp(i pi / N) (Sec. II-A: the canonical embedding restricted to one
+ * root of each conjugate pair). The paper encodes and decodes on the host
+ * (Sec. III); these calls do it on the device with an FP64 FFT of n points. */
+typedef struct he_encoder he_encoder;    /* FFT and CRT tables of a context */
+
+/* Builds the tables for every level of `ctx` (which must outlive the
+ * encoder). Synchronises. */
+he_status he_encoder_create(const he_context *ctx, he_encoder **out);
+he_status he_encoder_destroy(he_encoder *enc);
+
+/* Device scratch of he_encode / he_decode for `count` messages at `level`:
+ * encode count * N * 8 bytes; decode count * (level + 3) * N * 8 bytes. */
+size_t he_encode_scratch_bytes(const he_encoder *enc, uint32_t count);
+size_t he_decode_scratch_bytes(const he_encoder *enc, uint32_t level, uint32_t count);
+
+/* Encode: for each of `count` messages, the real polynomial m with
+ * m(zeta^(5^j)) = scale * slots_j and m(zeta^(-5^j)) = its conjugate,
+ * rounded coefficient by coefficient to the nearest integer (ties to even),
+ * reduced modulo q_0..q_level and transformed to the NTT domain:
+ * pt_out[(c * (level + 1) + l) * N + i] (the layout of a ciphertext
+ * component). The FFT rounds like any FP64 computation: a coefficient whose
+ * exact value lies within about 2^-52 * scale * max|slots| * log2(N) of a
+ * half-integer may round to either neighbour. scale must be finite and
+ * positive and every scaled coefficient below 2^62 in magnitude (larger
+ * ones give unspecified residues). slots: device, count * N/2 pairs;
+ * scratch: he_encode_scratch_bytes. HE_EINVAL for a bad level, scale,
+ * pointer or short scratch. */
+he_status he_encode(const he_encoder *enc, uint64_t *pt_out, const double *slots, uint32_t count,
+                    double scale, uint32_t level, void *scratch, size_t scratch_bytes, he_stream_t stream);
+
+/* Decode: the inverse NTT of each plaintext pt[c] (count messages of
+ * level + 1 limbs, NTT domain, canonical), the CRT lift of every
+ * coefficient to the centred integer in [-(Q-1)/2, (Q-1)/2], Q = q_0 ...
+ * q_level, its nearest double, the slot values m(zeta^(5^j)) of that real
+ * polynomial (FP64 FFT), divided by scale, into slots_out (device,
+ * count * N/2 pairs). pt is not modified. A coefficient beyond the double
+ * range becomes +-inf. scratch: he_decode_scratch_bytes. */
+he_status he_decode(const he_encoder *enc, double *slots_out, const uint64_t *pt, uint32_t count,
+                    double scale, uint32_t level, void *scratch, size_t scratch_bytes, he_stream_t stream);
+
+/* The CRT step of decoding alone: out[c * N + i] = the nearest double
+ * (round to nearest even) of the centred integer whose residues modulo
+ * q_0..q_level are coeffs[(c * (level + 1) + l) * N + i] (coefficient
+ * domain, canonical). out and coeffs are device buffers, 8-byte aligned
+ * and 16-byte aligned respectively. */
+he_status he_crt_compose(const he_encoder *enc, double *out, const uint64_t *coeffs, uint32_t count,
+                         uint32_t level, he_stream_t stream);
+
 /* ---- batched plans (Sec. III-B parallelism over limbs and instances) -------- */
 
 /* One polynomial of a batched NTT: `limbs` limbs of degree N at `data`
@@ -382,6 +435,12 @@ he_status he_ntt_host(const uint64_t *in_host, uint64_t *out_host, uint32_t N, u
  * compute roof against which the transforms are reported. */
 he_status he_butterfly_probe(uint64_t *sink, uint32_t blocks, uint32_t threads, uint32_t iters,
                              he_stream_t stream);
+
+/* FP64 throughput probe: blocks x threads threads each run 8 independent
+ * chains of `iters` fused multiply-adds in registers (16 FLOP per step) and
+ * write one double to sink[blocks * threads] (device). Timing the launch
+ * gives the FP64 rate that bounds the slot FFT of he_encode / he_decode. */
+he_status he_fp64_probe(double *sink, uint32_t blocks, uint32_t threads, uint32_t iters, he_stream_t stream);
 
 /* The transform butterflies applied elementwise to device arrays of n
  * entries, for checking their contract (Algorithm 1) on the device. Forward

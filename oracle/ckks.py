@@ -32,9 +32,10 @@ def slot_positions(N: int) -> tuple[np.ndarray, np.ndarray]:
     return (e - 1) // 2, (2 * N - e - 1) // 2
 
 
-def encode_real(z: np.ndarray, N: int, scale: float) -> np.ndarray:
-    """Encode (Sec. II-A): the real polynomial m with m(zeta^(5^j)) =
-    scale * z_j (before rounding), rounded to integers (int64)."""
+def encode_unrounded(z: np.ndarray, N: int, scale: float) -> np.ndarray:
+    """Encode (Sec. II-A) before rounding: the real coefficients of the
+    polynomial m with m(zeta^(5^j)) = scale * z_j and m(zeta^(-5^j)) =
+    scale * conj(z_j), as float64."""
     pos, cpos = slot_positions(N)
     E = np.zeros(N, dtype=np.complex128)
     E[pos] = scale * z
@@ -42,7 +43,12 @@ def encode_real(z: np.ndarray, N: int, scale: float) -> np.ndarray:
     k = np.arange(N)
     zeta_k = np.exp(1j * np.pi * k / N)
     m = np.fft.fft(E) / N / zeta_k
-    return np.rint(m.real).astype(np.int64)
+    return m.real
+
+
+def encode_real(z: np.ndarray, N: int, scale: float) -> np.ndarray:
+    """Encode (Sec. II-A): encode_unrounded rounded to integers (int64)."""
+    return np.rint(encode_unrounded(z, N, scale)).astype(np.int64)
 
 
 def eval_slots(m: np.ndarray, N: int) -> np.ndarray:

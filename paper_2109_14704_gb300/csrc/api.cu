@@ -10,6 +10,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <atomic>
 #include <map>
 #include <mutex>
@@ -970,6 +971,243 @@ extern "C" he_status he_ct_matmul_tensor(uint64_t *t_out, const uint64_t *a, con
     return HE_OK;
 }
 
+// ------------------------------------------------------------- encoding
+
+struct he_encoder {
+    const he_context *ctx = nullptr;
+    u32 log_n = 0;                  // FFT length n = N / 2
+    double2 *d_omega = nullptr;     // exp(-2 pi i j / n)
+    double2 *d_zeta = nullptr;      // exp(i pi k / N), k < n
+    u32 *d_slot = nullptr;          // slot of FFT index t
+    u64 *d_primes = nullptr;        // (q_i, floor(2^64 / q_i)), i < n_data
+    u64 *d_crt = nullptr;           // per-level CRT tables
+    std::vector<size_t> crt_off;    // word offset of level l's table
+    std::vector<u32> crt_nw;        // words per integer at level l
+};
+
+// Little-endian multi-word integers for the host-side CRT tables.
+static void mw_mul_small(std::vector<u64> &a, u64 m)
+{
+    u64 carry = 0;
+    for (u64 &w : a) {
+        const u128 t = (u128)w * m + carry;
+        w = (u64)t;
+        carry = (u64)(t >> 64);
+    }
+    if (carry) a.push_back(carry);
+}
+
+static int mw_bits(const std::vector<u64> &a)
+{
+    for (size_t i = a.size(); i-- > 0;)
+        if (a[i]) return (int)(64 * i) + bit_length(a[i]);
+    return 0;
+}
+
+static void encoder_free(he_encoder *e)
+{
+    cudaFree(e->d_omega);
+    cudaFree(e->d_zeta);
+    cudaFree(e->d_slot);
+    cudaFree(e->d_primes);
+    cudaFree(e->d_crt);
+    delete e;
+}
+
+extern "C" he_status he_encoder_create(const he_context *ctx, he_encoder **out)
+{
+    if (!out) return fail(HE_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!ctx) return fail(HE_EINVAL, "context is NULL");
+    const u32 N = ctx->N, n = N / 2;
+    const long double pi = 3.141592653589793238462643383279502884L;
+    std::vector<double2> omega(n), zeta(n);
+    for (u32 j = 0; j < n; j++) {
+        const long double a = 2 * pi * (long double)j / (long double)n;
+        omega[j] = make_double2((double)cosl(a), (double)-sinl(a));
+        const long double b = pi * (long double)j / (long double)N;
+        zeta[j] = make_double2((double)cosl(b), (double)sinl(b));
+    }
+    std::vector<u32> slot(n);
+    u64 e5 = 1;
+    for (u32 j = 0; j < n; j++) {   // 5^j mod 2N = 4 t + 1
+        slot[(e5 - 1) / 4] = j;
+        e5 = e5 * 5 % (2 * (u64)N);
+    }
+    std::vector<u64> primes(2 * (size_t)ctx->n_data);
+    for (u32 i = 0; i < ctx->n_data; i++) {
+        primes[2 * i] = ctx->data[i];
+        primes[2 * i + 1] = shoup(1, ctx->data[i]);
+    }
+    // CRT tables per level l (limbs q_0..q_l): Q, (Q - 1) / 2, Q / q_i,
+    // then {q_i, (Q / q_i)^-1 mod q_i, its Shoup quotient, bits of 1 / q_i}
+    he_encoder *e = new he_encoder;
+    e->ctx = ctx;
+    e->log_n = (u32)(ctx->log_n - 1);
+    std::vector<u64> crt;
+    for (u32 l = 0; l < ctx->n_data; l++) {
+        const u32 limbs = l + 1;
+        std::vector<u64> Q{1};
+        for (u32 i = 0; i < limbs; i++) mw_mul_small(Q, ctx->data[i]);
+        const u32 nw = he::crt_words((u32)((mw_bits(Q) + 6 + 63) / 64));
+        if (!nw) {
+            delete e;
+            return fail(HE_EUNSUPPORTED, "modulus chain too long for the CRT lift (level %u)", l);
+        }
+        e->crt_off.push_back(crt.size());
+        e->crt_nw.push_back(nw);
+        auto put = [&](const std::vector<u64> &x) {
+            for (u32 w = 0; w < nw; w++) crt.push_back(w < x.size() ? x[w] : 0);
+        };
+        put(Q);
+        std::vector<u64> Qh(Q);
+        for (size_t w = 0; w < Qh.size(); w++) Qh[w] = (Qh[w] >> 1) | (w + 1 < Qh.size() ? Qh[w + 1] << 63 : 0);
+        put(Qh);
+        for (u32 i = 0; i < limbs; i++) {
+            std::vector<u64> Qi{1};
+            for (u32 j = 0; j < limbs; j++)
+                if (j != i) mw_mul_small(Qi, ctx->data[j]);
+            put(Qi);
+        }
+        for (u32 i = 0; i < limbs; i++) {
+            const u64 q = ctx->data[i];
+            u64 r = 1;
+            for (u32 j = 0; j < limbs; j++)
+                if (j != i) r = h_mul(r, ctx->data[j] % q, q);
+            const u64 inv = h_inv(r, q);
+            const double rq = 1.0 / (double)q;
+            u64 bits;
+            memcpy(&bits, &rq, 8);
+            crt.insert(crt.end(), {q, inv, shoup(inv, q), bits});
+        }
+    }
+    cudaError_t ce = cudaSuccess;
+    auto up = [&](auto **dst, const auto &src) {
+        if (ce != cudaSuccess) return;
+        const size_t bytes = src.size() * sizeof(src[0]);
+        ce = cudaMalloc(dst, bytes);
+        if (ce == cudaSuccess) ce = cudaMemcpy(*dst, src.data(), bytes, cudaMemcpyHostToDevice);
+    };
+    up(&e->d_omega, omega);
+    up(&e->d_zeta, zeta);
+    up(&e->d_slot, slot);
+    up(&e->d_primes, primes);
+    up(&e->d_crt, crt);
+    if (ce != cudaSuccess) {
+        encoder_free(e);
+        return cuda_fail(ce, "encoder tables");
+    }
+    *out = e;
+    return HE_OK;
+}
+
+extern "C" he_status he_encoder_destroy(he_encoder *enc)
+{
+    if (!enc) return fail(HE_EINVAL, "encoder is NULL");
+    encoder_free(enc);
+    return HE_OK;
+}
+
+extern "C" size_t he_encode_scratch_bytes(const he_encoder *enc, uint32_t count)
+{
+    return enc ? (size_t)count * enc->ctx->N * 8 : 0;
+}
+
+extern "C" size_t he_decode_scratch_bytes(const he_encoder *enc, uint32_t level, uint32_t count)
+{
+    return enc ? (size_t)count * (level + 3) * enc->ctx->N * 8 : 0;
+}
+
+static he_status check_encode_args(const he_encoder *enc, uint32_t level, double scale)
+{
+    if (!enc) return fail(HE_EINVAL, "encoder is NULL");
+    if (he_status s = check_level(enc->ctx, level, false)) return s;
+    if (!(scale > 0) || !std::isfinite(scale)) return fail(HE_EINVAL, "scale must be finite and positive");
+    return HE_OK;
+}
+
+static he::FftArgs fft_args(const he_encoder *enc, u32 count, u32 limbs, double scale)
+{
+    he::FftArgs a = {};
+    a.omega = enc->d_omega;
+    a.zeta = enc->d_zeta;
+    a.slot_of = enc->d_slot;
+    a.primes = enc->d_primes;
+    a.scale = scale;
+    a.inv_n = 1.0 / (double)(1u << enc->log_n);
+    a.log_n = enc->log_n;
+    a.log_n1 = enc->log_n / 2;
+    a.limbs = limbs;
+    a.count = count;
+    return a;
+}
+
+extern "C" he_status he_encode(const he_encoder *enc, uint64_t *pt_out, const double *slots, uint32_t count,
+                               double scale, uint32_t level, void *scratch, size_t scratch_bytes, he_stream_t stream)
+{
+    if (he_status s = check_encode_args(enc, level, scale)) return s;
+    if (he_status s = check_ptr(pt_out, "pt_out")) return s;
+    if (he_status s = check_ptr(slots, "slots")) return s;
+    if (count == 0) return HE_OK;
+    if (he_status s = check_ptr(scratch, "scratch")) return s;
+    if (scratch_bytes < he_encode_scratch_bytes(enc, count)) return fail(HE_EINVAL, "scratch too small");
+    if ((u64)count * (level + 1) * enc->ctx->N >= (1ull << 40)) return fail(HE_EINVAL, "batch too large");
+    he::FftArgs a = fft_args(enc, count, level + 1, scale);
+    a.z_in = (const double2 *)slots;
+    a.pt_out = pt_out;
+    a.u = (double2 *)scratch;
+    HE_CUDA(he::launch_encode_fft(a, (cudaStream_t)stream));
+    return ntt_launch(uniform_launch(pt_out, level + 1, count, enc->ctx->tables), enc->ctx->log_n, false,
+                      (cudaStream_t)stream);
+}
+
+static he_status crt_compose(const he_encoder *enc, double *out, const uint64_t *coeffs, uint32_t count, uint32_t level,
+                             cudaStream_t s)
+{
+    const u64 total = (u64)count * enc->ctx->N;
+    HE_CUDA(he::launch_crt_compose(out, coeffs, enc->d_crt + enc->crt_off[level], enc->crt_nw[level],
+                                   (u32)enc->ctx->log_n, level + 1, total, stream_grid(total, 128), s));
+    return HE_OK;
+}
+
+extern "C" he_status he_crt_compose(const he_encoder *enc, double *out, const uint64_t *coeffs, uint32_t count,
+                                    uint32_t level, he_stream_t stream)
+{
+    if (!enc) return fail(HE_EINVAL, "encoder is NULL");
+    if (he_status s = check_level(enc->ctx, level, false)) return s;
+    if (!out || ((uintptr_t)out & 7)) return fail(HE_EINVAL, "out is NULL or not 8-byte aligned");
+    if (he_status s = check_ptr(coeffs, "coeffs")) return s;
+    if (count == 0) return HE_OK;
+    return crt_compose(enc, out, coeffs, count, level, (cudaStream_t)stream);
+}
+
+extern "C" he_status he_decode(const he_encoder *enc, double *slots_out, const uint64_t *pt, uint32_t count,
+                               double scale, uint32_t level, void *scratch, size_t scratch_bytes, he_stream_t stream)
+{
+    if (he_status s = check_encode_args(enc, level, scale)) return s;
+    if (he_status s = check_ptr(slots_out, "slots_out")) return s;
+    if (he_status s = check_ptr(pt, "pt")) return s;
+    if (count == 0) return HE_OK;
+    if (he_status s = check_ptr(scratch, "scratch")) return s;
+    if (scratch_bytes < he_decode_scratch_bytes(enc, level, count)) return fail(HE_EINVAL, "scratch too small");
+    if ((u64)count * (level + 1) * enc->ctx->N >= (1ull << 40)) return fail(HE_EINVAL, "batch too large");
+    const he_context *ctx = enc->ctx;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t words = (size_t)count * (level + 1) * ctx->N;
+    u64 *coef = (u64 *)scratch;                            // [count][level + 1][N]
+    double *m = (double *)(coef + words);                  // [count][N]
+    double2 *u = (double2 *)(m + (size_t)count * ctx->N);  // [count][N / 2]
+    HE_CUDA(cudaMemcpyAsync(coef, pt, words * 8, cudaMemcpyDeviceToDevice, s));
+    if (he_status r = ntt_launch(uniform_launch(coef, level + 1, count, ctx->tables), ctx->log_n, true, s)) return r;
+    if (he_status r = crt_compose(enc, m, coef, count, level, s)) return r;
+    he::FftArgs a = fft_args(enc, count, level + 1, 1.0 / scale);
+    a.m_in = m;
+    a.z_out = (double2 *)slots_out;
+    a.u = u;
+    HE_CUDA(he::launch_decode_fft(a, s));
+    return HE_OK;
+}
+
 // ------------------------------------------------------------- measurement
 
 // Register-resident butterfly probe: each thread runs `iters` rounds of 8
@@ -1005,6 +1243,34 @@ extern "C" he_status he_butterfly_probe(uint64_t *sink, uint32_t blocks, uint32_
     const u64 w = 123456789012345ull % p;
     k_butterfly_probe<<<blocks, threads, 0, (cudaStream_t)stream>>>(sink, prime_const(p, 1u << 15, w), w,
                                                                     shoup(w, p), iters);
+    HE_CUDA(cudaGetLastError());
+    return HE_OK;
+}
+
+// FP64 throughput probe: each thread runs 8 independent chains of `iters`
+// fused multiply-adds (x <- x a + b) in registers, 16 FLOP per step, and
+// writes one double. Timing the launch gives the FP64 rate that bounds the
+// slot FFT of encoding and decoding.
+__global__ void k_fp64_probe(double *sink, u32 iters, double a, double b)
+{
+    double x[8];
+#pragma unroll
+    for (int i = 0; i < 8; i++) x[i] = (double)(threadIdx.x + i) * 1e-3;
+    for (u32 it = 0; it < iters; it++) {
+#pragma unroll
+        for (int i = 0; i < 8; i++) x[i] = fma(x[i], a, b);
+    }
+    double acc = 0;
+#pragma unroll
+    for (int i = 0; i < 8; i++) acc += x[i];
+    sink[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = acc;
+}
+
+extern "C" he_status he_fp64_probe(double *sink, uint32_t blocks, uint32_t threads, uint32_t iters, he_stream_t stream)
+{
+    if (!sink || ((uintptr_t)sink & 7)) return fail(HE_EINVAL, "sink is NULL or not 8-byte aligned");
+    if (!blocks || !threads || threads > 1024 || (threads & 31)) return fail(HE_EINVAL, "bad probe shape");
+    k_fp64_probe<<<blocks, threads, 0, (cudaStream_t)stream>>>(sink, iters, 0.999999, 1e-7);
     HE_CUDA(cudaGetLastError());
     return HE_OK;
 }

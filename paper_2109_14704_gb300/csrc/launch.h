@@ -117,4 +117,28 @@ struct DegreeOps {
 
 const DegreeOps *degree_ops(int log_n);
 
+// Encoding and decoding (encode.cu): the slot FFT of n = N/2 points in two
+// passes (n = n1 n2, n1 = 2^log_n1), fused with the slot permutation and
+// scaling at one end and the twist by zeta^k at the other.
+struct FftArgs {
+    const double2 *z_in;     // encode: slots [count][n]
+    double2 *z_out;          // decode: slots [count][n]
+    const double *m_in;      // decode: centred coefficients [count][N]
+    u64 *pt_out;             // encode: coefficient residues [count][limbs][N]
+    double2 *u;              // scratch between the passes [count][n]
+    const double2 *omega;    // exp(-2 pi i j / n), j < n
+    const double2 *zeta;     // exp(i pi k / N), k < n
+    const u32 *slot_of;      // slot j of FFT index t_j = (5^j mod 2N - 1) / 4
+    const u64 *primes;       // encode: (q_i, floor(2^64 / q_i)), i < limbs
+    double scale;            // encode: Delta; decode: 1 / Delta
+    double inv_n;            // 1 / n
+    u32 log_n, log_n1, limbs, count;
+};
+cudaError_t launch_encode_fft(const FftArgs &a, cudaStream_t s);
+cudaError_t launch_decode_fft(const FftArgs &a, cudaStream_t s);
+// Words of the CRT kernel's multi-word integers for `need` words (0: too many).
+u32 crt_words(u32 need);
+cudaError_t launch_crt_compose(double *out, const u64 *coef, const u64 *tab, u32 nw, u32 log_N, u32 limbs, u64 total,
+                               u32 blocks, cudaStream_t s);
+
 }  // namespace he

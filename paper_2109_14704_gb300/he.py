@@ -103,6 +103,16 @@ _SIGS = {
                                    ctypes.c_size_t, _vp]),
     "he_mul_relin_rescale_noalloc": (ctypes.c_int32, [_vp, _vp, _vp, ctypes.c_uint32, _vp, _vp, ctypes.c_uint32,
                                                       _vp]),
+    "he_encoder_create": (ctypes.c_int32, [_vp, ctypes.POINTER(_vp)]),
+    "he_encoder_destroy": (ctypes.c_int32, [_vp]),
+    "he_encode_scratch_bytes": (ctypes.c_size_t, [_vp, ctypes.c_uint32]),
+    "he_decode_scratch_bytes": (ctypes.c_size_t, [_vp, ctypes.c_uint32, ctypes.c_uint32]),
+    "he_encode": (ctypes.c_int32, [_vp, _vp, _vp, ctypes.c_uint32, ctypes.c_double, ctypes.c_uint32, _vp,
+                                   ctypes.c_size_t, _vp]),
+    "he_decode": (ctypes.c_int32, [_vp, _vp, _vp, ctypes.c_uint32, ctypes.c_double, ctypes.c_uint32, _vp,
+                                   ctypes.c_size_t, _vp]),
+    "he_crt_compose": (ctypes.c_int32, [_vp, _vp, _vp, ctypes.c_uint32, ctypes.c_uint32, _vp]),
+    "he_fp64_probe": (ctypes.c_int32, [_vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, _vp]),
 }
 
 
@@ -159,6 +169,20 @@ def _ptr(x, words: int | None = None):
         raise ValueError("expected 64-bit words (int64 or uint64)")
     if words is not None and x.numel() < words:
         raise ValueError(f"device tensor holds {x.numel()} words, the call needs {words}")
+    return x.data_ptr()
+
+
+def _fptr(x, doubles: int):
+    """Device pointer of a float64 or complex128 torch tensor holding at least
+    `doubles` FP64 values."""
+    import torch
+    if not x.is_cuda or not x.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    per = {torch.float64: 1, torch.complex128: 2}.get(x.dtype)
+    if per is None:
+        raise ValueError("expected float64 or complex128")
+    if x.numel() * per < doubles:
+        raise ValueError(f"device tensor holds {x.numel() * per} doubles, the call needs {doubles}")
     return x.data_ptr()
 
 
@@ -467,6 +491,55 @@ def rotate(ct_out, ct_in, count: int, galois_elt: int, galois_key: RelinKey, ctx
                             _ptr(scratch), scratch.numel() * 8, _stream(stream)))
 
 
+class Encoder:
+    """he_encoder: slot FFT and CRT tables of a context (Sec. II-A Encode /
+    Decode on the device). Slots are complex128 tensors [count][N/2] (or
+    float64 [count][N/2][2])."""
+
+    def __init__(self, ctx: Context):
+        h = _vp()
+        _check(load().he_encoder_create(ctx.handle, ctypes.byref(h)))
+        self.handle = h
+        self.ctx = ctx
+
+    def encode_scratch_bytes(self, count: int) -> int:
+        return int(load().he_encode_scratch_bytes(self.handle, count))
+
+    def decode_scratch_bytes(self, level: int, count: int) -> int:
+        return int(load().he_decode_scratch_bytes(self.handle, level, count))
+
+    def encode(self, pt_out, slots, count: int, scale: float, level: int, scratch, stream=None):
+        """pt_out [count][level+1][N] (NTT domain) = residues of the rounded
+        scale-times-slots polynomial."""
+        N = self.ctx.N
+        _check(load().he_encode(self.handle, _ptr(pt_out, count * (level + 1) * N), _fptr(slots, count * N), count,
+                                float(scale), level, _ptr(scratch), scratch.numel() * 8, _stream(stream)))
+
+    def decode(self, slots_out, pt, count: int, scale: float, level: int, scratch, stream=None):
+        """slots_out [count][N/2] = slot values of the NTT-domain plaintexts / scale."""
+        N = self.ctx.N
+        _check(load().he_decode(self.handle, _fptr(slots_out, count * N), _ptr(pt, count * (level + 1) * N), count,
+                                float(scale), level, _ptr(scratch), scratch.numel() * 8, _stream(stream)))
+
+    def crt_compose(self, out, coeffs, count: int, level: int, stream=None):
+        """out [count][N] (float64) = nearest doubles of the centred CRT lifts
+        of coefficient-domain residues coeffs [count][level+1][N]."""
+        N = self.ctx.N
+        _check(load().he_crt_compose(self.handle, _fptr(out, count * N), _ptr(coeffs, count * (level + 1) * N), count,
+                                     level, _stream(stream)))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().he_encoder_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class NttPlan:
     """he_plan over a list of (tensor, tables, N, limbs, first_prime).
     `shapes` maps N to log_block or to (log_block, log_thread_words)."""
@@ -516,6 +589,12 @@ def butterfly_probe(sink, blocks: int, threads: int, iters: int, stream=None):
     """Launch the register-resident butterfly probe (16 * iters butterflies
     per thread)."""
     _check(load().he_butterfly_probe(_ptr(sink), blocks, threads, iters, _stream(stream)))
+
+
+def fp64_probe(sink, blocks: int, threads: int, iters: int, stream=None):
+    """Launch the FP64 probe (16 * iters FLOP per thread); sink is a float64
+    tensor of blocks * threads entries."""
+    _check(load().he_fp64_probe(_fptr(sink, blocks * threads), blocks, threads, iters, _stream(stream)))
 
 
 # Bytes of the scratch buffer built into the library (HE_NOALLOC_SCRATCH_BYTES).

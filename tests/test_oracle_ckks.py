@@ -139,3 +139,16 @@ def test_matmul_tensor_decrypts_to_slot_matrix_product():
             z = ckks.decrypt_decode(T[i, j], keys, scale * scale)
             exact = sum(zA[i, l] * zB[l, j] for l in range(k))
             assert _err(z, exact) < 1e-5
+
+
+@pytest.mark.parametrize("N", [16, 2048])
+def test_encode_unrounded_recovers_integer_polynomial(N):
+    """Slots of an integer polynomial (evaluated directly at the slot roots)
+    encode back to that polynomial's coefficients before any rounding."""
+    r = Rng(N + 1)
+    m = (r.unit_doubles(N) * 2e6 - 1e6).round()
+    k = np.arange(N)
+    z = np.array([np.sum(m * np.exp(1j * np.pi * pow(5, j, 2 * N) * k / N)) for j in range(N // 2)])
+    got = ckks.encode_unrounded(z, N, 1.0)
+    assert np.abs(got - m).max() < 1e-6
+    assert np.array_equal(ckks.encode_real(z, N, 1.0), m.astype(np.int64))
