@@ -68,7 +68,7 @@ def _args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle sample")
-    ap.add_argument("--profile-case", choices=["ntt", "mrr", "probe"],
+    ap.add_argument("--profile-case", choices=["ntt", "mrr", "probe", "encode"],
                     help="run one small case of a kernel family and exit (for profilers)")
     ap.add_argument("--instances", type=int, default=64,
                     help="NTT instances of --profile-case ntt, ciphertext pairs of --profile-case mrr")
@@ -347,7 +347,22 @@ def run_ours(args, rank, world, local):
         back.copy_(d, non_blocking=True)
 
     ms_serial = max_over_ranks(_time_steps(step_serial, 3, 1, stream, barrier))
-    del work
+
+    # the host link alone: the same bytes copied in and out at the same time
+    # (two streams), the floor of any step that moves them
+    s_out = torch.cuda.Stream()
+    d2 = d.clone()   # holds the round-tripped batch, so `back` stays equal to the input
+
+    def step_link():
+        s_out.wait_stream(stream)
+        with torch.cuda.stream(stream):
+            d.copy_(pinned, non_blocking=True)
+        with torch.cuda.stream(s_out):
+            back.copy_(d2, non_blocking=True)
+        stream.wait_stream(s_out)
+
+    ms_link = max_over_ranks(_time_steps(step_link, 3, 1, stream, barrier))
+    del work, d2
     clk = clocks.stop()
     assert torch.equal(back, pinned), "round trip changed the data"
     del pinned, back
@@ -443,7 +458,10 @@ def run_ours(args, rank, world, local):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * limbs_total * N,
                 "d2h_bytes_per_step": 8 * limbs_total * N, "ms_per_step": ms_e2e,
                 "call": "he_ntt_host(forward | inverse), pinned host buffers, 4 streams x 32-polynomial chunks",
-                "whole_batch_copies_value": world * 2 * limbs_total / (ms_serial / 1e3)},
+                "whole_batch_copies_value": world * 2 * limbs_total / (ms_serial / 1e3),
+                "host_link": {"ms_copy_in_and_out": ms_link,
+                              "gbs_per_direction": 8 * limbs_total * N / (ms_link / 1e3) / 1e9,
+                              "e2e_frac_of_link_bound": ms_link / ms_e2e}},
         "gpu_launches": 2 * args.steps,
         "clocks": clk,
     }
@@ -816,7 +834,8 @@ def profile_case(args):
     limbs at N = 2^15 (64 instances = 128 MiB, above the L2 size) forward
     then inverse, `mrr` runs one MulLinRS batch of args.instances pairs on
     the CKKS workload (--shape: log2 words per thread of its kernels),
-    `probe` the butterfly probe. Each runs `--steps` times."""
+    `encode` encodes and decodes args.instances messages at N = 2^15 with 8
+    limbs, `probe` the butterfly probe. Each runs `--steps` times."""
     import numpy as np
     import torch
 
@@ -855,6 +874,19 @@ def profile_case(args):
             ctx.set_eval_shape(int(args.shape))
         for _ in range(args.steps):
             he.mul_relin_rescale(out, ca, cb, count, key, ctx, L, scratch)
+    elif args.profile_case == "encode":
+        N, level = 32768, 7
+        data, P = he.chain_primes(N, [60] + [50] * 7, 60)
+        enc = he.Encoder(he.Context(N, data, P))
+        count = args.instances
+        r = Rng(9)
+        z = torch.from_numpy(np.stack([r.complex_slots(N // 2) for _ in range(count)])).to(dev)
+        zo = torch.empty_like(z)
+        pt = torch.empty((count, level + 1, N), dtype=torch.int64, device=dev)
+        sc = torch.empty(enc.decode_scratch_bytes(level, count) // 8, dtype=torch.int64, device=dev)
+        for _ in range(args.steps):
+            enc.encode(pt, z, count, 2.0 ** 40, level, sc)
+            enc.decode(zo, pt, count, 2.0 ** 40, level, sc)
     else:
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
         sink = torch.empty(sms * 8 * 256, dtype=torch.int64, device=dev)

@@ -1040,7 +1040,8 @@ extern "C" he_status he_encoder_create(const he_context *ctx, he_encoder **out)
         primes[2 * i + 1] = shoup(1, ctx->data[i]);
     }
     // CRT tables per level l (limbs q_0..q_l): Q, (Q - 1) / 2, Q / q_i,
-    // then {q_i, (Q / q_i)^-1 mod q_i, its Shoup quotient, bits of 1 / q_i}
+    // then {q_i, (Q / q_i)^-1 mod q_i, its Shoup quotient}, then
+    // 1 / (Q / 2^(64 (nw - 2))) for the estimate of the multiple of Q
     he_encoder *e = new he_encoder;
     e->ctx = ctx;
     e->log_n = (u32)(ctx->log_n - 1);
@@ -1075,11 +1076,16 @@ extern "C" he_status he_encoder_create(const he_context *ctx, he_encoder **out)
             for (u32 j = 0; j < limbs; j++)
                 if (j != i) r = h_mul(r, ctx->data[j] % q, q);
             const u64 inv = h_inv(r, q);
-            const double rq = 1.0 / (double)q;
-            u64 bits;
-            memcpy(&bits, &rq, 8);
-            crt.insert(crt.end(), {q, inv, shoup(inv, q), bits});
+            crt.insert(crt.end(), {q, inv, shoup(inv, q)});
         }
+        // 1 / (Q / 2^(64 (nw - 2))), the reciprocal of the top two words
+        std::vector<u64> Qp(Q);
+        Qp.resize(nw, 0);
+        const double qtop = std::ldexp((double)Qp[nw - 1], 64) + (double)Qp[nw - 2];
+        const double inv = 1.0 / qtop;
+        u64 bits;
+        memcpy(&bits, &inv, 8);
+        crt.push_back(bits);
     }
     cudaError_t ce = cudaSuccess;
     auto up = [&](auto **dst, const auto &src) {

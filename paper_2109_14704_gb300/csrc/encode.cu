@@ -12,7 +12,8 @@
 // FP64 as a four-step FFT (n = n1 n2): pass A, n2 transforms of length n1
 // over the columns followed by the twiddles omega^(k2 t1); pass B, n1
 // transforms of length n2 over the rows. Each pass is a batch of short
-// radix-2 transforms in shared memory (2^11 complex values per CTA).
+// radix-4 (and one radix-2) transforms in shared memory (2^10 complex values
+// per CTA: more CTAs than SMs several times over, so the last wave is short).
 //
 // Decoding first lifts the RNS residues of every coefficient to the nearest
 // double of the centred integer in (-Q/2, Q/2): a multi-word sum
@@ -22,11 +23,13 @@
 // bits with a sticky bit for the rest).
 #include <math.h>
 
+#include <algorithm>
+
 #include "launch.h"
 
 namespace he {
 
-static const int kLogTile = 11;   // complex values per CTA of an FFT pass
+static const int kLogTile = 10;   // complex values per CTA of an FFT pass
 static const int kFftThreads = 256;
 
 __device__ __forceinline__ double2 c_add(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
@@ -84,17 +87,44 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_pass(FftArgs a)
     }
     __syncthreads();
 
-    // ---- radix-2 decimation in frequency: natural order in, bit-reversed out
-    for (u32 log_h = log_L; log_h-- > 0;) {
-        const u32 h = 1u << log_h;
+    // ---- decimation in frequency: natural order in, bit-reversed out. Groups
+    // of 2^log_g elements; an odd number of stages starts with one radix-2
+    // stage, the rest are radix-4 stages (two radix-2 stages with 3 twiddle
+    // products instead of 4): for a quarter span h and j < h,
+    //   a = x0 + x2, b = x1 + x3, c = x0 - x2, d = (x1 - x3) W_4,
+    //   (x0, x1, x2, x3) <- (a + b, (a - b) W^2j, (c + d) W^j, (c - d) W^3j),
+    // W = W_{4h} = omega^(n / 4h) and W_4 = -i (its conjugates for decoding).
+    u32 log_g = log_L;
+    if (log_L & 1) {
+        const u32 lh = log_L - 1, h = 1u << lh;
         for (u32 b = threadIdx.x; b < tile / 2; b += kFftThreads) {
             const u32 g = b & (G - 1), j = b >> log_G;
-            const u32 r = j & (h - 1), k = ((j >> log_h) << (log_h + 1)) | r;
+            const u32 r = j & (h - 1), k = ((j >> lh) << (lh + 1)) | r;
             double2 *px = sm + k * P + g, *py = px + h * P;
             const double2 x = *px, y = *py;
-            const double2 w = c_conj_if(a.omega[r << (a.log_n - log_h - 1)], conj);   // W_{2h}^r
+            const double2 w = c_conj_if(a.omega[r << (a.log_n - lh - 1)], conj);   // W_{2h}^r
             *px = c_add(x, y);
             *py = c_mul(c_sub(x, y), w);
+        }
+        __syncthreads();
+        log_g = lh;
+    }
+    for (; log_g >= 2; log_g -= 2) {
+        const u32 lq = log_g - 2, h = 1u << lq, hp = h * P, sh = a.log_n - log_g;
+        for (u32 b = threadIdx.x; b < tile / 4; b += kFftThreads) {
+            const u32 g = b & (G - 1), j = b >> log_G;
+            const u32 r = j & (h - 1), k = ((j >> lq) << (lq + 2)) | r;
+            double2 *p0 = sm + k * P + g;
+            const double2 x0 = p0[0], x1 = p0[hp], x2 = p0[2 * hp], x3 = p0[3 * hp];
+            const double2 w1 = c_conj_if(a.omega[r << sh], conj);
+            const double2 w2 = c_conj_if(a.omega[(2 * r) << sh], conj);
+            const double2 w3 = c_conj_if(a.omega[(3 * r) << sh], conj);
+            const double2 s02 = c_add(x0, x2), d02 = c_sub(x0, x2), s13 = c_add(x1, x3), t = c_sub(x1, x3);
+            const double2 d13 = conj ? make_double2(-t.y, t.x) : make_double2(t.y, -t.x);
+            p0[0] = c_add(s02, s13);
+            p0[hp] = c_mul(c_sub(s02, s13), w2);
+            p0[2 * hp] = c_mul(c_add(d02, d13), w1);
+            p0[3 * hp] = c_mul(c_sub(d02, d13), w3);
         }
         __syncthreads();
     }
@@ -238,28 +268,33 @@ __device__ __forceinline__ double mw_to_double(u64 (&v)[NW])
 // out[e] = the nearest double of the centred CRT lift of the residues
 // coef[(c l + i) N + k] (i < limbs), e = c N + k. Table (level of `limbs`
 // primes, NW words per integer): Q, (Q - 1) / 2, Q / q_i for each i, then
-// {q_i, [(Q/q_i)^-1]_{q_i}, its Shoup quotient, bits of 1.0 / q_i}.
+// {q_i, [(Q/q_i)^-1]_{q_i}, its Shoup quotient} per i, then the bits of
+// 1.0 / (Q / 2^(64 (NW - 2))) as a double. NW = ceil((log2 Q + 6) / 64), so
+// that quotient is at least 2^58.
 template <int NW>
 __global__ void __launch_bounds__(128) k_crt_compose(double *out, const u64 *coef, const u64 *tab, u32 log_N,
                                                      u32 limbs, u64 total)
 {
     const u64 *Q = tab, *Qh = tab + NW, *Qhat = tab + 2 * NW, *pr = tab + (2 + limbs) * NW;
+    const double inv_qtop = __longlong_as_double((long long)pr[3 * limbs]);
     const u64 N = 1ull << log_N;
     for (u64 e = (u64)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (u64)gridDim.x * blockDim.x) {
         const u64 c = e >> log_N, k = e & (N - 1);
         u64 acc[NW];
 #pragma unroll
         for (int w = 0; w < NW; w++) acc[w] = 0;
-        double f = 0.0;
         for (u32 i = 0; i < limbs; i++) {
-            const u64 q = pr[4 * i];
-            const u64 y = mul_shoup(coef[(c * limbs + i) * N + k], pr[4 * i + 1], pr[4 * i + 2], q);
-            f = fma((double)y, __longlong_as_double((long long)pr[4 * i + 3]), f);
+            const u64 q = pr[3 * i];
+            const u64 y = mul_shoup(coef[(c * limbs + i) * N + k], pr[3 * i + 1], pr[3 * i + 2], q);
             mw_mac<NW>(acc, y, Qhat + (size_t)i * NW);
         }
-        // sum y_i / q_i = acc / Q: subtract the nearest multiple of Q, then
-        // correct the (rare) off-by-one of the estimate exactly
-        mw_sub_mul<NW>(acc, (u64)rint(f), Q);
+        // acc = x + k Q with 0 <= k < limbs: estimate k from the top two
+        // words of acc against Q / 2^(64 (NW - 2)) >= 2^58 (the dropped words
+        // and the roundings move it by far less than 1/2), subtract the
+        // nearest multiple of Q, and correct the estimate's possible
+        // off-by-one exactly
+        const double top = fma(__ull2double_rn(acc[NW - 1]), 18446744073709551616.0, __ull2double_rn(acc[NW - 2]));
+        mw_sub_mul<NW>(acc, (u64)rint(top * inv_qtop), Q);
         if ((long long)acc[NW - 1] < 0) {
             u64 t[NW];   // t = -acc - 1, and acc < -(Q - 1) / 2 <=> t >= (Q - 1) / 2
 #pragma unroll
@@ -274,7 +309,7 @@ __global__ void __launch_bounds__(128) k_crt_compose(double *out, const u64 *coe
 
 // ------------------------------------------------------------- launchers
 
-// 2^11 complex values plus one padding column: below the 48 KB default
+// 2^10 complex values plus one padding column: below the 48 KB default
 static size_t fft_smem(u32 log_L) { return (size_t)((1u << kLogTile) + (1u << log_L)) * sizeof(double2); }
 
 static u32 fft_blocks(const FftArgs &a, u32 log_L)
@@ -296,15 +331,11 @@ static cudaError_t fft_two_pass(const FftArgs &a, cudaStream_t s)
 cudaError_t launch_encode_fft(const FftArgs &a, cudaStream_t s) { return fft_two_pass<0>(a, s); }
 cudaError_t launch_decode_fft(const FftArgs &a, cudaStream_t s) { return fft_two_pass<1>(a, s); }
 
-#define HE_CRT_NW(X) X(2) X(3) X(4) X(5) X(6) X(8) X(10) X(12) X(14) X(16) X(20) X(24) X(28) X(32)
+#define HE_CRT_NW(X)                                                                                  \
+    X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16) X(17) X(18) X(19) \
+    X(20) X(21) X(22) X(23) X(24) X(25) X(26) X(27) X(28) X(29) X(30) X(31) X(32)
 
-u32 crt_words(u32 need)
-{
-#define HE_CRT_PICK(w) if (need <= (w)) return (w);
-    HE_CRT_NW(HE_CRT_PICK)
-#undef HE_CRT_PICK
-    return 0;
-}
+u32 crt_words(u32 need) { return need <= 32 ? std::max(need, 2u) : 0; }
 
 cudaError_t launch_crt_compose(double *out, const u64 *coef, const u64 *tab, u32 nw, u32 log_N, u32 limbs, u64 total,
                                u32 blocks, cudaStream_t s)
