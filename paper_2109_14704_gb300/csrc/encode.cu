@@ -18,9 +18,9 @@
 // Decoding first lifts the RNS residues of every coefficient to the nearest
 // double of the centred integer in (-Q/2, Q/2): a multi-word sum
 // sum_i [c_i (Q/q_i)^-1]_{q_i} (Q/q_i), minus the multiple of Q that a
-// floating-point estimate of sum_i y_i / q_i gives, with exact multi-word
-// corrections, and a correctly rounded conversion (the mantissa is the top 64
-// bits with a sticky bit for the rest).
+// floating-point estimate from the sum's top two words gives, with an exact
+// multi-word correction, and a correctly rounded conversion (the mantissa is
+// the top 64 bits with a sticky bit for the rest).
 #include <math.h>
 
 #include <algorithm>
