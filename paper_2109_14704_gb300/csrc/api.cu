@@ -532,12 +532,13 @@ extern "C" he_status he_context_create(uint32_t N, uint32_t n_data, const uint64
         delete c;
         return s;
     }
-    std::vector<u64> cst(3 * (size_t)n_data + 3 * (size_t)n_data * n_data, 0);
+    std::vector<u64> cst(3 * (size_t)n_data + 3 * (size_t)n_data * n_data + n_data, 0);
     for (u32 i = 0; i < n_data; i++) {
         const u64 q = all[i];
         cst[3 * i + 0] = h_inv(special_modulus % q, q);
         cst[3 * i + 1] = shoup(cst[3 * i + 0], q);
         cst[3 * i + 2] = special_modulus % q;
+        cst[3 * (size_t)n_data * (1 + n_data) + i] = shoup(special_modulus % q, q);
     }
     for (u32 l = 1; l < n_data; l++)
         for (u32 i = 0; i < l; i++) {

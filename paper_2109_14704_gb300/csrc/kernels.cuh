@@ -586,7 +586,7 @@ k_ks_modup(EvalArgs a)
         }
     }
     if (t < n) {
-        const u64 P_mod_q = a.ctx.cst[3 * t + 2];
+        const u64 P_mod_q = a.ctx.cst[3 * t + 2], P_mod_q_sh = a.ctx.cst[p_shoup_index(a.ctx, t)];
 #pragma unroll
         for (int k = 0; k < 2; k++) {
             u64 *dst = a.accq + (((size_t)c * 2 + k) * n + t) * Sh::N;
@@ -594,7 +594,7 @@ k_ks_modup(EvalArgs a)
             for (int e = 0; e < Sh::E; e++) {
                 const int P = last_pos<Sh>(m, tid, e);
                 const u64 s = reduce_once(reduce_once(acc[(k * Sh::E + e) * Sh::T + tid], pc.two_p), pc.p);
-                dst[P] = add_mod(s, mul_mod(ds.d(k, t, Sh::LOG_N, (u32)P, pc), P_mod_q, pc), pc.p);
+                dst[P] = add_mod(s, mul_shoup(ds.d(k, t, Sh::LOG_N, (u32)P, pc), P_mod_q, P_mod_q_sh, pc.p), pc.p);
             }
         }
     } else {
@@ -670,46 +670,43 @@ constexpr u32 MAC_CTS = 2;
 
 __global__ void __launch_bounds__(256, 4) k_ks_mac(EvalArgs a, u32 groups)
 {
-    const u32 n = a.n, N = a.ctx.N;
-    u32 log_n = 0;
-    while ((1u << log_n) < N) log_n++;
+    const u32 n = a.n, N = a.ctx.N, nd1 = a.ctx.n_data + 1;
+    const u32 log_n = 31 - __clz(N);
     const u32 chunks = (groups + MAC_CTS - 1) / MAC_CTS;
-    const size_t total = (size_t)chunks * (n + 1) * (N / 2);
-    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
-        const u32 P = (u32)(q % (N / 2)) * 2;
-        const u32 t = (u32)((q / (N / 2)) % (n + 1));
-        const u32 g0 = (u32)(q / ((size_t)(N / 2) * (n + 1))) * MAC_CTS;
+    // items (chunk, target, position pair): below 2^32 for every accepted
+    // size (at most 64 ciphertexts per group, 33 targets, 2^15 pairs)
+    const u32 total = chunks * (n + 1) << (log_n - 1);
+    const size_t key_j = (size_t)2 * nd1 * N, key_k = (size_t)nd1 * N;   // evk [j][k][target][N]
+    const size_t mx_g = (size_t)(n + 1) * n * N;                          // mx [g][target][j][N]
+    for (u32 q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
+        const u32 P = (q & ((N >> 1) - 1)) * 2;
+        const u32 r = q >> (log_n - 1);
+        const u32 t = r % (n + 1), g0 = (r / (n + 1)) * MAC_CTS;
         const u32 ng = min(MAC_CTS, groups - g0);
         const u32 tp = (t == n) ? a.ctx.n_data : t;
         const PrimeConst pc = a.ctx.pc[tp];
+        const ulonglong2 *key = a.evk + (size_t)tp * N + P;                  // digit 0, k = 0
+        const u64 *mx = a.mx + ((size_t)g0 * (n + 1) + t) * n * N + P;      // ciphertext g0, digit 0
         u64 acc[MAC_CTS][2][2];
-        for (u32 j = 0; j < n; j++) {
+        for (u32 j = 0; j < n; j++, key += key_j, mx += N) {
             ulonglong2 w[2][2];
 #pragma unroll
             for (int k = 0; k < 2; k++) {
-                const ulonglong2 *key = a.evk + (((size_t)j * 2 + k) * (a.ctx.n_data + 1) + tp) * N + P;
-                w[k][0] = __ldg(key);
-                w[k][1] = __ldg(key + 1);
+                w[k][0] = __ldg(key + k * key_k);
+                w[k][1] = __ldg(key + k * key_k + 1);
             }
 #pragma unroll
             for (u32 gi = 0; gi < MAC_CTS; gi++) {
                 if (gi >= ng) break;
-                const u32 g = g0 + gi;
-                u64 x0, x1;
-                if (j == t) {
-                    const ulonglong2 v = dsource(a, a.c_first + g).d2(2, j, log_n, P, pc);
-                    x0 = v.x;
-                    x1 = v.y;
-                } else {
-                    const ulonglong2 v =
-                        __ldg(reinterpret_cast<const ulonglong2 *>(a.mx + (((size_t)g * (n + 1) + t) * n + j) * N + P));
-                    x0 = v.x;
-                    x1 = v.y;
-                }
+                ulonglong2 v;
+                if (j == t)
+                    v = dsource(a, a.c_first + g0 + gi).d2(2, j, log_n, P, pc);
+                else
+                    v = __ldg(reinterpret_cast<const ulonglong2 *>(mx + gi * mx_g));
 #pragma unroll
                 for (int k = 0; k < 2; k++) {
-                    const u64 p0 = mul_shoup_lazy4_asm(x0, w[k][0].x, w[k][0].y, pc.neg_p);
-                    const u64 p1 = mul_shoup_lazy4_asm(x1, w[k][1].x, w[k][1].y, pc.neg_p);
+                    const u64 p0 = mul_shoup_lazy4_asm(v.x, w[k][0].x, w[k][0].y, pc.neg_p);
+                    const u64 p1 = mul_shoup_lazy4_asm(v.y, w[k][1].x, w[k][1].y, pc.neg_p);
                     acc[gi][k][0] = j == 0 ? p0 : reduce_once(acc[gi][k][0] + p0, pc.four_p);
                     acc[gi][k][1] = j == 0 ? p1 : reduce_once(acc[gi][k][1] + p1, pc.four_p);
                 }
@@ -725,12 +722,12 @@ __global__ void __launch_bounds__(256, 4) k_ks_mac(EvalArgs a, u32 groups)
                 ulonglong2 o;
                 if (t < n) {
                     // stored as d_k P + acc_k (see the mod-down)
-                    const u64 P_mod_q = a.ctx.cst[3 * t + 2];
+                    const u64 P_mod_q = a.ctx.cst[3 * t + 2], P_mod_q_sh = a.ctx.cst[p_shoup_index(a.ctx, t)];
                     const u64 s0 = reduce_once(reduce_once(acc[gi][k][0], pc.two_p), pc.p);
                     const u64 s1 = reduce_once(reduce_once(acc[gi][k][1], pc.two_p), pc.p);
                     const ulonglong2 dv = ds.d2(k, t, log_n, P, pc);
-                    o.x = add_mod(s0, mul_mod(dv.x, P_mod_q, pc), pc.p);
-                    o.y = add_mod(s1, mul_mod(dv.y, P_mod_q, pc), pc.p);
+                    o.x = add_mod(s0, mul_shoup(dv.x, P_mod_q, P_mod_q_sh, pc.p), pc.p);
+                    o.y = add_mod(s1, mul_shoup(dv.y, P_mod_q, P_mod_q_sh, pc.p), pc.p);
                     *reinterpret_cast<ulonglong2 *>(a.accq + (((size_t)c * 2 + k) * n + t) * N + P) = o;
                 } else {
                     o.x = acc[gi][k][0];

@@ -53,11 +53,14 @@ struct DevCtx {
     const PrimeConst *pc;       // [n_data + 1]
     // cst[3 i + {0,1,2}] = P^-1 mod q_i, its Shoup quotient, P mod q_i;
     // cst[3 n_data + 3 (l n_data + i) + {0,1,2}] = q_l^-1 mod q_i, Shoup,
-    // q_l mod q_i (rescale from level l, i < l).
+    // q_l mod q_i (rescale from level l, i < l);
+    // cst[3 n_data + 3 n_data^2 + i] = Shoup quotient of P mod q_i.
     const u64 *cst;
     u32 N;
     u32 n_data;
 };
+
+__host__ __device__ inline u32 p_shoup_index(const DevCtx &c, u32 i) { return 3 * c.n_data * (1 + c.n_data) + i; }
 
 struct EvalArgs {
     const u64 *ct_a, *ct_b;     // [count][2][n][N] (fused Mul) or null
