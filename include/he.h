@@ -300,6 +300,40 @@ he_status he_mul_relin_rescale_noalloc(uint64_t *ct_out, const uint64_t *ct_a, c
                                        uint32_t count, const he_relin_key *key, const he_context *ctx,
                                        uint32_t level, he_stream_t stream);
 
+/* ---- mixed-level batches (Sec. III-B batching over instances) ---------------- */
+
+/* One job of a mixed-level MulLinRS batch: `count` ciphertext pairs at
+ * `level` (ct_a, ct_b: count x 2 x (level + 1) x N words, NTT domain; ct_out:
+ * count x 2 x level x N words), all under one context and key. */
+typedef struct he_mrr_job {
+    uint64_t *ct_out;
+    const uint64_t *ct_a;
+    const uint64_t *ct_b;
+    uint32_t count;
+    uint32_t level;
+} he_mrr_job;
+
+/* Device scratch of he_mul_relin_rescale_batch for these jobs (host array):
+ * per job count * (level + 3)^2 * N * 8 bytes (the expanded
+ * mod-up buffer of all its pairs included). 0 for invalid jobs. */
+size_t he_mul_relin_rescale_batch_scratch_bytes(const he_context *ctx, const he_mrr_job *jobs_host,
+                                                uint32_t n_jobs);
+
+/* MulLinRS of every job, each with exactly the result he_mul_relin_rescale
+ * gives for it alone, with ONE launch per pipeline stage for all jobs
+ * together (digit INTT, mod-up transforms, key multiply-accumulate, the
+ * special prime's INTT, and the three mod-down / rescale kernels): the
+ * kernels read a table of the jobs (at most 16 per pass; more jobs take
+ * further passes) and map each CTA or thread to its job. Jobs may have
+ * different levels and counts; jobs with count 0 are skipped. Outputs must
+ * not overlap inputs or each other. scratch: device, 16-byte aligned,
+ * he_mul_relin_rescale_batch_scratch_bytes. HE_EINVAL for a bad level (< 1
+ * or beyond the chain), pointer, key, short scratch, or a batch whose item
+ * count exceeds the launch limits. */
+he_status he_mul_relin_rescale_batch(const he_mrr_job *jobs_host, uint32_t n_jobs, const he_relin_key *key,
+                                     const he_context *ctx, void *scratch, size_t scratch_bytes,
+                                     he_stream_t stream);
+
 /* ---- encoding and decoding (Sec. II-A Encode / Decode) ------------------------ */
 
 /* Slot vectors are n = N/2 complex numbers, stored as interleaved FP64

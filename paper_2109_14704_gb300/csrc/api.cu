@@ -698,11 +698,26 @@ extern "C" size_t he_mul_relin_rescale_scratch_bytes(const he_context *ctx, uint
 }
 
 static he_status run_eval(const he_context *ctx, he::EvalKernel k, const he::EvalArgs &a, u32 items,
-                          cudaStream_t s)
+                          cudaStream_t s, const he::JobTable *jobs = nullptr)
 {
     if (!items) return HE_OK;
-    HE_CUDA(he::degree_ops(ctx->log_n)->eval(k, a, items, ctx->eval_log_e.load(), s));
+    HE_CUDA(he::degree_ops(ctx->log_n)->eval(k, a, items, ctx->eval_log_e.load(), jobs, s));
     return HE_OK;
+}
+
+// The special prime's accumulators of `limbs` back-to-back N-word rows at
+// `plift` go through the inverse transform in place.
+static he_status plift_intt(const he_context *ctx, u64 *plift, u32 limbs, cudaStream_t s)
+{
+    he::NttLaunch L = {};
+    L.base = plift;
+    L.limbs = 1;
+    L.first_prime = ctx->n_data;
+    L.items = limbs;
+    L.tw_fwd = ctx->tables->d_fwd;
+    L.tw_inv = ctx->tables->d_inv;
+    L.pc = ctx->tables->d_pc;
+    return ntt_launch(L, ctx->log_n, true, s);
 }
 
 // Mod-up of key switching for `count` ciphertexts (a.c2 holds their
@@ -725,21 +740,13 @@ static he_status ks_modup(const he_context *ctx, he::EvalArgs &a, u32 count, u64
         const u32 gs = std::min(group, count - c0);
         a.c_first = c0;
         if (he_status r = run_eval(ctx, he::EK_KS_EXPAND, a, gs * (n + 1) * n, s)) return r;
-        const u64 chunks = (gs + he::MAC_CTS - 1) / he::MAC_CTS;
-        he::k_ks_mac<<<stream_grid(chunks * (n + 1) * (ctx->N / 2), 256), 256, 0, s>>>(a, gs);
+        const u32 total = (u32)((gs + he::MAC_CTS - 1) / he::MAC_CTS * (n + 1) * (ctx->N / 2));
+        he::k_ks_mac<false><<<stream_grid(total, 256), 256, 0, s>>>(a, gs, total, he::NoJobs{});
         HE_CUDA(cudaGetLastError());
     }
     a.mx = nullptr;
     a.c_first = 0;
-    he::NttLaunch L = {};
-    L.base = a.plift;
-    L.limbs = 1;
-    L.first_prime = ctx->n_data;
-    L.items = 2 * count;
-    L.tw_fwd = ctx->tables->d_fwd;
-    L.tw_inv = ctx->tables->d_inv;
-    L.pc = ctx->tables->d_pc;
-    return ntt_launch(L, ctx->log_n, true, s);
+    return plift_intt(ctx, a.plift, 2 * count, s);
 }
 
 extern "C" he_status he_relin(uint64_t *ct_out2, const uint64_t *ct_in3, const he_relin_key *key,
@@ -861,6 +868,116 @@ extern "C" he_status he_relin_rescale(uint64_t *ct_out, const uint64_t *ct3, uin
     if (!ct3) return fail(HE_EINVAL, "ct3 is NULL");
     return key_switch_common(ct_out, nullptr, nullptr, ct3, count, key, ctx, level, scratch, scratch_bytes, stream,
                              true);
+}
+
+// ---- mixed-level MulLinRS batches (one launch per pipeline stage) -----------
+
+// Scratch words of one job of a mixed batch: c2, accq, lift2, the expanded
+// mod-up buffer of all its ciphertexts, and its share of the common plift.
+static size_t mrr_job_words(const he_context *c, u32 n, u32 count)
+{
+    return ((size_t)n + 2 * n + 2 + (size_t)(n + 1) * n + 2) * c->N * count;
+}
+
+// Levels and counts of every job; with `pointers`, also each live job's buffers.
+static he_status check_mrr_jobs(const he_context *ctx, const he_mrr_job *jobs, uint32_t n_jobs, bool pointers)
+{
+    if (!ctx) return fail(HE_EINVAL, "context is NULL");
+    if (n_jobs && !jobs) return fail(HE_EINVAL, "jobs_host is NULL");
+    for (u32 i = 0; i < n_jobs; i++) {
+        const he_mrr_job &J = jobs[i];
+        if (he_status s = check_level(ctx, J.level, true)) return s;
+        if (J.count > 4096) return fail(HE_EINVAL, "job %u: more than 4096 ciphertext pairs", i);
+        if (!J.count || !pointers) continue;
+        if (he_status s = check_ptr(J.ct_out, "ct_out")) return s;
+        if (he_status s = check_ptr(J.ct_a, "ct_a")) return s;
+        if (he_status s = check_ptr(J.ct_b, "ct_b")) return s;
+    }
+    return HE_OK;
+}
+
+extern "C" size_t he_mul_relin_rescale_batch_scratch_bytes(const he_context *ctx, const he_mrr_job *jobs_host,
+                                                           uint32_t n_jobs)
+{
+    if (check_mrr_jobs(ctx, jobs_host, n_jobs, false) != HE_OK) return 0;
+    size_t words = 0;
+    for (u32 i = 0; i < n_jobs; i++) words += mrr_job_words(ctx, jobs_host[i].level + 1, jobs_host[i].count);
+    return words * 8;
+}
+
+// One pass of the pipeline over up to kMaxJobs jobs whose scratch starts at w.
+static he_status mrr_jobs_pass(const he_mrr_job *jobs, u32 n_jobs, const he_relin_key *key, const he_context *ctx,
+                               u64 *w, cudaStream_t s)
+{
+    he::JobTable t = {};
+    u64 tot[he::JS_COUNT] = {};
+    u32 pairs = 0;
+    for (u32 i = 0; i < n_jobs; i++) pairs += jobs[i].count;
+    u64 *plift = w;                       // [all pairs][2][N], contiguous for one transform launch
+    w += (size_t)pairs * 2 * ctx->N;
+    u64 *pl = plift;
+    for (u32 i = 0; i < n_jobs; i++) {
+        const he_mrr_job &J = jobs[i];
+        const u32 n = J.level + 1, c = J.count;
+        he::EvalJob &E = t.job[t.n_jobs++];
+        E.ct_a = J.ct_a;
+        E.ct_b = J.ct_b;
+        E.out = J.ct_out;
+        E.n = n;
+        E.count = c;
+        E.c2 = w;
+        E.accq = E.c2 + (size_t)c * n * ctx->N;
+        E.lift2 = E.accq + (size_t)c * 2 * n * ctx->N;
+        E.mx = E.lift2 + (size_t)c * 2 * ctx->N;
+        w = E.mx + (size_t)c * (n + 1) * n * ctx->N;
+        E.plift = pl;
+        pl += (size_t)c * 2 * ctx->N;
+        const u64 items[he::JS_COUNT] = {(u64)c * n, (u64)c * (n + 1) * n,
+                                         (u64)(c + he::MAC_CTS - 1) / he::MAC_CTS * (n + 1) * (ctx->N / 2), 2ull * c,
+                                         2ull * c * (n - 1)};
+        for (int st = 0; st < he::JS_COUNT; st++) {
+            if (tot[st] + items[st] > 0x7fffffffull) return fail(HE_EINVAL, "batch too large");
+            E.begin[st] = (u32)tot[st];
+            tot[st] += items[st];
+        }
+    }
+    u64 grid_items = 0;
+    for (int st = 0; st < he::JS_COUNT; st++) grid_items = std::max<u64>(grid_items, tot[st]);
+    if (grid_items * 8 > 0x7fffffffull) return fail(HE_EINVAL, "batch too large");
+    he::EvalArgs a = {};
+    a.evk = key->d_evk;
+    a.ctx = dev_ctx(ctx);
+    a.n = t.job[0].n;   // unused with a job table; kept valid
+    if (he_status r = run_eval(ctx, he::EK_KS_DIGITS, a, (u32)tot[he::JS_DIGITS], s, &t)) return r;
+    if (he_status r = run_eval(ctx, he::EK_KS_EXPAND, a, (u32)tot[he::JS_EXPAND], s, &t)) return r;
+    he::k_ks_mac<true><<<stream_grid(tot[he::JS_MAC], 256), 256, 0, s>>>(a, 0, (u32)tot[he::JS_MAC], t);
+    HE_CUDA(cudaGetLastError());
+    if (he_status r = plift_intt(ctx, plift, 2 * pairs, s)) return r;
+    if (he_status r = run_eval(ctx, he::EK_MRR_LAST, a, (u32)tot[he::JS_LAST], s, &t)) return r;
+    if (he_status r = run_eval(ctx, he::EK_MRR_REST_Z, a, (u32)tot[he::JS_REST], s, &t)) return r;
+    return run_eval(ctx, he::EK_MRR_REST_OUT, a, (u32)tot[he::JS_REST], s, &t);
+}
+
+extern "C" he_status he_mul_relin_rescale_batch(const he_mrr_job *jobs_host, uint32_t n_jobs,
+                                                const he_relin_key *key, const he_context *ctx, void *scratch,
+                                                size_t scratch_bytes, he_stream_t stream)
+{
+    if (he_status s = check_mrr_jobs(ctx, jobs_host, n_jobs, true)) return s;
+    if (!key || key->ctx != ctx) return fail(HE_EINVAL, "relin key is NULL or belongs to another context");
+    std::vector<he_mrr_job> live;
+    for (u32 i = 0; i < n_jobs; i++)
+        if (jobs_host[i].count) live.push_back(jobs_host[i]);
+    if (live.empty()) return HE_OK;
+    if (he_status s = check_ptr(scratch, "scratch")) return s;
+    if (scratch_bytes < he_mul_relin_rescale_batch_scratch_bytes(ctx, live.data(), (u32)live.size()))
+        return fail(HE_EINVAL, "scratch too small");
+    u64 *w = (u64 *)scratch;
+    for (size_t i = 0; i < live.size(); i += he::kMaxJobs) {
+        const u32 m = (u32)std::min<size_t>(he::kMaxJobs, live.size() - i);
+        if (he_status r = mrr_jobs_pass(live.data() + i, m, key, ctx, w, (cudaStream_t)stream)) return r;
+        for (u32 k = 0; k < m; k++) w += mrr_job_words(ctx, live[i + k].level + 1, live[i + k].count);
+    }
+    return HE_OK;
 }
 
 extern "C" size_t he_mul_relin_scratch_bytes(const he_context *ctx, uint32_t level, uint32_t count)

@@ -89,7 +89,7 @@ struct ShapeOps {
         return n;
     }
 
-    static cudaError_t eval(EvalKernel k, const EvalArgs &a, u32 items, cudaStream_t s)
+    static cudaError_t eval(EvalKernel k, const EvalArgs &a, u32 items, const JobTable *jobs, cudaStream_t s)
     {
         const u32 grid = items * Sh::C;
         const u32 sm1 = Sh::SMEM_BYTES;
@@ -97,20 +97,35 @@ struct ShapeOps {
         switch (k) {
 #define HE_EVAL_CASE(ID, KERNEL, SMEM)                                                   \
     case ID: {                                                                           \
+        if (jobs) return cudaErrorInvalidValue;                                          \
         static std::once_flag f;                                                         \
         static cudaError_t e = cudaSuccess;                                              \
         if (cudaError_t r = smem_attr(KERNEL<LOG_B, LOG_C, LOG_E>, SMEM, f, e)) return r; \
         return launch_k(KERNEL<LOG_B, LOG_C, LOG_E>, grid, Sh::T, SMEM, Sh::C, s, a);     \
     }
-            HE_EVAL_CASE(EK_KS_DIGITS, k_ks_digits, sm1)
+#define HE_EVAL_CASE_J(ID, KERNEL, SMEM)                                                                    \
+    case ID: {                                                                                              \
+        if (jobs) {                                                                                         \
+            static std::once_flag f;                                                                        \
+            static cudaError_t e = cudaSuccess;                                                             \
+            if (cudaError_t r = smem_attr(KERNEL<LOG_B, LOG_C, LOG_E, true>, SMEM, f, e)) return r;         \
+            return launch_k(KERNEL<LOG_B, LOG_C, LOG_E, true>, grid, Sh::T, SMEM, Sh::C, s, a, *jobs);      \
+        }                                                                                                   \
+        static std::once_flag f;                                                                            \
+        static cudaError_t e = cudaSuccess;                                                                 \
+        if (cudaError_t r = smem_attr(KERNEL<LOG_B, LOG_C, LOG_E, false>, SMEM, f, e)) return r;            \
+        return launch_k(KERNEL<LOG_B, LOG_C, LOG_E, false>, grid, Sh::T, SMEM, Sh::C, s, a, NoJobs{});      \
+    }
+            HE_EVAL_CASE_J(EK_KS_DIGITS, k_ks_digits, sm1)
             HE_EVAL_CASE(EK_KS_MODUP, k_ks_modup, sm3)
-            HE_EVAL_CASE(EK_KS_EXPAND, k_ks_expand, sm1)
+            HE_EVAL_CASE_J(EK_KS_EXPAND, k_ks_expand, sm1)
             HE_EVAL_CASE(EK_KS_MODDOWN, k_ks_moddown, sm1)
             HE_EVAL_CASE(EK_RS_LIFT, k_rs_lift, sm1)
             HE_EVAL_CASE(EK_RS, k_rs, sm1)
-            HE_EVAL_CASE(EK_MRR_LAST, k_mrr_last, sm1)
-            HE_EVAL_CASE(EK_MRR_REST_Z, k_mrr_rest_z, sm1)
-            HE_EVAL_CASE(EK_MRR_REST_OUT, k_mrr_rest_out, sm1)
+            HE_EVAL_CASE_J(EK_MRR_LAST, k_mrr_last, sm1)
+            HE_EVAL_CASE_J(EK_MRR_REST_Z, k_mrr_rest_z, sm1)
+            HE_EVAL_CASE_J(EK_MRR_REST_OUT, k_mrr_rest_out, sm1)
+#undef HE_EVAL_CASE_J
 #undef HE_EVAL_CASE
         default:
             return cudaErrorInvalidValue;
@@ -183,11 +198,11 @@ struct DegreeImpl;
         });                                                                                        \
     }                                                                                              \
     static cudaError_t eval_##LOG_N_(EvalKernel k, const EvalArgs &a, u32 items, int log_e,        \
-                                     cudaStream_t s)                                               \
+                                     const JobTable *jobs, cudaStream_t s)                         \
     {                                                                                              \
         using D = DegreeImpl<LOG_N_>;                                                              \
-        if (log_e == 3) return ShapeOps<D::def_b, LOG_N_ - D::def_b, 3>::eval(k, a, items, s);     \
-        return ShapeOps<D::def_b, LOG_N_ - D::def_b, 4>::eval(k, a, items, s);                     \
+        if (log_e == 3) return ShapeOps<D::def_b, LOG_N_ - D::def_b, 3>::eval(k, a, items, jobs, s); \
+        return ShapeOps<D::def_b, LOG_N_ - D::def_b, 4>::eval(k, a, items, jobs, s);               \
     }                                                                                              \
     static bool has_##LOG_N_(int log_b, int log_e)                                                 \
     {                                                                                              \

@@ -464,6 +464,33 @@ __device__ __forceinline__ u64 rd(const u64 *p) { return __ldg(reinterpret_cast<
 
 // d_k[i] at position P for component k (0 or 1): from the tensor of the two
 // input ciphertexts (fused Mul) or from a 3-component input.
+// Job of a mixed-level batch that owns global item `item` of stage S (the
+// last job whose first item is not above it): its buffers and sizes go into
+// a, and the item's index within the job is returned.
+__device__ __forceinline__ u32 bind_job(EvalArgs &a, const JobTable &t, int S, u32 item)
+{
+    u32 lo = 0, hi = t.n_jobs - 1;
+    while (lo < hi) {
+        const u32 mid = (lo + hi + 1) / 2;
+        if (t.job[mid].begin[S] <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    const EvalJob &J = t.job[lo];
+    a.ct_a = J.ct_a;
+    a.ct_b = J.ct_b;
+    a.ct3 = nullptr;
+    a.out = J.out;
+    a.c2 = J.c2;
+    a.accq = J.accq;
+    a.plift = J.plift;
+    a.lift2 = J.lift2;
+    a.mx = J.mx;
+    a.n = J.n;
+    a.count = J.count;
+    a.c_first = 0;
+    return item - J.begin[S];
+}
+
 struct DSource {
     const u64 *ct_a, *ct_b, *ct3;  // per-ciphertext bases
     size_t per;                    // n * N words per component
@@ -507,14 +534,16 @@ __device__ __forceinline__ DSource dsource(const EvalArgs &a, u32 c)
     return s;
 }
 
-template <int LOG_B, int LOG_C, int LOG_E>
+template <int LOG_B, int LOG_C, int LOG_E, bool JOBS = false>
 __global__ void __launch_bounds__(NttShape<LOG_B, LOG_C, LOG_E>::T, NttShape<LOG_B, LOG_C, LOG_E>::MIN_CTAS)
-k_ks_digits(EvalArgs a)
+k_ks_digits(EvalArgs a0, JobsArg<JOBS> tab)
 {
+    EvalArgs a = a0;
     using Sh = NttShape<LOG_B, LOG_C, LOG_E>;
     extern __shared__ __align__(16) u64 smem[];
     const u32 m = (LOG_C > 0) ? cluster_ctarank() : 0u;
-    const u32 item = blockIdx.x >> LOG_C;
+    u32 item = blockIdx.x >> LOG_C;
+    if constexpr (JOBS) item = bind_job(a, tab, JS_DIGITS, item);
     const u32 c = item / a.n, j = item % a.n;
     const PrimeConst pc = a.ctx.pc[j];
     const DSource ds = dsource(a, c);
@@ -622,15 +651,17 @@ k_ks_modup(EvalArgs a)
 // accumulating cluster; k_ks_mac then accumulates them with the key.
 // Clusters of the diagonal (j = t) exit at once: there the digit is already
 // in the NTT domain.
-template <int LOG_B, int LOG_C, int LOG_E>
+template <int LOG_B, int LOG_C, int LOG_E, bool JOBS = false>
 __global__ void __launch_bounds__(NttShape<LOG_B, LOG_C, LOG_E>::T, NttShape<LOG_B, LOG_C, LOG_E>::MIN_CTAS)
-k_ks_expand(EvalArgs a)
+k_ks_expand(EvalArgs a0, JobsArg<JOBS> tab)
 {
+    EvalArgs a = a0;
     using Sh = NttShape<LOG_B, LOG_C, LOG_E>;
     extern __shared__ __align__(16) u64 smem[];
     const u32 tid = threadIdx.x;
     const u32 m = (LOG_C > 0) ? cluster_ctarank() : 0u;
-    const u32 item = blockIdx.x >> LOG_C;
+    u32 item = blockIdx.x >> LOG_C;
+    if constexpr (JOBS) item = bind_job(a, tab, JS_EXPAND, item);
     const u32 n = a.n;
     const u32 j = item % n, t = (item / n) % (n + 1), g = item / (n * (n + 1));
     if (j == t) return;
@@ -668,73 +699,87 @@ k_ks_expand(EvalArgs a)
 // (one: fewer key reuses; four: too few warps to cover the loads).
 constexpr u32 MAC_CTS = 2;
 
-__global__ void __launch_bounds__(256, 4) k_ks_mac(EvalArgs a, u32 groups)
+// One item of k_ks_mac: two positions of one target for up to MAC_CTS
+// ciphertexts of the group (item q of the group's chunks x targets x pairs).
+__device__ __forceinline__ void ks_mac_item(const EvalArgs &a, u32 groups, u32 q)
 {
     const u32 n = a.n, N = a.ctx.N, nd1 = a.ctx.n_data + 1;
     const u32 log_n = 31 - __clz(N);
-    const u32 chunks = (groups + MAC_CTS - 1) / MAC_CTS;
-    // items (chunk, target, position pair): below 2^32 for every accepted
-    // size (at most 64 ciphertexts per group, 33 targets, 2^15 pairs)
-    const u32 total = chunks * (n + 1) << (log_n - 1);
     const size_t key_j = (size_t)2 * nd1 * N, key_k = (size_t)nd1 * N;   // evk [j][k][target][N]
     const size_t mx_g = (size_t)(n + 1) * n * N;                          // mx [g][target][j][N]
-    for (u32 q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
-        const u32 P = (q & ((N >> 1) - 1)) * 2;
-        const u32 r = q >> (log_n - 1);
-        const u32 t = r % (n + 1), g0 = (r / (n + 1)) * MAC_CTS;
-        const u32 ng = min(MAC_CTS, groups - g0);
-        const u32 tp = (t == n) ? a.ctx.n_data : t;
-        const PrimeConst pc = a.ctx.pc[tp];
-        const ulonglong2 *key = a.evk + (size_t)tp * N + P;                  // digit 0, k = 0
-        const u64 *mx = a.mx + ((size_t)g0 * (n + 1) + t) * n * N + P;      // ciphertext g0, digit 0
-        u64 acc[MAC_CTS][2][2];
-        for (u32 j = 0; j < n; j++, key += key_j, mx += N) {
-            ulonglong2 w[2][2];
+    const u32 P = (q & ((N >> 1) - 1)) * 2;
+    const u32 r = q >> (log_n - 1);
+    const u32 t = r % (n + 1), g0 = (r / (n + 1)) * MAC_CTS;
+    const u32 ng = min(MAC_CTS, groups - g0);
+    const u32 tp = (t == n) ? a.ctx.n_data : t;
+    const PrimeConst pc = a.ctx.pc[tp];
+    const ulonglong2 *key = a.evk + (size_t)tp * N + P;                  // digit 0, k = 0
+    const u64 *mx = a.mx + ((size_t)g0 * (n + 1) + t) * n * N + P;      // ciphertext g0, digit 0
+    u64 acc[MAC_CTS][2][2];
+    for (u32 j = 0; j < n; j++, key += key_j, mx += N) {
+        ulonglong2 w[2][2];
 #pragma unroll
-            for (int k = 0; k < 2; k++) {
-                w[k][0] = __ldg(key + k * key_k);
-                w[k][1] = __ldg(key + k * key_k + 1);
-            }
-#pragma unroll
-            for (u32 gi = 0; gi < MAC_CTS; gi++) {
-                if (gi >= ng) break;
-                ulonglong2 v;
-                if (j == t)
-                    v = dsource(a, a.c_first + g0 + gi).d2(2, j, log_n, P, pc);
-                else
-                    v = __ldg(reinterpret_cast<const ulonglong2 *>(mx + gi * mx_g));
-#pragma unroll
-                for (int k = 0; k < 2; k++) {
-                    const u64 p0 = mul_shoup_lazy4_asm(v.x, w[k][0].x, w[k][0].y, pc.neg_p);
-                    const u64 p1 = mul_shoup_lazy4_asm(v.y, w[k][1].x, w[k][1].y, pc.neg_p);
-                    acc[gi][k][0] = j == 0 ? p0 : reduce_once(acc[gi][k][0] + p0, pc.four_p);
-                    acc[gi][k][1] = j == 0 ? p1 : reduce_once(acc[gi][k][1] + p1, pc.four_p);
-                }
-            }
+        for (int k = 0; k < 2; k++) {
+            w[k][0] = __ldg(key + k * key_k);
+            w[k][1] = __ldg(key + k * key_k + 1);
         }
 #pragma unroll
         for (u32 gi = 0; gi < MAC_CTS; gi++) {
             if (gi >= ng) break;
-            const u32 c = a.c_first + g0 + gi;
-            const DSource ds = dsource(a, c);
+            ulonglong2 v;
+            if (j == t)
+                v = dsource(a, a.c_first + g0 + gi).d2(2, j, log_n, P, pc);
+            else
+                v = __ldg(reinterpret_cast<const ulonglong2 *>(mx + gi * mx_g));
 #pragma unroll
             for (int k = 0; k < 2; k++) {
-                ulonglong2 o;
-                if (t < n) {
-                    // stored as d_k P + acc_k (see the mod-down)
-                    const u64 P_mod_q = a.ctx.cst[3 * t + 2], P_mod_q_sh = a.ctx.cst[p_shoup_index(a.ctx, t)];
-                    const u64 s0 = reduce_once(reduce_once(acc[gi][k][0], pc.two_p), pc.p);
-                    const u64 s1 = reduce_once(reduce_once(acc[gi][k][1], pc.two_p), pc.p);
-                    const ulonglong2 dv = ds.d2(k, t, log_n, P, pc);
-                    o.x = add_mod(s0, mul_shoup(dv.x, P_mod_q, P_mod_q_sh, pc.p), pc.p);
-                    o.y = add_mod(s1, mul_shoup(dv.y, P_mod_q, P_mod_q_sh, pc.p), pc.p);
-                    *reinterpret_cast<ulonglong2 *>(a.accq + (((size_t)c * 2 + k) * n + t) * N + P) = o;
-                } else {
-                    o.x = acc[gi][k][0];
-                    o.y = acc[gi][k][1];
-                    *reinterpret_cast<ulonglong2 *>(a.plift + ((size_t)c * 2 + k) * N + P) = o;
-                }
+                const u64 p0 = mul_shoup_lazy4_asm(v.x, w[k][0].x, w[k][0].y, pc.neg_p);
+                const u64 p1 = mul_shoup_lazy4_asm(v.y, w[k][1].x, w[k][1].y, pc.neg_p);
+                acc[gi][k][0] = j == 0 ? p0 : reduce_once(acc[gi][k][0] + p0, pc.four_p);
+                acc[gi][k][1] = j == 0 ? p1 : reduce_once(acc[gi][k][1] + p1, pc.four_p);
             }
+        }
+    }
+#pragma unroll
+    for (u32 gi = 0; gi < MAC_CTS; gi++) {
+        if (gi >= ng) break;
+        const u32 c = a.c_first + g0 + gi;
+        const DSource ds = dsource(a, c);
+#pragma unroll
+        for (int k = 0; k < 2; k++) {
+            ulonglong2 o;
+            if (t < n) {
+                // stored as d_k P + acc_k (see the mod-down)
+                const u64 P_mod_q = a.ctx.cst[3 * t + 2], P_mod_q_sh = a.ctx.cst[p_shoup_index(a.ctx, t)];
+                const u64 s0 = reduce_once(reduce_once(acc[gi][k][0], pc.two_p), pc.p);
+                const u64 s1 = reduce_once(reduce_once(acc[gi][k][1], pc.two_p), pc.p);
+                const ulonglong2 dv = ds.d2(k, t, log_n, P, pc);
+                o.x = add_mod(s0, mul_shoup(dv.x, P_mod_q, P_mod_q_sh, pc.p), pc.p);
+                o.y = add_mod(s1, mul_shoup(dv.y, P_mod_q, P_mod_q_sh, pc.p), pc.p);
+                *reinterpret_cast<ulonglong2 *>(a.accq + (((size_t)c * 2 + k) * n + t) * N + P) = o;
+            } else {
+                o.x = acc[gi][k][0];
+                o.y = acc[gi][k][1];
+                *reinterpret_cast<ulonglong2 *>(a.plift + ((size_t)c * 2 + k) * N + P) = o;
+            }
+        }
+    }
+}
+
+// Items: for a uniform group, (groups / MAC_CTS rounded up) x (n + 1)
+// targets x N / 2 position pairs; for a job table, those of every job back
+// to back (each job one group of all its ciphertexts). `total` is below 2^32
+// for every accepted size (64 ciphertexts per group, 33 targets, 2^15 pairs).
+template <bool JOBS = false>
+__global__ void __launch_bounds__(256, 4) k_ks_mac(EvalArgs a0, u32 groups, u32 total, JobsArg<JOBS> tab)
+{
+    for (u32 q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
+        if constexpr (JOBS) {
+            EvalArgs a = a0;
+            const u32 local = bind_job(a, tab, JS_MAC, q);
+            ks_mac_item(a, a.count, local);
+        } else {
+            ks_mac_item(a0, groups, q);
         }
     }
 }
@@ -815,15 +860,17 @@ k_rs(EvalArgs a)
 
 // MulLinRS, limb q_l: relin output c_k[q_l] = d_k[l] + (acc - NTT(r)) P^-1,
 // then straight into INTT_{q_l} (values stay in registers) -> lift2.
-template <int LOG_B, int LOG_C, int LOG_E>
+template <int LOG_B, int LOG_C, int LOG_E, bool JOBS = false>
 __global__ void __launch_bounds__(NttShape<LOG_B, LOG_C, LOG_E>::T, NttShape<LOG_B, LOG_C, LOG_E>::EVAL_MIN_CTAS)
-k_mrr_last(EvalArgs a)
+k_mrr_last(EvalArgs a0, JobsArg<JOBS> tab)
 {
+    EvalArgs a = a0;
     using Sh = NttShape<LOG_B, LOG_C, LOG_E>;
     extern __shared__ __align__(16) u64 smem[];
     const u32 tid = threadIdx.x;
     const u32 m = (LOG_C > 0) ? cluster_ctarank() : 0u;
-    const u32 item = blockIdx.x >> LOG_C;
+    u32 item = blockIdx.x >> LOG_C;
+    if constexpr (JOBS) item = bind_job(a, tab, JS_LAST, item);
     const u32 n = a.n, l = n - 1;
     const u32 c = item / 2, k = item % 2;
     const PrimeConst pc = a.ctx.pc[l];
@@ -853,15 +900,17 @@ k_mrr_last(EvalArgs a)
 //                   thread rewrites only the positions it read);
 //   k_mrr_rest_out: out[c][k][i] = (z_k[i] - NTT_i([y2_k]_{q_l})) q_l^-1.
 // Both transforms are left lazy (their outputs only enter Shoup products).
-template <int LOG_B, int LOG_C, int LOG_E>
+template <int LOG_B, int LOG_C, int LOG_E, bool JOBS = false>
 __global__ void __launch_bounds__(NttShape<LOG_B, LOG_C, LOG_E>::T, NttShape<LOG_B, LOG_C, LOG_E>::MIN_CTAS)
-k_mrr_rest_z(EvalArgs a)
+k_mrr_rest_z(EvalArgs a0, JobsArg<JOBS> tab)
 {
+    EvalArgs a = a0;
     using Sh = NttShape<LOG_B, LOG_C, LOG_E>;
     extern __shared__ __align__(16) u64 smem[];
     const u32 tid = threadIdx.x;
     const u32 m = (LOG_C > 0) ? cluster_ctarank() : 0u;
-    const u32 item = blockIdx.x >> LOG_C;
+    u32 item = blockIdx.x >> LOG_C;
+    if constexpr (JOBS) item = bind_job(a, tab, JS_REST, item);
     const u32 n = a.n, l = n - 1;
     const u32 c = item / (2 * l), k = (item / l) % 2, i = item % l;
     const PrimeConst pc = a.ctx.pc[i];
@@ -878,15 +927,17 @@ k_mrr_rest_z(EvalArgs a)
     store_pairs<Sh>(accp, x, m, tid);
 }
 
-template <int LOG_B, int LOG_C, int LOG_E>
+template <int LOG_B, int LOG_C, int LOG_E, bool JOBS = false>
 __global__ void __launch_bounds__(NttShape<LOG_B, LOG_C, LOG_E>::T, NttShape<LOG_B, LOG_C, LOG_E>::MIN_CTAS)
-k_mrr_rest_out(EvalArgs a)
+k_mrr_rest_out(EvalArgs a0, JobsArg<JOBS> tab)
 {
+    EvalArgs a = a0;
     using Sh = NttShape<LOG_B, LOG_C, LOG_E>;
     extern __shared__ __align__(16) u64 smem[];
     const u32 tid = threadIdx.x;
     const u32 m = (LOG_C > 0) ? cluster_ctarank() : 0u;
-    const u32 item = blockIdx.x >> LOG_C;
+    u32 item = blockIdx.x >> LOG_C;
+    if constexpr (JOBS) item = bind_job(a, tab, JS_REST, item);
     const u32 n = a.n, l = n - 1;
     const u32 c = item / (2 * l), k = (item / l) % 2, i = item % l;
     const PrimeConst pc = a.ctx.pc[i];

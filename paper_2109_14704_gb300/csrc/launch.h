@@ -5,6 +5,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "modarith.cuh"
 
 namespace he {
@@ -80,6 +82,26 @@ struct EvalArgs {
     DevCtx ctx;
 };
 
+// Mixed-level batches (one context): each launch of the MulLinRS pipeline
+// covers every job; job i's items in stage S start at job[i].begin[S].
+enum JobStage { JS_DIGITS = 0, JS_EXPAND, JS_MAC, JS_LAST, JS_REST, JS_COUNT };
+constexpr u32 kMaxJobs = 16;
+struct EvalJob {
+    const u64 *ct_a, *ct_b;     // [count][2][n][N]
+    u64 *out;                   // [count][2][n - 1][N]
+    u64 *c2, *accq, *plift, *lift2, *mx;   // the job's scratch regions
+    u32 n, count;
+    u32 begin[JS_COUNT];
+    u32 pad;
+};
+struct JobTable {               // passed by value (kernel parameter space)
+    EvalJob job[kMaxJobs];
+    u32 n_jobs;
+};
+struct NoJobs {};
+template <bool JOBS>
+using JobsArg = typename std::conditional<JOBS, JobTable, NoJobs>::type;
+
 enum EvalKernel {
     EK_KS_DIGITS = 0,
     EK_KS_MODUP,
@@ -109,8 +131,10 @@ struct DegreeOps {
     // Largest number of co-resident clusters of the persistent kernel.
     int (*max_clusters)(int log_b, int log_e, bool inverse);
     // Evaluation kernels over `items` clusters (the default words per CTA;
-    // log_e = 3 or 4 words per thread, 0 = 4).
-    cudaError_t (*eval)(EvalKernel k, const EvalArgs &a, u32 items, int log_e, cudaStream_t s);
+    // log_e = 3 or 4 words per thread, 0 = 4); with a job table (MulLinRS
+    // kernels only) the items run over every job of a mixed-level batch.
+    cudaError_t (*eval)(EvalKernel k, const EvalArgs &a, u32 items, int log_e, const JobTable *jobs,
+                        cudaStream_t s);
     // Is the shape built for this degree?
     bool (*has_shape)(int log_b, int log_e);
     // Shapes built for this degree: n pairs (log_b, log_e), default first.

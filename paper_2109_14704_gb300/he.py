@@ -35,6 +35,11 @@ class PolyDesc(ctypes.Structure):
                 ("first_prime", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
+class MrrJob(ctypes.Structure):
+    _fields_ = [("ct_out", ctypes.c_void_p), ("ct_a", ctypes.c_void_p), ("ct_b", ctypes.c_void_p),
+                ("count", ctypes.c_uint32), ("level", ctypes.c_uint32)]
+
+
 class NttShape(ctypes.Structure):
     _fields_ = [("N", ctypes.c_uint32), ("log_block", ctypes.c_uint32), ("log_thread_words", ctypes.c_uint32),
                 ("reserved", ctypes.c_uint32)]
@@ -113,6 +118,9 @@ _SIGS = {
                                    ctypes.c_size_t, _vp]),
     "he_crt_compose": (ctypes.c_int32, [_vp, _vp, _vp, ctypes.c_uint32, ctypes.c_uint32, _vp]),
     "he_fp64_probe": (ctypes.c_int32, [_vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, _vp]),
+    "he_mul_relin_rescale_batch_scratch_bytes": (ctypes.c_size_t, [_vp, ctypes.POINTER(MrrJob), ctypes.c_uint32]),
+    "he_mul_relin_rescale_batch": (ctypes.c_int32, [ctypes.POINTER(MrrJob), ctypes.c_uint32, _vp, _vp, _vp,
+                                                    ctypes.c_size_t, _vp]),
 }
 
 
@@ -378,6 +386,15 @@ class Context:
             return int(load().he_mul_relin_rescale_scratch_bytes(self.handle, level, count))
         return int(load().he_mul_relin_rescale_scratch_bytes_ex(self.handle, level, count, expand_group))
 
+    def mrr_batch_scratch_bytes(self, jobs) -> int:
+        """Scratch bytes of mul_relin_rescale_batch for jobs given as
+        (count, level) pairs (or full job tuples)."""
+        arr = (MrrJob * max(1, len(jobs)))()
+        for i, j in enumerate(jobs):
+            count, level = (j[0], j[1]) if len(j) == 2 else (j[3], j[4])
+            arr[i] = MrrJob(None, None, None, count, level)
+        return int(load().he_mul_relin_rescale_batch_scratch_bytes(self.handle, arr, len(jobs)))
+
     def close(self):
         if getattr(self, "handle", None):
             load().he_context_destroy(self.handle)
@@ -438,6 +455,17 @@ def mul_relin_rescale(ct_out, ct_a, ct_b, count: int, key: RelinKey, ctx: Contex
     w_in, w_out = count * 2 * (level + 1) * ctx.N, count * 2 * level * ctx.N
     _check(load().he_mul_relin_rescale(_ptr(ct_out, w_out), _ptr(ct_a, w_in), _ptr(ct_b, w_in), count, key.handle,
                                        ctx.handle, level, _ptr(scratch), scratch.numel() * 8, _stream(stream)))
+
+
+def mul_relin_rescale_batch(jobs, key: RelinKey, ctx: Context, scratch, stream=None):
+    """MulLinRS of a mixed-level batch, one launch per pipeline stage: jobs
+    are (ct_out, ct_a, ct_b, count, level) tuples of device tensors."""
+    arr = (MrrJob * max(1, len(jobs)))()
+    for i, (out, a, b, count, level) in enumerate(jobs):
+        w_in, w_out = count * 2 * (level + 1) * ctx.N, count * 2 * level * ctx.N
+        arr[i] = MrrJob(_ptr(out, w_out), _ptr(a, w_in), _ptr(b, w_in), count, level)
+    _check(load().he_mul_relin_rescale_batch(arr, len(jobs), key.handle, ctx.handle, _ptr(scratch),
+                                             scratch.numel() * 8, _stream(stream)))
 
 
 def sqr_relin_rescale(ct_out, ct_a, count: int, key: RelinKey, ctx: Context, level: int, scratch, stream=None):
