@@ -721,7 +721,9 @@ def bench_encode(args, stream, barrier):
 def bench_serving(args):
     """Poisson arrivals at 2000 requests/s of MulLinRS jobs, N in {8192,
     16384, 32768}, levels 2-16, keys resident, 64 GB admission budget: the
-    continuous-batching server versus the same server with one request per
+    continuous-batching server (batches per degree and level), the same
+    server batching every level of a degree together (mixed-level batches,
+    one launch per pipeline stage), and the server with one request per
     launch (one slot, one stream). Each server reserves its buffer pool at
     start-up (prewarm) and runs its loop without collector pauses."""
     from paper_2109_14704_gb300 import serving
@@ -730,6 +732,7 @@ def bench_serving(args):
 
     out = {"workload": "Poisson 2000 req/s, N in {8192,16384,32768}, levels 2-16, budget 64 GB"}
     for name, kw in (("batched", dict(slots=16, streams=4, prewarm_batches=8)),
+                     ("mixed_levels", dict(slots=16, streams=4, prewarm_batches=8, mixed_levels=True)),
                      ("plain", dict(slots=1, streams=1, prewarm_batches=4))):
         # every server starts from an empty allocator cache (the previous
         # phases' freed blocks would otherwise count against device memory)

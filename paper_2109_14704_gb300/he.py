@@ -457,6 +457,10 @@ def mul_relin_rescale(ct_out, ct_a, ct_b, count: int, key: RelinKey, ctx: Contex
                                        ctx.handle, level, _ptr(scratch), scratch.numel() * 8, _stream(stream)))
 
 
+# Jobs of a mixed-level batch that one pass of he_mul_relin_rescale_batch takes.
+MAX_BATCH_JOBS = 16
+
+
 def mul_relin_rescale_batch(jobs, key: RelinKey, ctx: Context, scratch, stream=None):
     """MulLinRS of a mixed-level batch, one launch per pipeline stage: jobs
     are (ct_out, ct_a, ct_b, count, level) tuples of device tensors."""

@@ -15,10 +15,14 @@ buffers come from a memory cache that reuses any free buffer large enough
   input ciphertexts are copied from pinned host memory straight into the
   batch slot.
 * A bucket's open batch is launched (one he_mul_relin_rescale call over all
-  its slots: four kernels) when it is full, when a stream is idle, or when
-  its oldest request has waited max_wait_s; meanwhile new arrivals fill the
-  next open batch (continuous batching), and batches in flight on several
-  streams overlap on the device.
+  its slots) when it is full, when a stream is idle, or when its oldest
+  request has waited max_wait_s; meanwhile new arrivals fill the next open
+  batch (continuous batching), and batches in flight on several streams
+  overlap on the device.
+* With mixed_levels, the buckets are the degrees alone: a batch takes
+  requests of any level (each slot sized for the highest level) and runs as
+  one he_mul_relin_rescale_batch call, one launch per pipeline stage for the
+  whole mix (each request one job).
 * Completion is timed with CUDA events; latency = completion - arrival on
   one clock (events are anchored to the host clock at start). Buffers go
   back to the memory cache when the batch's completion event has fired.
@@ -164,7 +168,7 @@ class Server:
 
     def __init__(self, degrees=(8192, 16384, 32768), min_level=2, max_level=16, budget_bytes=64 << 30,
                  slots=16, streams=4, max_wait_s=0.002, pool_per_bucket=2, seed=5, device=None, expand_group=4,
-                 prewarm_batches=0):
+                 prewarm_batches=0, mixed_levels=False):
         import torch
         self.torch = torch
         self.device = device or torch.device("cuda", torch.cuda.current_device())
@@ -179,6 +183,9 @@ class Server:
         # key-switching mod-up expanded in groups of at most this many
         # ciphertexts (bounds a batch's scratch; 0 = the fused minimum)
         self.expand_group = expand_group
+        self.mixed = mixed_levels
+        if mixed_levels and slots > he.MAX_BATCH_JOBS:
+            raise ValueError(f"mixed-level batches take at most {he.MAX_BATCH_JOBS} slots")
         self.rng = Rng(seed)
         self.ctx, self.key, self.moduli = {}, {}, {}
         self.static_bytes = 0
@@ -216,7 +223,7 @@ class Server:
         reuse them), allocated and returned to the cache, so that requests
         seldom wait for the device allocator."""
         N, lvl = max(self.degrees), self.max_level
-        words = self._batch_words(N, lvl, self.slots)
+        words = self._batch_words(N, lvl, self.slots)   # also the mixed form's size
         sets = []
         for _ in range(batches):
             got = self.cache.allocate_within(words, self.budget, self.static_bytes)
@@ -235,12 +242,21 @@ class Server:
     def _batch_words(self, N, lvl, cap):
         n = lvl + 1
         ct_in = 2 * n * N
-        return [cap * ct_in, cap * ct_in, cap * 2 * lvl * N,
-                self.ctx[N].mrr_scratch_bytes(lvl, cap, self.expand_group) // 8]
+        if self.mixed:   # slots sized for the highest level
+            scratch = self.ctx[N].mrr_batch_scratch_bytes([(1, lvl)] * cap) // 8
+        else:
+            scratch = self.ctx[N].mrr_scratch_bytes(lvl, cap, self.expand_group) // 8
+        return [cap * ct_in, cap * ct_in, cap * 2 * lvl * N, scratch]
+
+    def _slot_words(self, N, lvl):
+        """Input and output words of one slot of a batch (its stride)."""
+        if self.mixed:
+            lvl = self.max_level
+        return 2 * (lvl + 1) * N, 2 * lvl * N
 
     def _open_batch(self, key, now):
         N, lvl = key
-        words = self._batch_words(N, lvl, self.slots)
+        words = self._batch_words(N, self.max_level if self.mixed else lvl, self.slots)
         bufs = self.cache.allocate_within(words, self.budget, self.static_bytes)
         if bufs is None:
             return None
@@ -252,21 +268,21 @@ class Server:
 
     # ---- request flow
     def _admit(self, req: Request, now) -> bool:
-        key = (req.N, req.level)
+        key = (req.N, None if self.mixed else req.level)
         b = self.open.get(key)
         if b is None:
             b = self._open_batch(key, now)
             if b is None:
                 return False
         slot = len(b.reqs)
-        n = req.level + 1
-        per = 2 * n * req.N
-        src = self.pool[key][req.src]
+        per = 2 * (req.level + 1) * req.N
+        stride = self._slot_words(req.N, req.level)[0]
+        src = self.pool[(req.N, req.level)][req.src]
         a_t, b_t = b.bufs[0][1], b.bufs[1][1]
         # upload of the request's two ciphertexts into the batch slot
         with self.torch.cuda.stream(self.streams[0]):
-            a_t[slot * per:(slot + 1) * per].copy_(src[0].reshape(-1), non_blocking=True)
-            b_t[slot * per:(slot + 1) * per].copy_(src[1].reshape(-1), non_blocking=True)
+            a_t[slot * stride:slot * stride + per].copy_(src[0].reshape(-1), non_blocking=True)
+            b_t[slot * stride:slot * stride + per].copy_(src[1].reshape(-1), non_blocking=True)
         req.batch, req.slot = b, slot
         b.reqs.append(req)
         if len(b.reqs) == b.cap:
@@ -288,14 +304,23 @@ class Server:
         s = self.streams[stream_index]
         s.wait_stream(self.streams[0])          # the uploads
         N, lvl = b.key
-        n = lvl + 1
         count = len(b.reqs)
-        per_in, per_out = 2 * n * N, 2 * lvl * N
-        a = b.bufs[0][1][:count * per_in]
-        bb = b.bufs[1][1][:count * per_in]
-        out = b.bufs[2][1][:count * per_out]
         scratch = b.bufs[3][1]
-        he.mul_relin_rescale(out, a, bb, count, self.key[N], self.ctx[N], lvl, scratch, stream=s)
+        if self.mixed:
+            si, so = self._slot_words(N, None)
+            jobs = []
+            for r in b.reqs:
+                pi, po = 2 * (r.level + 1) * N, 2 * r.level * N
+                jobs.append((b.bufs[2][1][r.slot * so:r.slot * so + po], b.bufs[0][1][r.slot * si:r.slot * si + pi],
+                             b.bufs[1][1][r.slot * si:r.slot * si + pi], 1, r.level))
+            he.mul_relin_rescale_batch(jobs, self.key[N], self.ctx[N], scratch, stream=s)
+        else:
+            n = lvl + 1
+            per_in, per_out = 2 * n * N, 2 * lvl * N
+            a = b.bufs[0][1][:count * per_in]
+            bb = b.bufs[1][1][:count * per_in]
+            out = b.bufs[2][1][:count * per_out]
+            he.mul_relin_rescale(out, a, bb, count, self.key[N], self.ctx[N], lvl, scratch, stream=s)
         ev = torch.cuda.Event(enable_timing=True)
         ev.record(s)
         b.done_event, b.stream, b.launched = ev, s, True
@@ -310,13 +335,13 @@ class Server:
         for b in self.inflight:
             if b.done_event.query():
                 t = self.anchor.elapsed_time(b.done_event) / 1e3     # seconds since start
-                N, lvl = b.key
-                per_out = 2 * lvl * N
+                N = b.key[0]
                 for r in b.reqs:
                     r.done = t
                     self.completed.append(r)
                     if r.rid in self.keep:
-                        self.keep[r.rid] = b.bufs[2][1][r.slot * per_out:(r.slot + 1) * per_out].cpu().clone()
+                        so = self._slot_words(N, r.level)[1]
+                        self.keep[r.rid] = b.bufs[2][1][r.slot * so:r.slot * so + 2 * r.level * N].cpu().clone()
                 for cap, t_ in b.bufs:
                     self.cache.free(cap, t_)
                 if self.busy.get(b.stream_index) is b:

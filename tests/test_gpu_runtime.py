@@ -81,8 +81,9 @@ def _small_server(**kw):
     return serving.Server(**args)
 
 
-def test_serving_alone_equals_in_the_mix():
-    srv = _small_server()
+@pytest.mark.parametrize("mixed", [False, True])
+def test_serving_alone_equals_in_the_mix(mixed):
+    srv = _small_server(mixed_levels=mixed)
     reqs = srv.make_requests(240, rate=20000.0, seed=12)
     keep = [3, 50, 51, 52, 117, 200, 239]
     stats = srv.run(reqs, keep_ids=keep)
@@ -94,10 +95,13 @@ def test_serving_alone_equals_in_the_mix():
         assert torch.equal(srv.keep[rid], alone), rid
 
 
-def test_serving_result_matches_oracle():
-    srv = _small_server(degrees=(4096,), max_level=3)
+@pytest.mark.parametrize("mixed", [False, True])
+def test_serving_result_matches_oracle(mixed):
+    srv = _small_server(degrees=(4096,), max_level=3, mixed_levels=mixed)
     reqs = srv.make_requests(20, rate=5000.0, seed=13)
     srv.run(reqs, keep_ids=[7])
+    if mixed:   # one batch per degree held several levels
+        assert len({q.level for q in reqs}) > 1
     r = reqs[7]
     src = srv.pool[(r.N, r.level)][r.src].numpy().view(np.uint64)
     ctx = srv.ctx[r.N]
