@@ -387,6 +387,25 @@ he_status he_decode(const he_encoder *enc, double *slots_out, const uint64_t *pt
 he_status he_crt_compose(const he_encoder *enc, double *out, const uint64_t *coeffs, uint32_t count,
                          uint32_t level, he_stream_t stream);
 
+/* ---- encryption (Sec. II-A Encrypt) ------------------------------------------ */
+
+/* Device scratch of he_encrypt: count * 3 * (level + 1) * N * 8 bytes. */
+size_t he_encrypt_scratch_bytes(const he_context *ctx, uint32_t level, uint32_t count);
+
+/* Public-key encryption of `count` plaintexts at `level` (Sec. II-A):
+ *   c0 = v pk0 + m + e0,  c1 = v pk1 + e1  (mod q_0 .. q_level),
+ * with the products in the NTT domain. pt: count x (level + 1) x N words,
+ * NTT domain (he_encode's output); pk: the public key (pk0, pk1) as
+ * 2 x n_data x N words in the NTT domain, of which limbs 0..level are used;
+ * v, e0, e1: count x N signed 8-bit values each (device), the random
+ * ternary mask and the two error polynomials (any |x| < 2^7; the caller
+ * draws them, e.g. uniform {-1, 0, 1} and a rounded Gaussian of sigma 3.2);
+ * ct_out: count x 2 x (level + 1) x N words. scratch: he_encrypt_scratch_bytes.
+ * HE_EINVAL for a bad level, pointer or short scratch. */
+he_status he_encrypt(uint64_t *ct_out, const uint64_t *pt, const uint64_t *pk, const int8_t *v,
+                     const int8_t *e0, const int8_t *e1, uint32_t count, const he_context *ctx,
+                     uint32_t level, void *scratch, size_t scratch_bytes, he_stream_t stream);
+
 /* ---- batched plans (Sec. III-B parallelism over limbs and instances) -------- */
 
 /* One polynomial of a batched NTT: `limbs` limbs of degree N at `data`

@@ -392,6 +392,45 @@ __global__ void k_ct_matmul_tensor(u64 *t, const u64 *a, const u64 *b, u32 m, u3
     }
 }
 
+// ============================================================ Encrypt ======
+
+// Residues of the encryption's small random polynomials: out[c][w][l][i] =
+// src_w[c][i] mod q_l for w = 0, 1, 2 (v, e0, e1; signed 8-bit values with
+// |x| < q), count messages of n limbs.
+__global__ void k_enc_noise(u64 *out, const int8_t *v, const int8_t *e0, const int8_t *e1, u32 log_n, u32 n,
+                            u32 count, const PrimeConst *pcs)
+{
+    const u64 N = 1ull << log_n, words = (u64)count * 3 * n * N;
+    for (u64 e = (u64)blockIdx.x * blockDim.x + threadIdx.x; e < words; e += (u64)gridDim.x * blockDim.x) {
+        const u64 i = e & (N - 1), row = e >> log_n;
+        const u32 l = (u32)(row % n), w = (u32)((row / n) % 3);
+        const u64 c = row / (3 * (u64)n);
+        const int8_t *src = w == 0 ? v : (w == 1 ? e0 : e1);
+        const int x = src[c * N + i];
+        out[e] = x >= 0 ? (u64)x : pcs[l].p - (u64)(-x);
+    }
+}
+
+// Public-key encryption (Sec. II-A) from the transformed randomness:
+// c0 = v pk0 + pt + e0, c1 = v pk1 + e1 (NTT domain, limb by limb).
+// noise [count][3][n][N] (v, e0, e1 transformed), pt [count][n][N],
+// pk [2][pk_limbs][N], ct [count][2][n][N].
+__global__ void k_enc_combine(u64 *ct, const u64 *noise, const u64 *pt, const u64 *pk, u32 log_n, u32 n, u32 count,
+                              u32 pk_limbs, const PrimeConst *pcs)
+{
+    const u64 N = 1ull << log_n, per = (u64)n * N, total = (u64)count * per;
+    for (u64 e = (u64)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (u64)gridDim.x * blockDim.x) {
+        const u64 c = e / per, off = e - c * per;
+        const u32 l = (u32)(off >> log_n);
+        const PrimeConst pc = pcs[l];
+        const u64 *z = noise + c * 3 * per + off;
+        const u64 vh = z[0], e0h = z[per], e1h = z[2 * per];
+        const u64 c0 = add_mod(add_mod(mul_mod(vh, pk[off], pc), pt[e], pc.p), e0h, pc.p);
+        const u64 c1 = add_mod(mul_mod(vh, pk[(u64)pk_limbs * N + off], pc), e1h, pc.p);
+        ct[c * 2 * per + off] = c0;
+        ct[c * 2 * per + per + off] = c1;
+    }
+}
 #endif  // HE_MISC_KERNELS
 
 // ============================================== key switching and rescale ==

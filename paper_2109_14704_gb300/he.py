@@ -118,6 +118,9 @@ _SIGS = {
                                    ctypes.c_size_t, _vp]),
     "he_crt_compose": (ctypes.c_int32, [_vp, _vp, _vp, ctypes.c_uint32, ctypes.c_uint32, _vp]),
     "he_fp64_probe": (ctypes.c_int32, [_vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, _vp]),
+    "he_encrypt_scratch_bytes": (ctypes.c_size_t, [_vp, ctypes.c_uint32, ctypes.c_uint32]),
+    "he_encrypt": (ctypes.c_int32, [_vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_uint32, _vp, ctypes.c_uint32, _vp,
+                                    ctypes.c_size_t, _vp]),
     "he_mul_relin_rescale_batch_scratch_bytes": (ctypes.c_size_t, [_vp, ctypes.POINTER(MrrJob), ctypes.c_uint32]),
     "he_mul_relin_rescale_batch": (ctypes.c_int32, [ctypes.POINTER(MrrJob), ctypes.c_uint32, _vp, _vp, _vp,
                                                     ctypes.c_size_t, _vp]),
@@ -191,6 +194,16 @@ def _fptr(x, doubles: int):
         raise ValueError("expected float64 or complex128")
     if x.numel() * per < doubles:
         raise ValueError(f"device tensor holds {x.numel() * per} doubles, the call needs {doubles}")
+    return x.data_ptr()
+
+
+def _i8ptr(x, values: int):
+    """Device pointer of an int8 torch tensor holding at least `values` entries."""
+    import torch
+    if not x.is_cuda or not x.is_contiguous() or x.dtype != torch.int8:
+        raise ValueError("expected a contiguous int8 CUDA tensor")
+    if x.numel() < values:
+        raise ValueError(f"device tensor holds {x.numel()} values, the call needs {values}")
     return x.data_ptr()
 
 
@@ -386,6 +399,9 @@ class Context:
             return int(load().he_mul_relin_rescale_scratch_bytes(self.handle, level, count))
         return int(load().he_mul_relin_rescale_scratch_bytes_ex(self.handle, level, count, expand_group))
 
+    def encrypt_scratch_bytes(self, level: int, count: int) -> int:
+        return int(load().he_encrypt_scratch_bytes(self.handle, level, count))
+
     def mrr_batch_scratch_bytes(self, jobs) -> int:
         """Scratch bytes of mul_relin_rescale_batch for jobs given as
         (count, level) pairs (or full job tuples)."""
@@ -455,6 +471,16 @@ def mul_relin_rescale(ct_out, ct_a, ct_b, count: int, key: RelinKey, ctx: Contex
     w_in, w_out = count * 2 * (level + 1) * ctx.N, count * 2 * level * ctx.N
     _check(load().he_mul_relin_rescale(_ptr(ct_out, w_out), _ptr(ct_a, w_in), _ptr(ct_b, w_in), count, key.handle,
                                        ctx.handle, level, _ptr(scratch), scratch.numel() * 8, _stream(stream)))
+
+
+def encrypt(ct_out, pt, pk, v, e0, e1, count: int, ctx: Context, level: int, scratch, stream=None):
+    """Public-key encryption (Sec. II-A) of NTT-domain plaintexts with the
+    given randomness: v, e0, e1 are int8 tensors [count][N]; pk is the
+    public key [2][n_data][N] (NTT domain)."""
+    N, n = ctx.N, level + 1
+    _check(load().he_encrypt(_ptr(ct_out, count * 2 * n * N), _ptr(pt, count * n * N), _ptr(pk, 2 * ctx.n_data * N),
+                             _i8ptr(v, count * N), _i8ptr(e0, count * N), _i8ptr(e1, count * N), count, ctx.handle,
+                             level, _ptr(scratch), scratch.numel() * 8, _stream(stream)))
 
 
 # Jobs of a mixed-level batch that one pass of he_mul_relin_rescale_batch takes.

@@ -236,3 +236,60 @@ def test_edge_cases():
         enc.decode(z0, pt, 2, 2.0 ** 40, 3, empty(16))   # short scratch
     with pytest.raises(ValueError):
         enc.decode(z0[:1], pt, 2, 2.0 ** 40, 3, sc)      # short output (binding check)
+
+
+def _i8(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.int8)).cuda()
+
+
+@pytest.mark.parametrize("level", [3, 1])
+def test_encrypt_matches_oracle(level):
+    """Public-key encryption (Sec. II-A) with the same draws as the oracle's
+    (v ternary, e0 and e1 rounded Gaussian, in that order from one seeded
+    generator): bit-exact ciphertexts."""
+    N, data, ctx, enc = _setup("n4k")
+    P = ctx.P
+    keys = ckks.keygen(N, data, P, Rng(900))
+    qs = data[:level + 1]
+    count = 2
+    m = [ckks.encode_real(Rng(901 + c).complex_slots(N // 2), N, 2.0 ** 40) for c in range(count)]
+    ref = [ckks.encrypt(m[c], keys, Rng(910 + c), level) for c in range(count)]
+    draws = [Rng(910 + c) for c in range(count)]
+    v, e0, e1 = [], [], []
+    for r in draws:
+        v.append(r.ternary(N))
+        e0.append(r.gaussian(N))
+        e1.append(r.gaussian(N))
+    pt = dev(np.stack([oracle.ntt_fwd(ckks.to_residues(m[c], qs), qs) for c in range(count)]))
+    ct = empty(count, 2, level + 1, N)
+    he.encrypt(ct, pt, dev(keys.pk), _i8(np.stack(v)), _i8(np.stack(e0)), _i8(np.stack(e1)), count, ctx, level,
+               empty(ctx.encrypt_scratch_bytes(level, count) // 8))
+    got = host(ct)
+    for c in range(count):
+        assert np.array_equal(got[c], ref[c]), c
+
+
+def test_device_ckks_pipeline():
+    """Encode, encrypt, MulLinRS and decode on the device (decryption with the
+    secret key on the host): the decoded product matches the exact complex
+    product within the 1e-5 bar."""
+    N, data, ctx, enc = _setup("n8k")
+    P, L, scale = ctx.P, len(data) - 1, 2.0 ** 40
+    keys = ckks.keygen(N, data, P, Rng(920))
+    key = he.RelinKey(ctx, keys.evk)
+    r = Rng(921)
+    za, zb = r.complex_slots(N // 2), r.complex_slots(N // 2)
+    pt = empty(2, L + 1, N)
+    enc.encode(pt, _slots_dev(np.stack([za, zb])), 2, scale, L, empty(enc.encode_scratch_bytes(2) // 8))
+    draws = [[r.ternary(N), r.gaussian(N), r.gaussian(N)] for _ in range(2)]
+    ct = empty(2, 2, L + 1, N)
+    he.encrypt(ct, pt, dev(keys.pk), *[_i8(np.stack([d[w] for d in draws])) for w in range(3)], 2, ctx, L,
+               empty(ctx.encrypt_scratch_bytes(L, 2) // 8))
+    out = empty(1, 2, L, N)
+    he.mul_relin_rescale(out, ct[0:1], ct[1:2], 1, key, ctx, L, empty(ctx.mrr_scratch_bytes(L, 1) // 8))
+    dec = ckks.decrypt_residues(host(out)[0], keys)                  # coefficient domain
+    z = torch.empty((1, N // 2), dtype=torch.complex128, device="cuda")
+    enc.decode(z, dev(oracle.ntt_fwd(dec, data[:L])[None]), 1, scale * scale / data[L], L - 1,
+               empty(enc.decode_scratch_bytes(L - 1, 1) // 8))
+    exact = za * zb
+    assert _err(z.cpu().numpy()[0], exact) < 1e-5
