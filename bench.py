@@ -74,7 +74,7 @@ def _args():
                     help="NTT instances of --profile-case ntt, ciphertext pairs of --profile-case mrr")
     ap.add_argument("--shape", default="",
                     help="log_block,log_thread_words[,persistent] for --profile-case ntt (or fwd/inv)")
-    ap.add_argument("--skip", default="", help="comma list of sub-benchmarks to skip: uneven,matrix,routines,encode,serving")
+    ap.add_argument("--skip", default="", help="comma list of sub-benchmarks to skip: small,uneven,matrix,routines,encode,serving")
     ap.add_argument("--serve-requests", type=int, default=4000)
     ap.add_argument("--no-tune-cache", action="store_true", help="always re-run the autotuner")
     a = ap.parse_args()
@@ -321,6 +321,7 @@ def run_ours(args, rank, world, local):
 
     ms_mrr_plain = max_over_ranks(_time_steps(mrr_plain, max(2, args.steps // 5), 1, stream, barrier))
 
+    small = bench_small(args, stream, barrier) if "small" not in args.skip else None
     uneven = bench_uneven(args, stream, barrier) if "uneven" not in args.skip else None
     matrix = bench_matrix(args, stream, barrier) if "matrix" not in args.skip else None
     routines = bench_routines(args, stream, barrier) if "routines" not in args.skip else None
@@ -423,6 +424,7 @@ def run_ours(args, rank, world, local):
                      "inverse": dict(zip(("log_block", "log_thread_words", "persistent"), tune["inv"])),
                      "candidates": [{"shape": c["shape"], "ms_fwd": c.get("ms_fwd"), "ms_inv": c.get("ms_inv")}
                                     for c in tune["candidates"]]},
+        "small_ntt": small,
         "uneven_batch": uneven,
         "matrix_mul_relin_rescale": matrix,
         "routines": routines,
@@ -483,6 +485,83 @@ def _measured_peaks() -> dict:
 
 
 # ------------------------------------------------------ other workloads
+
+def bench_small(args, stream, barrier):
+    """The plain single transform (N = 4096, two 60-bit primes, two
+    polynomials a and b): latency of forward + inverse, and of the
+    negacyclic product a b = INTT(NTT(a) . NTT(b)), each a short chain of
+    launches on one stream (latency bound: reported in microseconds)."""
+    import numpy as np
+    import torch
+
+    from paper_2109_14704_gb300 import he
+    from paper_2109_14704_gb300.synth import Rng
+
+    N, limbs = 4096, 2
+    qs = he.primes_generate(60, 2 * N, limbs)
+    tables = he.NttTables(N, qs)
+    r = Rng(1)
+    a = torch.from_numpy(np.stack([r.uniform_limbs(qs, N)]).view(np.int64)).cuda()
+    b = torch.from_numpy(np.stack([r.uniform_limbs(qs, N)]).view(np.int64)).cuda()
+    c = torch.empty_like(a)
+
+    def fwd_inv():
+        he.ntt_fwd(a, N, limbs, 1, tables, stream=stream)
+        he.ntt_inv(a, N, limbs, 1, tables, stream=stream)
+
+    def product():
+        he.ntt_fwd(a, N, limbs, 1, tables, stream=stream)
+        he.ntt_fwd(b, N, limbs, 1, tables, stream=stream)
+        he.dyadic_mul(c, a, b, N, limbs, 1, tables, stream=stream)
+        he.ntt_inv(c, N, limbs, 1, tables, stream=stream)
+        he.ntt_inv(a, N, limbs, 1, tables, stream=stream)
+        he.ntt_inv(b, N, limbs, 1, tables, stream=stream)
+
+    def fused():
+        he.negacyclic_mul(c, a, b, N, limbs, 1, tables, stream=stream)
+
+    reps = 200
+    us_fi = _time_steps(fwd_inv, reps, 20, stream, barrier) * 1e3
+    us_prod = _time_steps(product, reps, 20, stream, barrier) * 1e3
+    us_fused = _time_steps(fused, reps, 20, stream, barrier) * 1e3
+
+    # the same product over a batch that does not fit in L2: 128 polynomials
+    # x 8 limbs at N = 2^15 (3 x 256 MiB), fused (one launch: 24 B per word
+    # through HBM) against forward, forward, dyadic, inverse (72 B per word)
+    Nb, lb, cb = 32768, 8, 128
+    qb = he.primes_generate(60, 2 * Nb, 4) + he.primes_generate(50, 2 * Nb, 4)
+    tb = he.NttTables(Nb, qb)
+    A = torch.from_numpy(np.stack([r.uniform_limbs(qb, Nb) for _ in range(cb)]).view(np.int64)).cuda()
+    B = torch.from_numpy(np.stack([r.uniform_limbs(qb, Nb) for _ in range(cb)]).view(np.int64)).cuda()
+    Cb = torch.empty_like(A)
+
+    def batch_fused():
+        he.negacyclic_mul(Cb, A, B, Nb, lb, cb, tb, stream=stream)
+
+    A2, B2, C2 = A.clone(), B.clone(), torch.empty_like(A)
+
+    def batch_unfused():
+        # the same four passes on copies, in place (their contents drift
+        # from step to step, which does not change the work)
+        he.ntt_fwd(A2, Nb, lb, cb, tb, stream=stream)
+        he.ntt_fwd(B2, Nb, lb, cb, tb, stream=stream)
+        he.dyadic_mul(C2, A2, B2, Nb, lb, cb, tb, stream=stream)
+        he.ntt_inv(C2, Nb, lb, cb, tb, stream=stream)
+
+    steps = max(3, args.steps // 2)
+    ms_f = _time_steps(batch_fused, steps, 2, stream, barrier)
+    ms_u = _time_steps(batch_unfused, steps, 2, stream, barrier)
+    limbs_b = lb * cb
+    bfly = 3 * limbs_b * (Nb // 2) * 15
+    return {"workload": "N=4096, 2 x 60-bit primes, one polynomial (forward + inverse) or two (product)",
+            "us_forward_inverse": us_fi, "us_negacyclic_product": us_prod, "us_negacyclic_product_fused": us_fused,
+            "launches": {"forward_inverse": 2, "product": 6, "product_fused": 1},
+            "note": "latency of back-to-back launches on one stream (inputs in L2)",
+            "batch": {"workload": "negacyclic product, 128 polys x 8 limbs at N=2^15",
+                      "ms_fused": ms_f, "fused_products_per_s": limbs_b / (ms_f / 1e3),
+                      "fused_tbfly_per_s": bfly / (ms_f / 1e3) / 1e12,
+                      "ms_unfused": ms_u, "unfused_products_per_s": limbs_b / (ms_u / 1e3)}}
+
 
 def bench_uneven(args, stream, barrier):
     """Uneven batch: 512 polynomials, N uniform in {2^12 .. 2^15}, 1-16 limbs

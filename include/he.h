@@ -147,6 +147,18 @@ he_status he_dyadic_mul(uint64_t *out, const uint64_t *a, const uint64_t *b, uin
                         uint32_t limbs, uint32_t count, const uint64_t *moduli_host,
                         const he_ntt_tables *tw, he_stream_t stream);
 
+/* Negacyclic product c = a * b mod (X^N + 1, q_l), coefficient domain in and
+ * out, for `count` polynomials of `limbs` limbs (Sec. II-B: the product is
+ * INTT(NTT(a) . NTT(b))), fused into ONE launch: per limb, one cluster runs
+ * both forward transforms, the pointwise product and the inverse transform
+ * with the data on chip (16 bytes read and 8 written per word, against 72
+ * for he_ntt_fwd x 2 + he_dyadic_mul + he_ntt_inv). The transform shape is
+ * the forward shape set for N (he_ntt_set_shape). c may equal a or b; any
+ * other overlap is HE_EINVAL. Same layout and checks as he_ntt_fwd. */
+he_status he_negacyclic_mul(uint64_t *c, const uint64_t *a, const uint64_t *b, uint32_t N,
+                            uint32_t limbs, uint32_t count, const uint64_t *moduli_host,
+                            const he_ntt_tables *tw, he_stream_t stream);
+
 /* ---- CKKS evaluation (Sec. II-A) ------------------------------------------- */
 
 /* A modulus chain: n_data data primes q_0..q_L (L = n_data - 1, n_data <= 32)

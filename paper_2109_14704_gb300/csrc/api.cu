@@ -485,6 +485,37 @@ extern "C" he_status he_dyadic_mul(uint64_t *out, const uint64_t *a, const uint6
     return HE_OK;
 }
 
+extern "C" he_status he_negacyclic_mul(uint64_t *c, const uint64_t *a, const uint64_t *b, uint32_t N,
+                                       uint32_t limbs, uint32_t count, const uint64_t *moduli_host,
+                                       const he_ntt_tables *tw, he_stream_t stream)
+{
+    int log_n;
+    if (he_status s = check_poly_args(c, N, limbs, moduli_host, tw, &log_n)) return s;
+    if (!a || !b || ((uintptr_t)a & 15) || ((uintptr_t)b & 15))
+        return fail(HE_EINVAL, "inputs must be non-NULL and 16-byte aligned");
+    const u64 items = (u64)limbs * count;
+    if (!items) return HE_OK;
+    if (items * (N / 4096 + 1) > 0x7fffffffull) return fail(HE_EINVAL, "batch too large");
+    const u64 words = items * N;
+    const uintptr_t cb = (uintptr_t)c, ce = cb + words * 8;
+    for (const uint64_t *in : {a, b})
+        if ((uintptr_t)in < ce && cb < (uintptr_t)in + words * 8 && (uintptr_t)in != cb)
+            return fail(HE_EINVAL, "c overlaps an input without being equal to it");
+    // c may equal a or b: each cluster reads its limb of both before it writes c
+    he::NegaLaunch L = {};
+    L.c = c;
+    L.a = a;
+    L.b = b;
+    L.limbs = limbs;
+    L.items = (u32)items;
+    L.tw_fwd = tw->d_fwd;
+    L.tw_inv = tw->d_inv;
+    L.pc = tw->d_pc;
+    HE_CUDA(he::degree_ops(log_n)->negacyclic(L, g_shape_b[0][log_n].load(), g_shape_e[0][log_n].load(),
+                                              (cudaStream_t)stream));
+    return HE_OK;
+}
+
 // ----------------------------------------------------------------- context
 
 struct he_context {

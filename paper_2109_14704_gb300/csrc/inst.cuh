@@ -64,6 +64,14 @@ struct ShapeOps {
                         s, a);
     }
 
+    static cudaError_t negacyclic(const NegaLaunch &a, cudaStream_t s)
+    {
+        static std::once_flag f;
+        static cudaError_t e = cudaSuccess;
+        if (cudaError_t r = smem_attr(k_negacyclic<LOG_B, LOG_C, LOG_E>, 2 * Sh::SMEM_BYTES, f, e)) return r;
+        return launch_k(k_negacyclic<LOG_B, LOG_C, LOG_E>, a.items * Sh::C, Sh::T, 2 * Sh::SMEM_BYTES, Sh::C, s, a);
+    }
+
     template <bool INV>
     static int max_clusters()
     {
@@ -204,13 +212,23 @@ struct DegreeImpl;
         if (log_e == 3) return ShapeOps<D::def_b, LOG_N_ - D::def_b, 3>::eval(k, a, items, jobs, s); \
         return ShapeOps<D::def_b, LOG_N_ - D::def_b, 4>::eval(k, a, items, jobs, s);               \
     }                                                                                              \
+    static cudaError_t nega_##LOG_N_(const NegaLaunch &a, int log_b, int log_e, cudaStream_t s)     \
+    {                                                                                              \
+        using D = DegreeImpl<LOG_N_>;                                                              \
+        bool found = false;                                                                        \
+        cudaError_t r = D::with_shape(log_b, log_e, [&](auto ops) {                                \
+            found = true;                                                                          \
+            return decltype(ops)::negacyclic(a, s);                                                \
+        });                                                                                        \
+        return found ? r : cudaErrorInvalidValue;                                                  \
+    }                                                                                              \
     static bool has_##LOG_N_(int log_b, int log_e)                                                 \
     {                                                                                              \
         return DegreeImpl<LOG_N_>::with_shape(log_b, log_e, [&](auto) { return true; });           \
     }                                                                                              \
     extern const DegreeOps degree_ops_##LOG_N_ = {                                                 \
         LOG_N_, DegreeImpl<LOG_N_>::def_b, DegreeImpl<LOG_N_>::def_e, ntt_##LOG_N_, ntt_p_##LOG_N_,  \
-        maxcl_##LOG_N_, eval_##LOG_N_, has_##LOG_N_,                                               \
+        maxcl_##LOG_N_, eval_##LOG_N_, has_##LOG_N_, nega_##LOG_N_,                                \
         (int)(sizeof(DegreeImpl<LOG_N_>::shapes) / sizeof(DegreeImpl<LOG_N_>::shapes[0])),         \
         DegreeImpl<LOG_N_>::shapes};                                                               \
     }

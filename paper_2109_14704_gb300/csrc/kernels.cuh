@@ -142,6 +142,55 @@ __global__ void __launch_bounds__(256, 4) k_ntt_mixed(const MixedUnit *units, u3
     }
 }
 
+// ============================================================ fused product
+
+// c = a b mod (X^N + 1, q) for one limb per cluster (Sec. II-B: the
+// product of two polynomials is the inverse transform of the pointwise
+// product of their transforms): the forward transform of a, its values
+// parked in a second shared-memory block (each thread its own positions),
+// the forward transform of b, the pointwise Barrett product in registers,
+// and the inverse transform straight to c. Per word 16 B are read and 8 B
+// written, against 72 B for three separate passes.
+template <int LOG_B, int LOG_C, int LOG_E>
+__global__ void __launch_bounds__(NttShape<LOG_B, LOG_C, LOG_E>::T, NttShape<LOG_B, LOG_C, LOG_E>::NEGA_MIN_CTAS)
+k_negacyclic(NegaLaunch a)
+{
+    using Sh = NttShape<LOG_B, LOG_C, LOG_E>;
+    extern __shared__ __align__(16) u64 smem[];
+    u64 *park = smem + Sh::B;                    // [E][T]
+    const u32 tid = threadIdx.x;
+    const u32 m = (LOG_C > 0) ? cluster_ctarank() : 0u;
+    const u32 item = blockIdx.x >> LOG_C;
+    const u32 pr = item % a.limbs;
+    const PrimeConst pc = a.pc[pr];
+    const ulonglong2 *twf = a.tw_fwd + (size_t)pr * Sh::N, *twi = a.tw_inv + (size_t)pr * Sh::N;
+    const u64 *A = a.a + (size_t)item * Sh::N, *Bp = a.b + (size_t)item * Sh::N;
+    u64 *C = a.c + (size_t)item * Sh::N;
+    u64 x[Sh::E];
+    auto nost = [&](u32, u64) {};
+    // one copy of the forward transform run twice (a loop, not unrolled):
+    // two inlined copies let the compiler keep the first one's address and
+    // twiddle values live into the second, which spills
+#pragma unroll 1
+    for (int it = 0; it < 2; it++) {
+        const u64 *src = it ? Bp : A;
+        if (it) ntt_barrier<Sh>();
+        auto ld = [&](int P) -> u64 { return __ldcs(reinterpret_cast<const unsigned long long *>(src + P)); };
+        ntt_fwd_block<Sh>(smem, m, 0, twf, pc, ld, nost, x);
+        if (it == 0) {
+#pragma unroll
+            for (int e = 0; e < Sh::E; e++) park[e * Sh::T + tid] = x[e];
+        } else {
+#pragma unroll
+            for (int e = 0; e < Sh::E; e++) x[e] = mul_mod(x[e], park[e * Sh::T + tid], pc);
+        }
+    }
+    ntt_barrier<Sh>();
+    auto nold = [&](u32) -> u64 { return 0; };
+    auto st = [&](int P, u64 v) { __stcs(reinterpret_cast<unsigned long long *>(C + P), (unsigned long long)v); };
+    ntt_inv_block<Sh, true>(smem, m, 0, twi, pc, nold, st, x);
+}
+
 #ifdef HE_MISC_KERNELS  // defined by the one translation unit that owns them
 // ======================================================== naive radix-2 ====
 // The baseline of Sec. III-B: one launch per stage, each thread one

@@ -33,6 +33,20 @@ struct NttLaunch {
     const LimbJob *jobs;        // non-null: per-item jobs instead of base/limbs
 };
 
+// Fused negacyclic product c = a b mod (X^N + 1, q) of items = count * limbs
+// limbs (limb l of polynomial p at (p limbs + l) N, prime first_prime + l):
+// forward transforms of a and b, pointwise product and inverse transform in
+// one launch, the data staying on chip in between.
+struct NegaLaunch {
+    u64 *c;
+    const u64 *a, *b;
+    u32 limbs;
+    u32 items;
+    const ulonglong2 *tw_fwd;   // [prime][N]
+    const ulonglong2 *tw_inv;
+    const PrimeConst *pc;       // [prime]
+};
+
 // A unit of the mixed-degree persistent transform: up to 8 >> (log_n - 12)
 // limbs of degree 2^log_n, jobs[first_job .. first_job + n_jobs).
 struct MixedUnit {
@@ -137,6 +151,8 @@ struct DegreeOps {
                         cudaStream_t s);
     // Is the shape built for this degree?
     bool (*has_shape)(int log_b, int log_e);
+    // Fused negacyclic product in the given transform shape (0, 0 = default).
+    cudaError_t (*negacyclic)(const NegaLaunch &a, int log_b, int log_e, cudaStream_t s);
     // Shapes built for this degree: n pairs (log_b, log_e), default first.
     int n_shapes;
     const int (*shapes)[2];

@@ -137,6 +137,11 @@ struct NttShape {
     static constexpr int MIN_CTAS = (65536 / (int)(T * REGS)) > 0 ? 65536 / (int)(T * REGS) : 1;
     // evaluation kernels carry more state per thread: 128 registers
     static constexpr int EVAL_MIN_CTAS = (65536 / (int)(T * 128)) > 0 ? 65536 / (int)(T * 128) : 1;
+    // the fused product (three transforms, a second shared-memory block):
+    // 80 registers with 16 words per thread (three CTAs per SM, which its
+    // shared memory allows anyway), 64 with 8
+    static constexpr int NEGA_REGS = LOG_E == 4 ? 80 : 64;
+    static constexpr int NEGA_MIN_CTAS = (65536 / (int)(T * NEGA_REGS)) > 0 ? 65536 / (int)(T * NEGA_REGS) : 1;
     static_assert(LOG_C <= 3, "portable clusters hold at most 8 CTAs");
     static_assert(LOG_C <= LOG_E, "a thread holds whole columns of the cross stages");
     static_assert(LOG_E == 3 || LOG_E == 4, "radix 8 or 16 rounds");

@@ -118,6 +118,8 @@ _SIGS = {
                                    ctypes.c_size_t, _vp]),
     "he_crt_compose": (ctypes.c_int32, [_vp, _vp, _vp, ctypes.c_uint32, ctypes.c_uint32, _vp]),
     "he_fp64_probe": (ctypes.c_int32, [_vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, _vp]),
+    "he_negacyclic_mul": (ctypes.c_int32, [_vp, _vp, _vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, _u64p,
+                                           _vp, _vp]),
     "he_encrypt_scratch_bytes": (ctypes.c_size_t, [_vp, ctypes.c_uint32, ctypes.c_uint32]),
     "he_encrypt": (ctypes.c_int32, [_vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_uint32, _vp, ctypes.c_uint32, _vp,
                                     ctypes.c_size_t, _vp]),
@@ -357,6 +359,15 @@ def dyadic_mul(out, a, b, N, limbs, count, tables: NttTables, moduli=None, strea
     w = N * limbs * count
     _check(load().he_dyadic_mul(_ptr(out, w), _ptr(a, w), _ptr(b, w), N, limbs, count, _hp(m), tables.handle,
                                 _stream(stream)))
+
+
+def negacyclic_mul(c, a, b, N, limbs, count, tables: NttTables, moduli=None, stream=None):
+    """Fused negacyclic product c = a b mod (X^N + 1, q) in one launch
+    (coefficient domain in and out)."""
+    m = _moduli_arg(tables, limbs, moduli)
+    w = N * limbs * count
+    _check(load().he_negacyclic_mul(_ptr(c, w), _ptr(a, w), _ptr(b, w), N, limbs, count, _hp(m), tables.handle,
+                                    _stream(stream)))
 
 
 class Context:
