@@ -261,7 +261,7 @@ def matmul_tensor(A, B, moduli) -> np.ndarray:
     return out
 
 
-# ---- multi-threaded drivers for the timed CPU baseline -------------------------
+# ---- multi-threaded runners for the timed CPU baseline -------------------------
 
 def ntt_fwd_many(polys: np.ndarray, moduli, threads: int) -> np.ndarray:
     """Forward NTT of polys[poly][limb][N] over (poly, limb) units on
