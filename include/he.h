@@ -434,21 +434,25 @@ typedef struct he_poly_desc {
 /* Kernel shape of a plan for one N: 2^log_block words per CTA (the rest of
  * the transform is split over a cluster of N / 2^log_block CTAs exchanging
  * through distributed shared memory) and 2^log_thread_words words per
- * thread (radix-2^log_thread_words register rounds; 0 = 16 words). */
+ * thread (radix-2^log_thread_words register rounds; 0 = 16 words);
+ * persistent != 0 launches a fixed grid of co-resident clusters walking the
+ * degree's limbs instead of one cluster per limb (the default, measured
+ * faster). */
 typedef struct he_ntt_shape {
     uint32_t N;
     uint32_t log_block;
     uint32_t log_thread_words;
-    uint32_t reserved;
+    uint32_t persistent;
 } he_ntt_shape;
 
 /* A plan that transforms all `count` polynomials (any mix of N and limb
- * counts) with persistent kernels driven by a device-resident work list.
- * Without shape overrides (n_shapes = 0) and with every N in [2^12, 2^15],
- * the whole plan is ONE launch per direction: clusters of 8 CTAs split into
+ * counts) with kernels driven by a device-resident work list. Without shape
+ * overrides (n_shapes = 0) and with every N in [2^12, 2^15], the whole plan
+ * is ONE launch per direction: one cluster of 8 CTAs per unit of work (8
+ * limbs of 2^12, 4 of 2^13, 2 of 2^14 or 1 of 2^15), split into
  * sub-clusters per degree. With overrides (e.g. the autotuner's choices per
- * N), each degree gets its own persistent launch in the given shape.
- * Allocates the work list and synchronises; execution allocates nothing. */
+ * N), each degree gets its own launch in the given shape. Allocates the
+ * work list and synchronises; execution allocates nothing. */
 he_status he_ntt_plan_create(const he_poly_desc *descs_host, uint32_t count,
                              const he_ntt_shape *shapes_host, uint32_t n_shapes,
                              he_plan **out);

@@ -16,7 +16,7 @@ by device, N, limbs and count, and applied with he_ntt_set_shape so that the
 plain he_ntt_fwd / he_ntt_inv calls use them.
 
 For uneven batches, tune_plan compares the single mixed-degree launch with
-per-degree persistent launches in each degree's tuned shape.
+per-degree launches (one cluster per limb) in each degree's tuned shape.
 """
 from __future__ import annotations
 

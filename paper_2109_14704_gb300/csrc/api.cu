@@ -1501,10 +1501,10 @@ struct he_plan {
         int log_b;
         int log_e;
         u32 items;
-        u32 clusters;
+        u32 clusters;                  // persistent grid (0: one cluster per limb)
         he::LimbJob *d_jobs;
     };
-    std::vector<Group> groups;         // per-degree persistent launches
+    std::vector<Group> groups;         // per-degree launches
     bool mixed = false;                // one mixed-degree launch per direction
     he::MixedUnit *d_units = nullptr;
     he::LimbJob *d_mixed_jobs = nullptr;
@@ -1596,8 +1596,11 @@ extern "C" he_status he_ntt_plan_create(const he_poly_desc *descs_host, uint32_t
         }
         plan->mixed = true;
         plan->n_units = (u32)units.size();
-        plan->clusters_fwd = std::min<u32>(plan->n_units, (u32)std::max(he::mixed_max_clusters(false), 1));
-        plan->clusters_inv = std::min<u32>(plan->n_units, (u32)std::max(he::mixed_max_clusters(true), 1));
+        // one cluster per unit: measured faster than a persistent grid of
+        // co-resident clusters walking the units (independent clusters keep
+        // every SM busy with CTAs in different phases)
+        plan->clusters_fwd = plan->n_units;
+        plan->clusters_inv = plan->n_units;
         *out = plan;
         return HE_OK;
     }
@@ -1607,14 +1610,18 @@ extern "C" he_status he_ntt_plan_create(const he_poly_desc *descs_host, uint32_t
         const he::DegreeOps *ops = he::degree_ops(g.log_n);
         g.log_b = ops->default_log_b;
         g.log_e = ops->default_log_e;
+        bool persistent = false;
         for (u32 s = 0; s < n_shapes; s++)
             if (shapes_host[s].N == (1u << g.log_n) && shapes_host[s].log_block) {
                 g.log_b = (int)shapes_host[s].log_block;
                 g.log_e = shapes_host[s].log_thread_words ? (int)shapes_host[s].log_thread_words : 4;
+                persistent = shapes_host[s].persistent != 0;
             }
         g.items = (u32)kv.second.size();
-        const int mc = std::max(ops->max_clusters(g.log_b, g.log_e, false), 1);
-        g.clusters = std::min<u32>(g.items, (u32)mc);
+        if (persistent) {
+            const int mc = std::max(ops->max_clusters(g.log_b, g.log_e, false), 1);
+            g.clusters = std::min<u32>(g.items, (u32)mc);
+        }
         cudaError_t e = upload(&g.d_jobs, kv.second);
         if (e != cudaSuccess) {
             he_plan_destroy(plan);
@@ -1638,7 +1645,11 @@ static he_status plan_run(const he_plan *plan, he_stream_t stream, bool inv)
         he::NttLaunch a = {};
         a.items = g.items;
         a.jobs = g.d_jobs;
-        HE_CUDA(he::degree_ops(g.log_n)->ntt_persistent(a, g.log_b, g.log_e, inv, g.clusters, (cudaStream_t)stream));
+        if (g.clusters)
+            HE_CUDA(he::degree_ops(g.log_n)->ntt_persistent(a, g.log_b, g.log_e, inv, g.clusters,
+                                                            (cudaStream_t)stream));
+        else
+            HE_CUDA(he::degree_ops(g.log_n)->ntt(a, g.log_b, g.log_e, inv, (cudaStream_t)stream));
     }
     return HE_OK;
 }

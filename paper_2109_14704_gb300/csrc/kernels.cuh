@@ -103,8 +103,8 @@ k_ntt_persistent(NttLaunch a)
     }
 }
 
-// Mixed-degree persistent form: clusters of 8 CTAs of 2^12 words each walk a
-// list of units; a unit of degree 2^(12+c) holds up to 8 >> c limbs, each
+// Mixed-degree form: clusters of 8 CTAs of 2^12 words each take units of a
+// list (plans launch one cluster per unit; a smaller grid walks the list); a unit of degree 2^(12+c) holds up to 8 >> c limbs, each
 // transformed by a sub-cluster of 2^c CTAs (cluster ranks rbase .. rbase +
 // 2^c - 1). One launch covers every degree from 2^12 to 2^15. Sub-clusters
 // without a limb in the last unit of a degree recompute the unit's first

@@ -47,7 +47,7 @@ struct NegaLaunch {
     const PrimeConst *pc;       // [prime]
 };
 
-// A unit of the mixed-degree persistent transform: up to 8 >> (log_n - 12)
+// A unit of the mixed-degree transform: up to 8 >> (log_n - 12)
 // limbs of degree 2^log_n, jobs[first_job .. first_job + n_jobs).
 struct MixedUnit {
     u32 log_n;
@@ -57,10 +57,10 @@ struct MixedUnit {
 };
 
 // Mixed-degree transform of N in [2^12, 2^15]: one launch of `clusters`
-// clusters of 8 CTAs walking the unit list (mixed.cu).
+// clusters of 8 CTAs walking the unit list (mixed.cu; plans launch one
+// cluster per unit).
 cudaError_t launch_ntt_mixed(const MixedUnit *units, u32 n_units, const LimbJob *jobs, bool inverse, u32 clusters,
                              cudaStream_t s);
-int mixed_max_clusters(bool inverse);
 
 // Device view of a modulus chain (q_0..q_{n_data-1}, then P at n_data).
 struct DevCtx {

@@ -1,4 +1,4 @@
-// mixed.cu -- launcher of the mixed-degree persistent transform (one launch
+// mixed.cu -- launcher of the mixed-degree transform (one launch
 // for every limb of degree 2^12 .. 2^15 in a plan; see k_ntt_mixed).
 #include <mutex>
 
@@ -46,22 +46,6 @@ cudaError_t launch_ntt_mixed(const MixedUnit *units, u32 n_units, const LimbJob 
     }
     if (cudaError_t e = mixed_prepare<false>()) return e;
     return cudaLaunchKernelEx(&cfg, k_ntt_mixed<false>, units, n_units, jobs);
-}
-
-int mixed_max_clusters(bool inverse)
-{
-    cudaLaunchAttribute attr[1];
-    cudaLaunchConfig_t cfg = mixed_cfg(1024, nullptr, attr);
-    int n = 0;
-    cudaError_t e = inverse ? mixed_prepare<true>() : mixed_prepare<false>();
-    if (e == cudaSuccess)
-        e = inverse ? cudaOccupancyMaxActiveClusters(&n, k_ntt_mixed<true>, &cfg)
-                    : cudaOccupancyMaxActiveClusters(&n, k_ntt_mixed<false>, &cfg);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return 0;
-    }
-    return n;
 }
 
 }  // namespace he

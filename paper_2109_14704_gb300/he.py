@@ -42,7 +42,7 @@ class MrrJob(ctypes.Structure):
 
 class NttShape(ctypes.Structure):
     _fields_ = [("N", ctypes.c_uint32), ("log_block", ctypes.c_uint32), ("log_thread_words", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32)]
+                ("persistent", ctypes.c_uint32)]
 
 
 _SIGS = {
@@ -611,7 +611,8 @@ class Encoder:
 
 class NttPlan:
     """he_plan over a list of (tensor, tables, N, limbs, first_prime).
-    `shapes` maps N to log_block or to (log_block, log_thread_words)."""
+    `shapes` maps N to log_block, (log_block, log_thread_words) or
+    (log_block, log_thread_words, persistent)."""
 
     def __init__(self, polys, shapes=None):
         arr = (PolyDesc * max(len(polys), 1))()
@@ -626,8 +627,8 @@ class NttPlan:
         shapes = shapes or {}
         sh = (NttShape * max(len(shapes), 1))()
         for i, (N, shape) in enumerate(shapes.items()):
-            lb, le = (shape, 4) if isinstance(shape, int) else shape
-            sh[i].N, sh[i].log_block, sh[i].log_thread_words = N, lb, le
+            lb, le, pe = (shape, 4, 0) if isinstance(shape, int) else (tuple(shape) + (0,))[:3]
+            sh[i].N, sh[i].log_block, sh[i].log_thread_words, sh[i].persistent = N, lb, le, pe
         h = _vp()
         _check(load().he_ntt_plan_create(arr, len(polys), sh, len(shapes), ctypes.byref(h)))
         self.handle = h
