@@ -283,14 +283,14 @@ def run_ours(args, rank, world, local):
         for t in per_poly:
             he.ntt_inv(t, N, NTT_LIMBS, 1, tables, stream=stream)
 
-    ms_plain = _time_steps(step_plain, max(2, args.steps // 5), 1, stream, barrier)
+    ms_plain = _time_steps(step_plain, max(2, args.steps // 5), 3, stream, barrier)
 
     # the paper's naive radix-2 baseline (one launch per stage)
     def step_naive():
         he.ntt_fwd_naive(d, N, NTT_LIMBS, NTT_INSTANCES, tables, stream=stream)
         he.ntt_inv_naive(d, N, NTT_LIMBS, NTT_INSTANCES, tables, stream=stream)
 
-    ms_naive = _time_steps(step_naive, max(2, args.steps // 5), 1, stream, barrier)
+    ms_naive = _time_steps(step_naive, max(2, args.steps // 5), 3, stream, barrier)
 
     # MulLinRS on the CKKS evaluation workload
     data, P = he.chain_primes(MRR_N, MRR_BITS, 60)
@@ -319,7 +319,7 @@ def run_ours(args, rank, world, local):
         for c in range(MRR_COUNT):
             he.mul_relin_rescale(out[c], ca[c], cb[c], 1, key, ctx, L, s1, stream=stream)
 
-    ms_mrr_plain = max_over_ranks(_time_steps(mrr_plain, max(2, args.steps // 5), 1, stream, barrier))
+    ms_mrr_plain = max_over_ranks(_time_steps(mrr_plain, max(2, args.steps // 5), 3, stream, barrier))
 
     small = bench_small(args, stream, barrier) if "small" not in args.skip else None
     uneven = bench_uneven(args, stream, barrier) if "uneven" not in args.skip else None
@@ -376,7 +376,7 @@ def run_ours(args, rank, world, local):
     def probe():
         he.butterfly_probe(sink, sms * 8, 256, iters, stream=stream)
 
-    ms_probe = _time_steps(probe, 5, 2, stream, lambda: None)
+    ms_probe = _time_steps(probe, 5, 3, stream, lambda: None)
     bfly_rate = sms * 8 * 256 * 16 * iters / (ms_probe / 1e3)
     bfly_per_launch = limbs_total * (N // 2) * NTT_LOG_N
 
@@ -551,8 +551,8 @@ def bench_small(args, stream, barrier):
         he.ntt_inv(C2, Nb, lb, cb, tb, stream=stream)
 
     steps = max(3, args.steps // 2)
-    ms_f = _time_steps(batch_fused, steps, 2, stream, barrier)
-    ms_u = _time_steps(batch_unfused, steps, 2, stream, barrier)
+    ms_f = _time_steps(batch_fused, steps, 3, stream, barrier)
+    ms_u = _time_steps(batch_unfused, steps, 3, stream, barrier)
     limbs_b = lb * cb
     bfly = 3 * limbs_b * (Nb // 2) * 15
     return {"workload": "N=4096, 2 x 60-bit primes, one polynomial (forward + inverse) or two (product)",
@@ -621,7 +621,7 @@ def bench_uneven(args, stream, barrier):
     ms_mixed = _time_steps(run_plan(mixed), args.steps, args.warmup, stream, barrier)
     ms_graph = _time_steps(g.replay, args.steps, args.warmup, stream, barrier)
     ms_deg = _time_steps(run_plan(per_degree), args.steps, args.warmup, stream, barrier)
-    ms_plain = _time_steps(step_plain, max(2, args.steps // 5), 1, stream, barrier)
+    ms_plain = _time_steps(step_plain, max(2, args.steps // 5), 3, stream, barrier)
     return {
         "workload": "512 polys, N in {4096..32768}, 1-16 limbs of 50-60-bit primes, seed 3",
         "limbs": limbs, "words": words,
@@ -691,8 +691,8 @@ def bench_matrix(args, stream, barrier):
             he.relin_rescale(R, T, m * n, key, ctx, L, sc, stream=stream)
             he.ct_add(Cm, Cm, R, m * n, 2, ctx, L - 1, stream=stream)
 
-        ms_t = _time_steps(t_step, max(3, args.steps // 2), 2, stream, barrier)
-        ms_mm = _time_steps(mm_step, max(3, args.steps // 2), 2, stream, barrier)
+        ms_t = _time_steps(t_step, max(3, args.steps // 2), 3, stream, barrier)
+        ms_mm = _time_steps(mm_step, max(3, args.steps // 2), 3, stream, barrier)
         res["matmul"][f"{m}x{k}x{n}"] = {
             "ms_per_matmul": ms_mm, "ms_tensor": ms_t, "tensor_products": m * k * n,
             "relin_rescale_outputs": m * n,
@@ -735,7 +735,7 @@ def bench_routines(args, stream, barrier):
     res = {"workload": f"N=32768, {len(data)} data primes (60 + 7 x 50) + 60-bit special, level {L}, "
                        f"batches of {count} ciphertexts"}
     for name, fn in ops.items():
-        ms = _time_steps(fn, max(3, args.steps // 2), 2, stream, barrier)
+        ms = _time_steps(fn, max(3, args.steps // 2), 3, stream, barrier)
         res[name] = {"ms_per_batch": ms, "per_s": count / (ms / 1e3)}
     return res
 
@@ -767,21 +767,21 @@ def bench_encode(args, stream, barrier):
     sc = torch.empty(max(enc.encode_scratch_bytes(count), enc.decode_scratch_bytes(level, count)) // 8,
                      dtype=torch.int64, device="cuda")
     steps = max(3, args.steps // 2)
-    ms_enc = _time_steps(lambda: enc.encode(pt, z, count, scale, level, sc, stream=stream), steps, 2, stream, barrier)
-    ms_dec = _time_steps(lambda: enc.decode(zo, pt, count, scale, level, sc, stream=stream), steps, 2, stream,
+    ms_enc = _time_steps(lambda: enc.encode(pt, z, count, scale, level, sc, stream=stream), steps, 3, stream, barrier)
+    ms_dec = _time_steps(lambda: enc.decode(zo, pt, count, scale, level, sc, stream=stream), steps, 3, stream,
                          barrier)
     torch.cuda.synchronize()
     err = float(((zo - z).abs().max() / z.abs().max()).item())
     coef.copy_(pt)
-    ms_crt = _time_steps(lambda: enc.crt_compose(m, coef, count, level, stream=stream), steps, 2, stream, barrier)
-    ms_fwd = _time_steps(lambda: he.ntt_fwd(coef, N, level + 1, count, tables, stream=stream), steps, 2, stream,
+    ms_crt = _time_steps(lambda: enc.crt_compose(m, coef, count, level, stream=stream), steps, 3, stream, barrier)
+    ms_fwd = _time_steps(lambda: he.ntt_fwd(coef, N, level + 1, count, tables, stream=stream), steps, 3, stream,
                          barrier)
-    ms_inv = _time_steps(lambda: he.ntt_inv(coef, N, level + 1, count, tables, stream=stream), steps, 2, stream,
+    ms_inv = _time_steps(lambda: he.ntt_inv(coef, N, level + 1, count, tables, stream=stream), steps, 3, stream,
                          barrier)
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     sink = torch.empty(sms * 8 * 256, dtype=torch.float64, device="cuda")
     iters = 4096
-    ms_probe = _time_steps(lambda: he.fp64_probe(sink, sms * 8, 256, iters, stream=stream), 5, 2, stream, barrier)
+    ms_probe = _time_steps(lambda: he.fp64_probe(sink, sms * 8, 256, iters, stream=stream), 5, 3, stream, barrier)
     fp64_peak = sms * 8 * 256 * iters * 16 / (ms_probe / 1e3) / 1e12
     fft_flop = 5.0 * n * math.log2(n) * count
     ms_fft_enc = ms_enc - ms_fwd
