@@ -868,9 +868,11 @@ def cpu_baseline(target_seconds: float, limbs: int | None = None) -> dict:
     assert np.array_equal(z, x)
     transforms = 2 * polys * NTT_LIMBS
     return {"value": transforms / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "single_thread_value": 1.0 / per_transform,
             "sample": f"{polys} instances x {NTT_LIMBS} limbs at N=2^15, forward + inverse "
                       f"({transforms} limb transforms, {wall:.1f} s wall, plain __int128 % oracle, "
-                      f"one host thread per (instance, limb) unit)"}
+                      f"one host thread per (instance, limb) unit); single_thread_value: one instance "
+                      f"({2 * NTT_LIMBS} limb transforms) on one thread"}
 
 
 def run_reference(args, rank, world):
