@@ -568,8 +568,8 @@ def bench_small(args, stream, barrier):
 def bench_uneven(args, stream, barrier):
     """Uneven batch: 512 polynomials, N uniform in {2^12 .. 2^15}, 1-16 limbs
     each from a pool of sixteen 50-60-bit primes = 1 mod 2^16 (seed 3). One
-    mixed-degree launch per direction versus per-degree persistent launches
-    versus one launch per polynomial."""
+    mixed-degree launch per direction versus per-degree launches (one cluster
+    per limb) versus one launch per polynomial."""
     import numpy as np
     import torch
 
