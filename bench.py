@@ -68,7 +68,7 @@ def _args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle sample")
-    ap.add_argument("--profile-case", choices=["ntt", "mrr", "probe", "encode"],
+    ap.add_argument("--profile-case", choices=["ntt", "mrr", "probe", "encode", "product"],
                     help="run one small case of a kernel family and exit (for profilers)")
     ap.add_argument("--instances", type=int, default=64,
                     help="NTT instances of --profile-case ntt, ciphertext pairs of --profile-case mrr")
@@ -921,7 +921,9 @@ def profile_case(args):
     then inverse, `mrr` runs one MulLinRS batch of args.instances pairs on
     the CKKS workload (--shape: log2 words per thread of its kernels),
     `encode` encodes and decodes args.instances messages at N = 2^15 with 8
-    limbs, `probe` the butterfly probe. Each runs `--steps` times."""
+    limbs, `product` runs the fused negacyclic product of args.instances x 8
+    limbs at N = 2^15, `probe` the butterfly probe. Each runs `--steps`
+    times."""
     import numpy as np
     import torch
 
@@ -960,6 +962,17 @@ def profile_case(args):
             ctx.set_eval_shape(int(args.shape))
         for _ in range(args.steps):
             he.mul_relin_rescale(out, ca, cb, count, key, ctx, L, scratch)
+    elif args.profile_case == "product":
+        N = 1 << NTT_LOG_N
+        qs = _ntt_moduli()
+        tables = he.NttTables(N, qs)
+        r = Rng(6)
+        mk = lambda: torch.from_numpy(np.stack([r.uniform_limbs(qs, N) for _ in range(args.instances)])
+                                      .view(np.int64)).to(dev)
+        a, b = mk(), mk()
+        c = torch.empty_like(a)
+        for _ in range(args.steps):
+            he.negacyclic_mul(c, a, b, N, NTT_LIMBS, args.instances, tables)
     elif args.profile_case == "encode":
         N, level = 32768, 7
         data, P = he.chain_primes(N, [60] + [50] * 7, 60)
