@@ -108,7 +108,7 @@ he_status he_ntt_tables_psi(const he_ntt_tables *t, uint32_t index, uint64_t *ps
 he_status he_ntt_fwd(uint64_t *poly, uint32_t N, uint32_t limbs, uint32_t count,
                      const uint64_t *moduli_host, const he_ntt_tables *tw, he_stream_t stream);
 
-/* Inverse negacyclic NTT, in place, including the factor N^-1, so that
+/* Inverse negacyclic NTT (Sec. II-B), in place, including the factor N^-1, so that
  * he_ntt_inv(he_ntt_fwd(a)) = a exactly. Same layout and checks. */
 he_status he_ntt_inv(uint64_t *poly, uint32_t N, uint32_t limbs, uint32_t count,
                      const uint64_t *moduli_host, const he_ntt_tables *tw, he_stream_t stream);
@@ -161,8 +161,10 @@ he_status he_negacyclic_mul(uint64_t *c, const uint64_t *a, const uint64_t *b, u
 
 /* ---- CKKS evaluation (Sec. II-A) ------------------------------------------- */
 
-/* A modulus chain: n_data data primes q_0..q_L (L = n_data - 1, n_data <= 32)
- * and one special prime P, all distinct, 2^30 <= q < 2^60, q = 1 mod 2N. Builds the
+/* A modulus chain (the RNS representation of Sec. II-B; levels and the
+ * special prime of key switching, Sec. II-A): n_data data primes q_0..q_L
+ * (L = n_data - 1, n_data <= 32) and one special prime P, all distinct,
+ * 2^30 <= q < 2^60, q = 1 mod 2N. Builds the
  * NTT tables of all n_data + 1 primes and the constants of key switching and
  * rescaling. Synchronises. */
 he_status he_context_create(uint32_t N, uint32_t n_data, const uint64_t *data_moduli_host,
@@ -174,7 +176,8 @@ he_status he_context_destroy(he_context *ctx);
  * it). The autotuner times both. */
 he_status he_context_set_eval_shape(he_context *ctx, uint32_t log_thread_words);
 
-/* Upload a relinearization key. evk_host is [n_data][2][n_data + 1][N] in the
+/* Upload a relinearization key (the evk of Relin, Sec. II-A; a Galois key
+ * for he_rotate has the same layout). evk_host is [n_data][2][n_data + 1][N] in the
  * NTT domain: digit j, component k, limbs q_0..q_L then P; it must satisfy
  * evk[j][0] + evk[j][1] s = e_j + [j = i] (P mod q_i) s^2 on limb q_i (and no
  * s^2 term on P), i.e. one RNS digit per data prime and one special prime.
@@ -236,7 +239,7 @@ he_status he_sqr_relin_rescale(uint64_t *ct_out, const uint64_t *ct_a, uint32_t 
                                const he_relin_key *key, const he_context *ctx, uint32_t level,
                                void *scratch, size_t scratch_bytes, he_stream_t stream);
 
-/* MulLin: Mul then Relin of `count` pairs, no rescale: ct_out
+/* MulLin (Sec. IV-C routine set): Mul then Relin of `count` pairs, no rescale: ct_out
  * [count][2][l+1][N] equals he_relin(he_ct_mul(a, b)). Scratch: at least
  * (3 n + 2) N words per pair; he_mul_relin_scratch_bytes also makes room
  * for the expanded mod-up (groups of up to 64). */
@@ -245,7 +248,8 @@ he_status he_mul_relin(uint64_t *ct_out, const uint64_t *ct_a, const uint64_t *c
                        const he_relin_key *key, const he_context *ctx, uint32_t level, void *scratch,
                        size_t scratch_bytes, he_stream_t stream);
 
-/* Relin then RS of `count` three-component ciphertexts ct3
+/* Relin then RS (Sec. II-A; the lazy relinearization of the matrix product,
+ * Sec. IV-E) of `count` three-component ciphertexts ct3
  * [count][3][l+1][N] (for instance tensors accumulated over a matrix
  * product, relinearized once per output), into [count][2][l][N]; equals
  * he_rescale(he_relin(ct3)). Scratch as MulLinRS. */
@@ -259,7 +263,8 @@ he_status he_relin_rescale(uint64_t *ct_out, const uint64_t *ct3, uint32_t count
 he_status he_ct_add(uint64_t *ct_out, const uint64_t *ct_a, const uint64_t *ct_b, uint32_t count,
                     uint32_t components, const he_context *ctx, uint32_t level, he_stream_t stream);
 
-/* The automorphism X -> X^galois_elt (odd, below 2N) applied to each of
+/* The automorphism X -> X^galois_elt (odd, below 2N; the first step of
+ * Rotate, Sec. IV-C) applied to each of
  * `components` components of `count` level-l ciphertexts in the NTT domain
  * ([count][components][l+1][N]); a permutation of every limb's evaluations.
  * Not in place. */
@@ -291,7 +296,8 @@ he_status he_rotate(uint64_t *ct_out, const uint64_t *ct_in, uint32_t count, uin
 he_status he_ct_matmul_tensor(uint64_t *t_out, const uint64_t *a, const uint64_t *b, uint32_t m, uint32_t k,
                               uint32_t n, const he_context *ctx, uint32_t level, he_stream_t stream);
 
-/* Allocation-free MulLinRS. The paper has no counterpart: this entry point
+/* Allocation-free MulLinRS (Sec. IV-C). The paper has no counterpart for the
+ * allocation-free form: this entry point
  * exists for callers that cannot allocate device memory when they need the
  * routine -- code running during stream capture, latency-critical serving
  * paths that must not block on the device allocator, and embedders whose
@@ -331,7 +337,7 @@ typedef struct he_mrr_job {
 size_t he_mul_relin_rescale_batch_scratch_bytes(const he_context *ctx, const he_mrr_job *jobs_host,
                                                 uint32_t n_jobs);
 
-/* MulLinRS of every job, each with exactly the result he_mul_relin_rescale
+/* MulLinRS (Sec. IV-C) of every job, each with exactly the result he_mul_relin_rescale
  * gives for it alone, with ONE launch per pipeline stage for all jobs
  * together (digit INTT, mod-up transforms, key multiply-accumulate, the
  * special prime's INTT, and the three mod-down / rescale kernels): the
@@ -356,7 +362,7 @@ he_status he_mul_relin_rescale_batch(const he_mrr_job *jobs_host, uint32_t n_job
  * (Sec. III); these calls do it on the device with an FP64 FFT of n points. */
 typedef struct he_encoder he_encoder;    /* FFT and CRT tables of a context */
 
-/* Builds the tables for every level of `ctx` (which must outlive the
+/* Builds the encoding tables (Sec. II-A) for every level of `ctx` (which must outlive the
  * encoder). Synchronises. */
 he_status he_encoder_create(const he_context *ctx, he_encoder **out);
 he_status he_encoder_destroy(he_encoder *enc);
@@ -366,7 +372,7 @@ he_status he_encoder_destroy(he_encoder *enc);
 size_t he_encode_scratch_bytes(const he_encoder *enc, uint32_t count);
 size_t he_decode_scratch_bytes(const he_encoder *enc, uint32_t level, uint32_t count);
 
-/* Encode: for each of `count` messages, the real polynomial m with
+/* Encode (Sec. II-A): for each of `count` messages, the real polynomial m with
  * m(zeta^(5^j)) = scale * slots_j and m(zeta^(-5^j)) = its conjugate,
  * rounded coefficient by coefficient to the nearest integer (ties to even),
  * reduced modulo q_0..q_level and transformed to the NTT domain:
@@ -381,7 +387,7 @@ size_t he_decode_scratch_bytes(const he_encoder *enc, uint32_t level, uint32_t c
 he_status he_encode(const he_encoder *enc, uint64_t *pt_out, const double *slots, uint32_t count,
                     double scale, uint32_t level, void *scratch, size_t scratch_bytes, he_stream_t stream);
 
-/* Decode: the inverse NTT of each plaintext pt[c] (count messages of
+/* Decode (Sec. II-A): the inverse NTT of each plaintext pt[c] (count messages of
  * level + 1 limbs, NTT domain, canonical), the CRT lift of every
  * coefficient to the centred integer in [-(Q-1)/2, (Q-1)/2], Q = q_0 ...
  * q_level, its nearest double, the slot values m(zeta^(5^j)) of that real
@@ -391,7 +397,7 @@ he_status he_encode(const he_encoder *enc, uint64_t *pt_out, const double *slots
 he_status he_decode(const he_encoder *enc, double *slots_out, const uint64_t *pt, uint32_t count,
                     double scale, uint32_t level, void *scratch, size_t scratch_bytes, he_stream_t stream);
 
-/* The CRT step of decoding alone: out[c * N + i] = the nearest double
+/* The CRT step of decoding (Sec. II-A, Sec. II-B RNS) alone: out[c * N + i] = the nearest double
  * (round to nearest even) of the centred integer whose residues modulo
  * q_0..q_level are coeffs[(c * (level + 1) + l) * N + i] (coefficient
  * domain, canonical). out and coeffs are device buffers, 8-byte aligned
@@ -445,7 +451,8 @@ typedef struct he_ntt_shape {
     uint32_t persistent;
 } he_ntt_shape;
 
-/* A plan that transforms all `count` polynomials (any mix of N and limb
+/* A plan (Sec. III-B parallelism over limbs and instances) that transforms
+ * all `count` polynomials (any mix of N and limb
  * counts) with kernels driven by a device-resident work list. Without shape
  * overrides (n_shapes = 0) and with every N in [2^12, 2^15], the whole plan
  * is ONE launch per direction: one cluster of 8 CTAs per unit of work (8
@@ -468,7 +475,7 @@ uint32_t he_plan_launches(const he_plan *plan);
 #define HE_NTT_OP_FORWARD 1u
 #define HE_NTT_OP_INVERSE 2u
 
-/* Transforms `count` polynomials of `limbs` limbs that live in HOST memory
+/* Transforms (Sec. III asynchronous pipeline) `count` polynomials of `limbs` limbs that live in HOST memory
  * (same layout and checks as he_ntt_fwd): in_host is copied to the device,
  * transformed and copied back to out_host. ops = HE_NTT_OP_FORWARD,
  * HE_NTT_OP_INVERSE or both (forward, then inverse). The batch is cut into
