@@ -70,3 +70,25 @@ def test_single_rank_collectives_are_identity():
     barrier()
     assert max_over_ranks(3.5) == 3.5
     assert bench.job_value(1, 100.0, 50.0) == pytest.approx(2000.0)
+
+
+def test_reference_arm_line_on_rank_zero():
+    """Rank 0 of the reference arm prints one JSON line with the contract's
+    keys: the oracle timed on the host cores, its own cpu_baseline, and an
+    e2e figure with no host-device traffic."""
+    import json
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class A:
+        steps, warmup = 2, 0
+    buf = io.StringIO()
+    with redirect_stdout(buf):
+        bench.run_reference(A, 0, 1)
+    lines = [l for l in buf.getvalue().splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["value"] > 0 and d["higher_is_better"] is True and d["steps"] == 2
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
