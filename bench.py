@@ -58,6 +58,8 @@ FWD_TRAFFIC = {"shape": [12, 4, 0], "bytes": 4 * (541124352 + 481917696)}
 # SMs x clock / FMAHEAVY_CYCLES_PER_BFLY butterflies per second.
 FMAHEAVY_CYCLES_PER_BFLY = 0.2536
 UNIT = "limb-NTT/s"
+CPU_RUNS = 5                          # the CPU baseline is the median of this many runs
+REF_INSTANCES = NTT_INSTANCES // 8    # reference arm: 1/8 of the batch per step
 
 
 def _args():
@@ -77,6 +79,8 @@ def _args():
     ap.add_argument("--skip", default="", help="comma list of sub-benchmarks to skip: small,uneven,matrix,routines,encode,serving")
     ap.add_argument("--serve-requests", type=int, default=4000)
     ap.add_argument("--no-tune-cache", action="store_true", help="always re-run the autotuner")
+    ap.add_argument("--ref-instances", type=int, default=REF_INSTANCES,
+                    help="instances per step of the reference arm (default: 1/8 of the batch)")
     a = ap.parse_args()
     a.skip = set(x for x in a.skip.split(",") if x)
     return a
@@ -405,12 +409,7 @@ def run_ours(args, rank, world, local):
         "vs_baseline": None,
         "dtype": "u64",
         "data": "synthetic: seeded uniform residues (SplitMix64), 60/50-bit NTT primes",
-        "config": {
-            "workload": "NTT N=2^15, 1024 instances x 8 RNS limbs (4 x 60-bit, 4 x 50-bit primes), "
-                        "forward + inverse per step, in place",
-            "N": N, "limbs": NTT_LIMBS, "instances": NTT_INSTANCES, "parallelism": f"replicas x{world}",
-            "l2": "inputs larger than L2 (2 GiB per direction)",
-        },
+        "config": _ntt_config(f"replicas x{world}"),
         "ntt": {
             "batched_limbs_per_s": value,
             "graph_limbs_per_s": world * 2 * limbs_total / (ms_graph / 1e3),
@@ -839,9 +838,18 @@ def bench_serving(args):
 
 # ------------------------------------------------------------- CPU oracle
 
+def _ntt_config(parallelism: str) -> dict:
+    N = 1 << NTT_LOG_N
+    return {"workload": "NTT N=2^15, 1024 instances x 8 RNS limbs (4 x 60-bit, 4 x 50-bit primes), "
+                        "forward + inverse per step, in place",
+            "N": N, "limbs": NTT_LIMBS, "instances": NTT_INSTANCES, "parallelism": parallelism,
+            "l2": "inputs larger than L2 (2 GiB per direction)"}
+
+
 def cpu_baseline(target_seconds: float, limbs: int | None = None) -> dict:
     """The oracle's forward + inverse NTT at N = 2^15 on a bounded sample of
-    the workload's limbs, on all host cores."""
+    the workload's limbs, on all host cores: the median of CPU_RUNS runs,
+    each about target_seconds / CPU_RUNS of CPU work."""
     import numpy as np
 
     import oracle
@@ -851,31 +859,43 @@ def cpu_baseline(target_seconds: float, limbs: int | None = None) -> dict:
     qs = _ntt_moduli(cpu_oracle=True)
     cores = os.cpu_count() or 1
     x = np.stack([Rng(3000).uniform_limbs(qs, N)])
-    t = time.perf_counter()
-    y = oracle.ntt_fwd_many(x, qs, 1)                 # calibrate on one thread
-    oracle.ntt_inv_many(y, qs, 1)
-    per_transform = (time.perf_counter() - t) / (2 * NTT_LIMBS)
+    singles = []
+    for _ in range(3):                                  # calibrate on one thread
+        t = time.perf_counter()
+        y = oracle.ntt_fwd_many(x, qs, 1)
+        oracle.ntt_inv_many(y, qs, 1)
+        singles.append((time.perf_counter() - t) / (2 * NTT_LIMBS))
+    per_transform = statistics.median(singles)
     if limbs is None:
-        polys = max(1, int(target_seconds / (per_transform * 2 * NTT_LIMBS)))
+        polys = max(1, int(target_seconds / CPU_RUNS * cores / (per_transform * 2 * NTT_LIMBS)))
     else:
         polys = max(1, limbs // NTT_LIMBS)
+    polys = min(polys, NTT_INSTANCES)
     r = Rng(3001)
     x = np.stack([r.uniform_limbs(qs, N) for _ in range(polys)])
-    t = time.perf_counter()
-    y = oracle.ntt_fwd_many(x, qs, cores)
-    z = oracle.ntt_inv_many(y, qs, cores)
-    wall = time.perf_counter() - t
-    assert np.array_equal(z, x)
+    walls = []
+    for _ in range(CPU_RUNS):
+        t = time.perf_counter()
+        y = oracle.ntt_fwd_many(x, qs, cores)
+        z = oracle.ntt_inv_many(y, qs, cores)
+        walls.append(time.perf_counter() - t)
+        assert np.array_equal(z, x)
+    wall = statistics.median(walls)
     transforms = 2 * polys * NTT_LIMBS
     return {"value": transforms / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
             "single_thread_value": 1.0 / per_transform,
-            "sample": f"{polys} instances x {NTT_LIMBS} limbs at N=2^15, forward + inverse "
-                      f"({transforms} limb transforms, {wall:.1f} s wall, plain __int128 % oracle, "
-                      f"one host thread per (instance, limb) unit); single_thread_value: one instance "
-                      f"({2 * NTT_LIMBS} limb transforms) on one thread"}
+            "runs": CPU_RUNS, "wall_s": walls,
+            "sample": f"{polys} of {NTT_INSTANCES} instances x {NTT_LIMBS} limbs at N=2^15, forward + inverse "
+                      f"({transforms} limb transforms per run, median of {CPU_RUNS} runs, {wall:.2f} s each; "
+                      f"plain __int128 % oracle built with gcc -O3, one host thread per (instance, limb) "
+                      f"unit on {cores} cores); single_thread_value: one instance ({2 * NTT_LIMBS} limb "
+                      f"transforms) on one thread, median of 3"}
 
 
 def run_reference(args, rank, world):
+    """The oracle on the headline workload: each step is the forward and the
+    inverse transform of REF_INSTANCES of the 1024 instances (all 8 limbs),
+    on all host cores."""
     if rank != 0:
         return
     import numpy as np
@@ -886,7 +906,7 @@ def run_reference(args, rank, world):
     N = 1 << NTT_LOG_N
     qs = _ntt_moduli(cpu_oracle=True)
     cores = os.cpu_count() or 1
-    polys = max(1, cores // NTT_LIMBS) * 2          # a bounded sample per step
+    polys = getattr(args, "ref_instances", REF_INSTANCES)
     r = Rng(4000)
     x = np.stack([r.uniform_limbs(qs, N) for _ in range(polys)])
 
@@ -896,21 +916,25 @@ def run_reference(args, rank, world):
 
     for _ in range(args.warmup):
         step()
-    t = time.perf_counter()
+    walls = []
     for _ in range(args.steps):
+        t = time.perf_counter()
         step()
-    wall = (time.perf_counter() - t) / args.steps
+        walls.append(time.perf_counter() - t)
+    wall = sum(walls) / len(walls)
     transforms = 2 * polys * NTT_LIMBS
     value = transforms / wall
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": "NTT N=2^15, 1024 instances x 8 RNS limbs (4 x 60-bit, 4 x 50-bit primes), "
-                               "forward + inverse per step, in place",
-                   "N": N, "limbs": NTT_LIMBS, "instances": NTT_INSTANCES, "parallelism": "host threads"},
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic: seeded uniform residues (SplitMix64), 60/50-bit NTT primes",
+        "config": _ntt_config("replicas x1"),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"{polys} instances x {NTT_LIMBS} limbs per step (of 1024 x 8)"},
+                         "sample": f"{polys} of {NTT_INSTANCES} instances (1/{NTT_INSTANCES // polys} of the batch) "
+                                   f"x {NTT_LIMBS} limbs per step, forward + inverse, plain __int128 % oracle "
+                                   f"(gcc -O3), one host thread per (instance, limb) unit; median step "
+                                   f"{statistics.median(walls):.2f} s"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 

@@ -35,7 +35,7 @@ def _worker(rank, world, port, out):
     value = bench.job_value(world, 1000.0, ms)
     # the reference arm: rank 0 alone runs and prints; the others return at once
     class A:
-        steps, warmup = 1, 0
+        steps, warmup, ref_instances = 1, 0, 2
     buf = io.StringIO()
     if rank != 0:
         with redirect_stdout(buf):
@@ -81,7 +81,7 @@ def test_reference_arm_line_on_rank_zero():
     import bench
 
     class A:
-        steps, warmup = 2, 0
+        steps, warmup, ref_instances = 2, 0, 2
     buf = io.StringIO()
     with redirect_stdout(buf):
         bench.run_reference(A, 0, 1)
@@ -92,3 +92,6 @@ def test_reference_arm_line_on_rank_zero():
     assert d["value"] > 0 and d["higher_is_better"] is True and d["steps"] == 2
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    # the same workload description as the GPU arm's line
+    assert d["config"] == bench._ntt_config("replicas x1")
+    assert "2 of 1024 instances" in d["cpu_baseline"]["sample"]
