@@ -296,10 +296,10 @@ he_status he_rotate(uint64_t *ct_out, const uint64_t *ct_in, uint32_t count, uin
 he_status he_ct_matmul_tensor(uint64_t *t_out, const uint64_t *a, const uint64_t *b, uint32_t m, uint32_t k,
                               uint32_t n, const he_context *ctx, uint32_t level, he_stream_t stream);
 
-/* Allocation-free MulLinRS (Sec. IV-C). The paper has no counterpart for the
- * allocation-free form: this entry point
- * exists for callers that cannot allocate device memory when they need the
- * routine -- code running during stream capture, latency-critical serving
+/* Allocation-free MulLinRS: the same result as he_mul_relin_rescale. The
+ * paper has no counterpart; this entry point exists for callers that cannot
+ * allocate device memory when they need the routine -- code running during
+ * stream capture, latency-critical serving
  * paths that must not block on the device allocator, and embedders whose
  * device memory is budgeted by another runtime. It computes exactly what
  * he_mul_relin_rescale computes (same arguments minus the scratch buffer),
@@ -308,9 +308,11 @@ he_status he_ct_matmul_tensor(uint64_t *t_out, const uint64_t *a, const uint64_t
  * exits. It never allocates. Requests needing more scratch than that
  * ((3 (level + 1) + 4) * N * 8 bytes per pair, the fused mod-up's minimum)
  * return HE_EINVAL with a message; the expanded mod-up runs when the
- * buffer also holds its group buffer. The first call on each device resolves the buffer's address
- * (cudaGetSymbolAddress, with that device current), so make that first call
- * before any stream capture. All calls share the buffer: calls that may
+ * buffer also holds its group buffer. The first call on each device (and
+ * the first after that device's context was destroyed and re-created, e.g. by
+ * cudaDeviceReset) resolves the buffer's address (cudaGetSymbolAddress, with
+ * that device current); the address is cached per context, so make that first
+ * call before any stream capture. All calls share the buffer: calls that may
  * overlap on the GPU race and must be ordered by the caller (e.g. one
  * stream). No scratch word needs to start at zero. */
 #define HE_NOALLOC_SCRATCH_BYTES (16u << 20)

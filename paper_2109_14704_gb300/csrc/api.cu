@@ -5,6 +5,7 @@
 // path runs in the CUDA kernels of kernels.cuh. Argument checks happen before
 // anything is enqueued.
 #define HE_MISC_KERNELS 1
+#include <cuda.h>   // driver types only (CUcontext, CUresult); no link against the driver library
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -1794,8 +1795,46 @@ extern "C" he_status he_ntt_host(const uint64_t *in_host, uint64_t *out_host, ui
 static const size_t kNoAllocScratchBytes = (size_t)HE_NOALLOC_SCRATCH_BYTES;
 static __device__ __align__(256) u64 g_noalloc_scratch[kNoAllocScratchBytes / 8];
 
+// The resolved address belongs to the device's current context: after a
+// cudaDeviceReset (or any teardown and re-creation of the context) the module
+// is loaded again and the array may sit elsewhere. So the cache is keyed by
+// device ordinal AND the context's process-unique id (cuCtxGetId, fetched
+// through the runtime's driver entry points, so the library needs no link
+// against the driver library), and a changed id resolves the address again.
+struct NoAllocSlot {
+    unsigned long long ctx_id;   // 0: never resolved
+    void *addr;
+};
 static std::mutex g_noalloc_mutex;
-static void *g_noalloc_addr[256];   // per device ordinal, resolved once
+static NoAllocSlot g_noalloc_slot[256];
+
+typedef CUresult (*PfnCtxGetCurrent)(CUcontext *);
+typedef CUresult (*PfnCtxGetId)(CUcontext, unsigned long long *);
+
+// Id of the calling thread's current context (0 if there is none yet).
+static he_status current_context_id(unsigned long long *id)
+{
+    static std::once_flag once;
+    static PfnCtxGetCurrent get_current = nullptr;
+    static PfnCtxGetId get_id = nullptr;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = (PfnCtxGetCurrent)f;
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = (PfnCtxGetId)f;
+    });
+    if (!get_current || !get_id) return fail(HE_ECUDA, "driver entry points cuCtxGetCurrent / cuCtxGetId unavailable");
+    CUcontext c = nullptr;
+    if (get_current(&c) != CUDA_SUCCESS) return fail(HE_ECUDA, "cuCtxGetCurrent failed");
+    *id = 0;
+    if (c && get_id(c, id) != CUDA_SUCCESS) return fail(HE_ECUDA, "cuCtxGetId failed");
+    return HE_OK;
+}
 
 static he_status noalloc_scratch_address(void **out)
 {
@@ -1803,13 +1842,19 @@ static he_status noalloc_scratch_address(void **out)
     HE_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 256) return fail(HE_EUNSUPPORTED, "device ordinal %d out of range", dev);
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_addr[dev]) {
+    unsigned long long id = 0;
+    if (he_status s = current_context_id(&id)) return s;
+    NoAllocSlot &slot = g_noalloc_slot[dev];
+    if (id == 0 || slot.ctx_id != id) {
         void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);   // makes the device's context current
         if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(built-in scratch)");
-        g_noalloc_addr[dev] = p;
+        if (he_status s = current_context_id(&id)) return s;
+        if (id == 0) return fail(HE_ECUDA, "no current context after resolving the built-in scratch");
+        slot.ctx_id = id;
+        slot.addr = p;
     }
-    *out = g_noalloc_addr[dev];
+    *out = slot.addr;
     return HE_OK;
 }
 

@@ -11,7 +11,7 @@ HEADER = os.path.join(ROOT, "include", "he.h")
 
 EXEMPT = re.compile(r"_destroy$|_scratch_bytes(_ex)?$|^he_version$|^he_last_error$|^he_plan_launches$|"
                     r"^he_ntt_shapes$|^he_ntt_set_shape$|^he_context_set_eval_shape$|^he_ntt_tables_psi$|"
-                    r"_probe$|^he_butterfly_apply$|^he_primes_generate$|^he_ntt_plan_(fwd|inv)$")
+                    r"_probe$|^he_butterfly_apply$|^he_primes_generate$|^he_ntt_plan_(fwd|inv)$|_noalloc$")
 
 
 def _declarations():

@@ -61,3 +61,35 @@ def test_noalloc_rejects_oversized_requests():
                                               level, None)
     assert status == he.HE_EINVAL
     assert "built-in" in he.last_error()
+
+
+def test_noalloc_near_capacity_takes_the_fused_modup():
+    """Five pairs at N = 2^14, level 6 (seven data primes) fill all but
+    393 216 bytes of the built-in buffer, less than one ciphertext's expanded
+    mod-up group, so the fused mod-up branch runs. Twice in a row, the output
+    equals the scratch-taking entry point given a buffer of the same size."""
+    N = 16384
+    data, P = he.chain_primes(N, [60] + [50] * 6, 60)
+    ctx = he.Context(N, data, P)
+    r = Rng(98)
+    evk = np.stack([np.stack([r.uniform_limbs(data + [P], N) for _ in range(2)]) for _ in range(len(data))])
+    key = he.RelinKey(ctx, evk)
+    level, count = 6, 5
+    need = (3 * (level + 1) + 4) * N * 8 * count
+    group = (level + 2) * (level + 1) * N * 8
+    assert need <= he.NOALLOC_SCRATCH_BYTES < need + group
+    lib = he.load()
+    stream = torch.cuda.current_stream().cuda_stream
+    for call in range(2):
+        ca = np.stack([np.stack([r.uniform_limbs(data, N) for _ in range(2)]) for _ in range(count)])
+        cb = np.stack([np.stack([r.uniform_limbs(data, N) for _ in range(2)]) for _ in range(count)])
+        da, db = dev(ca), dev(cb)
+        ref = empty(count, 2, level, N)
+        he.mul_relin_rescale(ref, da, db, count, key, ctx, level, empty(he.NOALLOC_SCRATCH_BYTES // 8))
+        got = empty(count, 2, level, N)
+        got.fill_(-1)
+        status = lib.he_mul_relin_rescale_noalloc(ctypes.c_void_p(got.data_ptr()), ctypes.c_void_p(da.data_ptr()),
+                                                  ctypes.c_void_p(db.data_ptr()), count, key.handle, ctx.handle,
+                                                  level, ctypes.c_void_p(stream))
+        assert status == he.HE_OK, he.last_error()
+        assert np.array_equal(host(got), host(ref)), f"call {call}"
