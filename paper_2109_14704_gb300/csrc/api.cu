@@ -381,13 +381,19 @@ extern "C" he_status he_ntt_set_shape(uint32_t N, uint32_t direction, uint32_t l
 }
 
 // One launch of a batch of limb transforms in the shape set for the degree.
-static he_status ntt_launch(const he::NttLaunch &a, int log_n, bool inv, cudaStream_t stream)
+static he_status ntt_launch(const he::NttLaunch &a0, int log_n, bool inv, cudaStream_t stream)
 {
     const he::DegreeOps *ops = he::degree_ops(log_n);
     const int lb = g_shape_b[inv][log_n].load(), le = g_shape_e[inv][log_n].load();
+    he::NttLaunch a = a0;
+    const u32 resident = (u32)std::max(ops->max_clusters(lb, le, inv), 1);
+#ifndef HE_NO_L2_PREFETCH
+    a.prefetch = a.items > resident ? resident : 0;   // persistent form: any non-zero value
+#else
+    a.prefetch = 0;
+#endif
     if (g_shape_persistent[inv][log_n].load()) {
-        const u32 clusters = std::min<u32>(a.items, (u32)std::max(ops->max_clusters(lb, le, inv), 1));
-        HE_CUDA(ops->ntt_persistent(a, lb, le, inv, clusters, stream));
+        HE_CUDA(ops->ntt_persistent(a, lb, le, inv, std::min<u32>(a.items, resident), stream));
     } else {
         HE_CUDA(ops->ntt(a, lb, le, inv, stream));
     }

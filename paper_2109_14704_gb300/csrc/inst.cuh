@@ -72,8 +72,19 @@ struct ShapeOps {
         return launch_k(k_negacyclic<LOG_B, LOG_C, LOG_E>, a.items * Sh::C, Sh::T, 2 * Sh::SMEM_BYTES, Sh::C, s, a);
     }
 
+    // Co-resident clusters of the transform (the persistent kernel has the
+    // plain kernel's resources), queried once per process.
     template <bool INV>
     static int max_clusters()
+    {
+        static std::once_flag once;
+        static int n = 0;
+        std::call_once(once, [] { n = query_max_clusters<INV>(); });
+        return n;
+    }
+
+    template <bool INV>
+    static int query_max_clusters()
     {
         static std::once_flag f;
         static cudaError_t e = cudaSuccess;

@@ -64,7 +64,22 @@ __device__ __forceinline__ void resolve_item(const NttLaunch &a, u32 item, u64 *
     }
 }
 
-// One cluster per limb.
+// Ask L2 for this CTA's block (B words at m B) of limb `item` of the batch,
+// if it exists: one bulk prefetch issued by one thread, no registers held
+// and nothing waited for. Limbs read later by other clusters then come from
+// L2 instead of HBM, which hides the first-stage load latency.
+template <class Sh>
+__device__ __forceinline__ void prefetch_limb_block(const NttLaunch &a, u32 item, u32 m)
+{
+    if (threadIdx.x != 0 || item >= a.items) return;
+    const u64 *p = a.jobs ? a.jobs[item].data : a.base + (size_t)item * Sh::N;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p + (size_t)m * Sh::B), "r"(Sh::B * 8u)
+                 : "memory");
+}
+
+// One cluster per limb. With a.prefetch = the number of co-resident
+// clusters, limb item + a.prefetch is the one a cluster started about one
+// limb-time from now will take.
 template <int LOG_B, int LOG_C, int LOG_E, bool INV>
 __global__ void __launch_bounds__(NttShape<LOG_B, LOG_C, LOG_E>::T, NttShape<LOG_B, LOG_C, LOG_E>::MIN_CTAS)
 k_ntt(NttLaunch a)
@@ -72,10 +87,12 @@ k_ntt(NttLaunch a)
     using Sh = NttShape<LOG_B, LOG_C, LOG_E>;
     extern __shared__ __align__(16) u64 smem[];
     const u32 m = (LOG_C > 0) ? cluster_ctarank() : 0u;
+    const u32 item = blockIdx.x >> LOG_C;
+    if (a.prefetch) prefetch_limb_block<Sh>(a, item + a.prefetch, m);
     u64 *data;
     const ulonglong2 *tw;
     const PrimeConst *pcp;
-    resolve_item<Sh, INV>(a, blockIdx.x >> LOG_C, data, tw, pcp);
+    resolve_item<Sh, INV>(a, item, data, tw, pcp);
     const PrimeConst pc = *pcp;
     ntt_limb<Sh, INV>(smem, m, 0, data, tw, pc);
 }
@@ -94,6 +111,7 @@ k_ntt_persistent(NttLaunch a)
     for (u32 item = blockIdx.x >> LOG_C; item < a.items; item += clusters) {
         if (!first) ntt_barrier<Sh>();
         first = false;
+        if (a.prefetch) prefetch_limb_block<Sh>(a, item + clusters, m);   // this cluster's next limb
         u64 *data;
         const ulonglong2 *tw;
         const PrimeConst *pcp;

@@ -26,7 +26,7 @@ struct NttLaunch {
     u32 limbs;
     u32 first_prime;
     u32 items;
-    u32 pad;
+    u32 prefetch;               // > 0: each cluster asks L2 for the limb this many items ahead
     const ulonglong2 *tw_fwd;   // [prime][N]
     const ulonglong2 *tw_inv;
     const PrimeConst *pc;       // [prime]

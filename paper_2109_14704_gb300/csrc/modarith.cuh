@@ -146,6 +146,26 @@ __device__ __forceinline__ u64 reduce_from_fwd_range(u64 x, const PrimeConst &c)
     return reduce_once(x, c.p);
 }
 
+// Last forward stage with canonical outputs: for x, y in [0, 8p + 2^32),
+// x' = x + W y mod p and y' = x - W y mod p, both in [0, p). x goes to
+// [0, p) by the four conditional subtractions above and T = W y mod p from
+// [0, 4p) by two; the sum then needs one more and the difference a
+// sign-tested correction (eight conditional steps for the pair, against four
+// for each of the two lazy outputs).
+__device__ __forceinline__ void ct_butterfly_canon(u64 &x, u64 &y, u64 w, u64 w_sh, const PrimeConst &c)
+{
+#ifdef HE_BUTTERFLY_CXX
+    u64 T = mul_shoup_lazy4(y, w, w_sh, c.neg_p);
+#else
+    u64 T = mul_shoup_lazy4_asm(y, w, w_sh, c.neg_p);
+#endif
+    const u64 X = reduce_from_fwd_range(x, c);
+    T = reduce_once(reduce_once(T, c.two_p), c.p);
+    x = reduce_once(X + T, c.p);
+    y = sub_mod(X, T, c.p);
+}
+
+
 // Inverse (Gentleman-Sande) butterfly on [0, 4p):
 // x, y -> x + y, (x - y) W^-1 (mod p), both in [0, 4p): x + y < 8p reduces
 // exactly once by 4p; x - y + 4p lies in (0, 8p) and its lazy Shoup product

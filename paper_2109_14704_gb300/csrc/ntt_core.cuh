@@ -107,6 +107,18 @@ __device__ __forceinline__ u64 ld_cluster(u32 addr)
 // own 64-bit address computation per access.
 __device__ __forceinline__ ulonglong2 ld_tw(const ulonglong2 *tw, int idx) { return __ldg(tw + idx); }
 
+// Two consecutive twiddle pairs (idx even, so 32-byte aligned: tables start
+// 256-byte aligned and hold N pairs per prime) in one 256-bit load. Half the
+// load instructions of two 128-bit loads, which measured clearly faster:
+// the per-stage twiddle loads, not their latency, are what the transform's
+// local rounds pay for beyond the butterflies.
+__device__ __forceinline__ void ld_tw2(const ulonglong2 *tw, int idx, ulonglong2 &a, ulonglong2 &b)
+{
+    asm("ld.global.nc.v4.u64 {%0, %1, %2, %3}, [%4];"
+        : "=l"(a.x), "=l"(a.y), "=l"(b.x), "=l"(b.y)
+        : "l"(tw + idx));
+}
+
 template <int LOG_B_, int LOG_C_, int LOG_E_ = 4>
 struct NttShape {
     static constexpr int LOG_B = LOG_B_;
@@ -158,6 +170,35 @@ struct RoundOf {
     static constexpr int LOG_TL = Sh::LOG_B - S0 - R;
     static constexpr u32 TL = 1u << LOG_TL;
 };
+
+// Threads that exchange words between round RI and round RI + 1 (in either
+// direction): a group of round RI, i.e. positions g 2^(LOG_TL + R) + k +
+// u TL for all k < TL and u, is held by TL / SUB consecutive threads in round
+// RI, and every group of round RI + 1 lies inside one group of round RI. So
+// the exchange needs no more than those threads to meet: the whole CTA, a
+// named barrier of 64 or 128 threads, or the warp. (Each thread only ever
+// overwrites the shared-memory words it read itself in the previous
+// exchange, so there is no write-after-read hazard across groups.)
+template <class Sh, int RI>
+struct RoundLink {
+    using Rd = RoundOf<Sh, RI>;
+    static constexpr u32 THREADS = Rd::TL / Rd::SUB;
+    static_assert(THREADS >= 1 && (Sh::T % (THREADS < 32 ? 32 : THREADS)) == 0, "groups tile the CTA");
+    static_assert(THREADS <= 32 || THREADS >= Sh::T || Sh::T / THREADS <= 15, "named barrier ids 1..15");
+};
+
+template <class Sh, int RI>
+__device__ __forceinline__ void round_link_sync(u32 tid)
+{
+    constexpr u32 G = RoundLink<Sh, RI>::THREADS;
+    if constexpr (G >= Sh::T) {
+        __syncthreads();
+    } else if constexpr (G <= 32) {
+        __syncwarp();
+    } else {
+        asm volatile("bar.sync %0, %1;" ::"r"(1u + tid / G), "n"(G) : "memory");
+    }
+}
 
 // Block-local position of element u of subgroup i of this thread in a round.
 template <class Rd>
@@ -231,7 +272,9 @@ __device__ __forceinline__ void round_store_smem(const u64 (&x)[Sh::E], u64 *s, 
 
 // ---------------------------------------------------------------- forward
 
-template <class Sh, class Rd, int q>
+// CANON_OUT: this is the transform's last stage and its outputs must be
+// canonical (ct_butterfly_canon); otherwise the lazy butterfly.
+template <class Sh, class Rd, int q, bool CANON_OUT>
 __device__ __forceinline__ void fwd_stage(u64 (&x)[Sh::E], u32 tid, u32 m, const ulonglong2 *tw,
                                           const PrimeConst &pc)
 {
@@ -240,26 +283,36 @@ __device__ __forceinline__ void fwd_stage(u64 (&x)[Sh::E], u32 tid, u32 m, const
 #pragma unroll
     for (int i = 0; i < Rd::SUB; i++) {
         const u32 G = round_group_base<Sh, Rd>(tid, i, m);
+        ulonglong2 ws[1 << q];
+        if constexpr (q == 0) {
+            ws[0] = ld_tw(tw, (1 << S) + (int)G);
+        } else {
+#pragma unroll
+            for (int grp = 0; grp < (1 << q); grp += 2) ld_tw2(tw, (1 << S) + (int)G * (1 << q) + grp, ws[grp], ws[grp + 1]);
+        }
 #pragma unroll
         for (int grp = 0; grp < (1 << q); grp++) {
-            const ulonglong2 w = ld_tw(tw, (1 << S) + (int)G * (1 << q) + grp);
+            const ulonglong2 w = ws[grp];
 #pragma unroll
             for (int v = 0; v < half; v++) {
                 const int u = grp * 2 * half + v;
-                ct_butterfly(x[i * (1 << Rd::R) + u], x[i * (1 << Rd::R) + u + half], w.x, w.y, pc);
+                if constexpr (CANON_OUT)
+                    ct_butterfly_canon(x[i * (1 << Rd::R) + u], x[i * (1 << Rd::R) + u + half], w.x, w.y, pc);
+                else
+                    ct_butterfly(x[i * (1 << Rd::R) + u], x[i * (1 << Rd::R) + u + half], w.x, w.y, pc);
             }
         }
     }
 }
 
-template <class Sh, class Rd, int... Q>
+template <class Sh, class Rd, bool CANON_LAST, int... Q>
 __device__ __forceinline__ void fwd_round_stages(u64 (&x)[Sh::E], u32 tid, u32 m, const ulonglong2 *tw,
                                                  const PrimeConst &pc, std::integer_sequence<int, Q...>)
 {
-    (fwd_stage<Sh, Rd, Q>(x, tid, m, tw, pc), ...);
+    (fwd_stage<Sh, Rd, Q, CANON_LAST && Q == Rd::R - 1>(x, tid, m, tw, pc), ...);
 }
 
-template <class Sh, int RI>
+template <class Sh, int RI, bool CANON>
 __device__ __forceinline__ void fwd_round(u64 (&x)[Sh::E], u64 *s, u32 tid, u32 m, const ulonglong2 *tw,
                                           const PrimeConst &pc)
 {
@@ -268,17 +321,18 @@ __device__ __forceinline__ void fwd_round(u64 (&x)[Sh::E], u64 *s, u32 tid, u32 
         // pull form: the peers have pulled their words out of this block
         if constexpr (RI == 1 && Sh::LOG_C > 0 && Sh::FWD_PULL) cluster_sync_war();
         round_store_smem<Sh, RoundOf<Sh, RI - 1>>(x, s, tid);
-        __syncthreads();
+        round_link_sync<Sh, RI - 1>(tid);
         round_load_smem<Sh, Rd>(x, s, tid);
     }
-    fwd_round_stages<Sh, Rd>(x, tid, m, tw, pc, std::make_integer_sequence<int, Rd::R>{});
+    fwd_round_stages<Sh, Rd, CANON && RI == Sh::NROUND - 1>(x, tid, m, tw, pc,
+                                                            std::make_integer_sequence<int, Rd::R>{});
 }
 
-template <class Sh, int... RI>
+template <class Sh, bool CANON, int... RI>
 __device__ __forceinline__ void fwd_rounds(u64 (&x)[Sh::E], u64 *s, u32 tid, u32 m, const ulonglong2 *tw,
                                            const PrimeConst &pc, std::integer_sequence<int, RI...>)
 {
-    (fwd_round<Sh, RI>(x, s, tid, m, tw, pc), ...);
+    (fwd_round<Sh, RI, CANON>(x, s, tid, m, tw, pc), ...);
 }
 
 // Cross-CTA stages of the forward transform: load columns, radix-C network,
@@ -363,16 +417,13 @@ __device__ __forceinline__ void ntt_fwd_block(u64 *s, u32 m, u32 rbase, const ul
 #pragma unroll
             for (int u = 0; u < (1 << R0::R); u++) x[i * (1 << R0::R) + u] = load(round_pos<R0>(tid, i, u));
     }
-    fwd_rounds<Sh>(x, s, tid, m, tw, pc, std::make_integer_sequence<int, Sh::NROUND>{});
+    fwd_rounds<Sh, CANON>(x, s, tid, m, tw, pc, std::make_integer_sequence<int, Sh::NROUND>{});
     using RL = RoundOf<Sh, Sh::NROUND - 1>;
 #pragma unroll
     for (int i = 0; i < RL::SUB; i++)
 #pragma unroll
-        for (int u = 0; u < (1 << RL::R); u++) {
-            const u64 v = CANON ? reduce_from_fwd_range(x[i * (1 << RL::R) + u], pc) : x[i * (1 << RL::R) + u];
-            x[i * (1 << RL::R) + u] = v;
-            store((int)(m * Sh::B) + round_pos<RL>(tid, i, u), v);
-        }
+        for (int u = 0; u < (1 << RL::R); u++)
+            store((int)(m * Sh::B) + round_pos<RL>(tid, i, u), x[i * (1 << RL::R) + u]);
 }
 
 // Position (within the limb) of element e of x[] after ntt_fwd_block, and of
@@ -406,6 +457,16 @@ __device__ __forceinline__ void inv_stage(u64 (&x)[Sh::E], u32 tid, u32 m, const
 #pragma unroll
     for (int i = 0; i < Rd::SUB; i++) {
         const u32 G = round_group_base<Sh, Rd>(tid, i, m);
+        ulonglong2 ws[1 << q];
+        if constexpr (S > 0) {
+            if constexpr (q == 0) {
+                ws[0] = ld_tw(tw, (1 << S) + (int)G);
+            } else {
+#pragma unroll
+                for (int grp = 0; grp < (1 << q); grp += 2)
+                    ld_tw2(tw, (1 << S) + (int)G * (1 << q) + grp, ws[grp], ws[grp + 1]);
+            }
+        }
 #pragma unroll
         for (int grp = 0; grp < (1 << q); grp++) {
             if constexpr (S == 0) {
@@ -415,7 +476,7 @@ __device__ __forceinline__ void inv_stage(u64 (&x)[Sh::E], u32 tid, u32 m, const
                     gs_last(x[i * (1 << Rd::R) + u], x[i * (1 << Rd::R) + u + half], pc);
                 }
             } else {
-                const ulonglong2 w = ld_tw(tw, (1 << S) + (int)G * (1 << q) + grp);
+                const ulonglong2 w = ws[grp];
 #pragma unroll
                 for (int v = 0; v < half; v++) {
                     const int u = grp * 2 * half + v;
@@ -442,7 +503,7 @@ __device__ __forceinline__ void inv_round(u64 (&x)[Sh::E], u64 *s, u32 tid, u32 
     using Rd = RoundOf<Sh, RI>;
     if constexpr (RI < Sh::NROUND - 1) {
         round_store_smem<Sh, RoundOf<Sh, RI + 1>>(x, s, tid);
-        __syncthreads();
+        round_link_sync<Sh, RI>(tid);
         round_load_smem<Sh, Rd>(x, s, tid);
     }
     inv_round_stages<Sh, Rd>(x, tid, m, tw, pc, std::make_integer_sequence<int, Rd::R>{});

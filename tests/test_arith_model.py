@@ -9,6 +9,8 @@ inputs and primes from 2^30 to just below 2^60:
   integer W Y - Q' p in [0, 4p);
 * the forward butterfly keeps x, y in [0, 8p + 2^32) with a high-word test;
 * four conditional subtractions bring [0, 8p + 2^32) to [0, p);
+* the forward transform's last butterfly, which reduces its input and the
+  lazy product before the sum and the difference, gives canonical outputs;
 * the inverse butterfly keeps [0, 4p);
 * Barrett with one correction reduces any z < 2 p^2;
 * the sign of the 64-bit difference decides x >= m for x, m < 2^63."""
@@ -45,6 +47,18 @@ def ct_butterfly(x, y, w, w_sh, p):
 def reduce_once(x, m):
     d = (x - m) & M64
     return x if d >= 1 << 63 else d
+
+
+def sub_mod(a, b, p):
+    d = (a - b) & M64
+    return (d + p) & M64 if d >= 1 << 63 else d
+
+
+def ct_butterfly_canon(x, y, w, w_sh, p):
+    T = lazy4(y, w, w_sh, p)
+    X = reduce_from_fwd_range(x, p)
+    T = reduce_once(reduce_once(T, 2 * p), p)
+    return reduce_once(X + T, p), sub_mod(X, T, p)
 
 
 def reduce_from_fwd_range(x, p):
@@ -102,6 +116,18 @@ def test_forward_butterfly_range(p):
             assert x2 < top and y2 < top
             assert (x2 - (x + w * y)) % p == 0 and (y2 - (x - w * y)) % p == 0
             assert reduce_from_fwd_range(x2, p) == (x + w * y) % p
+
+
+@pytest.mark.parametrize("p", PRIMES)
+def test_forward_last_butterfly_canonical(p):
+    rnd = random.Random(p + 5)
+    top = 8 * p + (1 << 32)
+    for w in (1, p - 1, rnd.randrange(p)):
+        w_sh = shoup_pre(w, p)
+        xs, ys = _cases(p, rnd, top), _cases(p, rnd, top)
+        for x, y in zip(xs + xs[::-1], ys + ys):
+            x2, y2 = ct_butterfly_canon(x, y, w, w_sh, p)
+            assert x2 == (x + w * y) % p and y2 == (x - w * y) % p
 
 
 @pytest.mark.parametrize("p", PRIMES)
