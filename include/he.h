@@ -354,6 +354,43 @@ he_status he_mul_relin_rescale_batch(const he_mrr_job *jobs_host, uint32_t n_job
                                      const he_context *ctx, void *scratch, size_t scratch_bytes,
                                      he_stream_t stream);
 
+/* ---- multi-degree batches (Sec. III-B batching over instances) ---------------- */
+
+/* One job of a multi-degree MulLinRS batch: `count` ciphertext pairs at
+ * `level` under their own context and relinearization key (ct_a, ct_b:
+ * count x 2 x (level + 1) x N words, NTT domain; ct_out: count x 2 x level
+ * x N words; N is the context's degree). */
+typedef struct he_mrr_multi_job {
+    uint64_t *ct_out;
+    const uint64_t *ct_a;
+    const uint64_t *ct_b;
+    uint32_t count;
+    uint32_t level;
+    const he_context *ctx;
+    const he_relin_key *key;
+} he_mrr_multi_job;
+
+/* Device scratch of he_mul_relin_rescale_multi for these jobs (host array):
+ * per job (level + 3)^2 x N x count x 8 bytes, N its context's degree.
+ * 0 for invalid jobs. */
+size_t he_mul_relin_rescale_multi_scratch_bytes(const he_mrr_multi_job *jobs_host, uint32_t n_jobs);
+
+/* MulLinRS (Sec. IV-C) of jobs of DIFFERENT degrees, each with exactly the
+ * result he_mul_relin_rescale gives for it alone, with ONE launch per
+ * pipeline stage for all of them (digit INTT, mod-up transforms, key
+ * multiply-accumulate, the special prime's INTT, and the three mod-down /
+ * rescale kernels; Sec. II-A Mul, Relin, RS). Each job names its context
+ * (degree N in [2^12, 2^15], HE_EUNSUPPORTED otherwise) and a key of that
+ * context; levels and counts may differ; count-0 jobs are skipped; at most
+ * 16 jobs per pass, more take further passes. The transform stages run
+ * clusters of 8 CTAs of 2^12 words, each holding 8 >> c items of a job of
+ * degree 2^(12 + c). Outputs must not overlap inputs or each other.
+ * scratch: device, 16-byte aligned, he_mul_relin_rescale_multi_scratch_bytes.
+ * HE_EINVAL for a bad context, key, level (< 1 or beyond the chain),
+ * pointer, short scratch, or a batch beyond the launch limits. */
+he_status he_mul_relin_rescale_multi(const he_mrr_multi_job *jobs_host, uint32_t n_jobs, void *scratch,
+                                     size_t scratch_bytes, he_stream_t stream);
+
 /* ---- encoding and decoding (Sec. II-A Encode / Decode) ------------------------ */
 
 /* Slot vectors are n = N/2 complex numbers, stored as interleaved FP64

@@ -970,6 +970,8 @@ static he_status mrr_jobs_pass(const he_mrr_job *jobs, u32 n_jobs, const he_reli
         w = E.mx + (size_t)c * (n + 1) * n * ctx->N;
         E.plift = pl;
         pl += (size_t)c * 2 * ctx->N;
+        E.evk = key->d_evk;
+        E.ctx = dev_ctx(ctx);
         const u64 items[he::JS_COUNT] = {(u64)c * n, (u64)c * (n + 1) * n,
                                          (u64)(c + he::MAC_CTS - 1) / he::MAC_CTS * (n + 1) * (ctx->N / 2), 2ull * c,
                                          2ull * c * (n - 1)};
@@ -1773,6 +1775,111 @@ extern "C" he_status he_ntt_host(const uint64_t *in_host, uint64_t *out_host, ui
         if (e != cudaSuccess && status == HE_OK) status = cuda_fail(e, "join the pipeline streams");
     }
     return status;
+}
+
+// ---- multi-degree MulLinRS batches (one launch per pipeline stage) -------
+
+static he_status check_multi_jobs(const he_mrr_multi_job *jobs, uint32_t n_jobs, bool pointers)
+{
+    if (n_jobs && !jobs) return fail(HE_EINVAL, "jobs_host is NULL");
+    for (u32 i = 0; i < n_jobs; i++) {
+        const he_mrr_multi_job &J = jobs[i];
+        if (!J.ctx) return fail(HE_EINVAL, "job %u: context is NULL", i);
+        if (J.ctx->log_n < 12 || J.ctx->log_n > 15)
+            return fail(HE_EUNSUPPORTED, "job %u: degree %u outside [2^12, 2^15]", i, J.ctx->N);
+        if (he_status s = check_level(J.ctx, J.level, true)) return s;
+        if (J.count > 4096) return fail(HE_EINVAL, "job %u: more than 4096 ciphertext pairs", i);
+        if (!J.count || !pointers) continue;
+        if (!J.key || J.key->ctx != J.ctx) return fail(HE_EINVAL, "job %u: key is NULL or of another context", i);
+        if (he_status s = check_ptr(J.ct_out, "ct_out")) return s;
+        if (he_status s = check_ptr(J.ct_a, "ct_a")) return s;
+        if (he_status s = check_ptr(J.ct_b, "ct_b")) return s;
+    }
+    return HE_OK;
+}
+
+extern "C" size_t he_mul_relin_rescale_multi_scratch_bytes(const he_mrr_multi_job *jobs_host, uint32_t n_jobs)
+{
+    if (check_multi_jobs(jobs_host, n_jobs, false) != HE_OK) return 0;
+    size_t words = 0;
+    for (u32 i = 0; i < n_jobs; i++) words += mrr_job_words(jobs_host[i].ctx, jobs_host[i].level + 1, jobs_host[i].count);
+    return words * 8;
+}
+
+// One pass over up to kMaxJobs jobs whose scratch starts at w. Per job:
+// c2 [count][n][N], accq [count][2][n][N], lift2 [count][2][N], the
+// expanded mod-up buffer [count][n + 1][n][N], plift [count][2][N].
+static he_status mrr_multi_pass(const he_mrr_multi_job *jobs, u32 n_jobs, u64 *w, cudaStream_t s)
+{
+    he::JobTable t = {};
+    u64 tot[he::JS_COUNT] = {};
+    for (u32 i = 0; i < n_jobs; i++) {
+        const he_mrr_multi_job &J = jobs[i];
+        const he_context *ctx = J.ctx;
+        const u32 n = J.level + 1, c = J.count;
+        const size_t N = ctx->N;
+        he::EvalJob &E = t.job[t.n_jobs++];
+        E.ct_a = J.ct_a;
+        E.ct_b = J.ct_b;
+        E.out = J.ct_out;
+        E.n = n;
+        E.count = c;
+        E.evk = J.key->d_evk;
+        E.ctx = dev_ctx(ctx);
+        E.c2 = w;
+        E.accq = E.c2 + (size_t)c * n * N;
+        E.lift2 = E.accq + (size_t)c * 2 * n * N;
+        E.mx = E.lift2 + (size_t)c * 2 * N;
+        E.plift = E.mx + (size_t)c * (n + 1) * n * N;
+        w = E.plift + (size_t)c * 2 * N;
+        const u64 per = 8u >> (ctx->log_n - 12);     // items side by side in one cluster
+        auto units = [&](u64 items) { return (items + per - 1) / per; };
+        u64 cnt[he::JS_COUNT] = {};
+        cnt[he::JS_DIGITS] = units((u64)c * n);
+        cnt[he::JS_EXPAND] = units((u64)c * n * n);
+        cnt[he::JS_MAC] = (u64)(c + he::MAC_CTS - 1) / he::MAC_CTS * (n + 1) * (N / 2);
+        cnt[he::JS_LAST] = units(2ull * c);
+        cnt[he::JS_REST] = units(2ull * c * (n - 1));
+        cnt[he::JS_PLIFT] = units(2ull * c);
+        for (int st = 0; st < he::JS_COUNT; st++) {
+            if (tot[st] + cnt[st] > 0x0fffffffull) return fail(HE_EINVAL, "batch too large");
+            E.begin[st] = (u32)tot[st];
+            tot[st] += cnt[st];
+        }
+    }
+    he::EvalArgs a = {};
+    a.evk = t.job[0].evk;   // every stage binds its job's own context and key
+    a.ctx = t.job[0].ctx;
+    a.n = t.job[0].n;
+    HE_CUDA(he::launch_mrr_multi(he::MS_DIGITS, a, t, (u32)tot[he::JS_DIGITS], s));
+    HE_CUDA(he::launch_mrr_multi(he::MS_EXPAND, a, t, (u32)tot[he::JS_EXPAND], s));
+    he::k_ks_mac<true><<<stream_grid(tot[he::JS_MAC], 256), 256, 0, s>>>(a, 0, (u32)tot[he::JS_MAC], t);
+    HE_CUDA(cudaGetLastError());
+    HE_CUDA(he::launch_mrr_multi(he::MS_PLIFT, a, t, (u32)tot[he::JS_PLIFT], s));
+    HE_CUDA(he::launch_mrr_multi(he::MS_LAST, a, t, (u32)tot[he::JS_LAST], s));
+    HE_CUDA(he::launch_mrr_multi(he::MS_REST_Z, a, t, (u32)tot[he::JS_REST], s));
+    HE_CUDA(he::launch_mrr_multi(he::MS_REST_OUT, a, t, (u32)tot[he::JS_REST], s));
+    return HE_OK;
+}
+
+extern "C" he_status he_mul_relin_rescale_multi(const he_mrr_multi_job *jobs_host, uint32_t n_jobs, void *scratch,
+                                                size_t scratch_bytes, he_stream_t stream)
+{
+    if (he_status s = check_multi_jobs(jobs_host, n_jobs, true)) return s;
+    std::vector<he_mrr_multi_job> live;
+    for (u32 i = 0; i < n_jobs; i++)
+        if (jobs_host[i].count) live.push_back(jobs_host[i]);
+    if (live.empty()) return HE_OK;
+    if (he_status s = check_ptr(scratch, "scratch")) return s;
+    if (scratch_bytes < he_mul_relin_rescale_multi_scratch_bytes(live.data(), (u32)live.size()))
+        return fail(HE_EINVAL, "scratch too small");
+    u64 *w = (u64 *)scratch;
+    for (size_t i = 0; i < live.size(); i += he::kMaxJobs) {
+        const u32 m = (u32)std::min<size_t>(he::kMaxJobs, live.size() - i);
+        if (he_status r = mrr_multi_pass(live.data() + i, m, w, (cudaStream_t)stream)) return r;
+        for (u32 k = 0; k < m; k++) w += mrr_job_words(live[i + k].ctx, live[i + k].level + 1, live[i + k].count);
+    }
+    return HE_OK;
 }
 
 // ------------------------------------------- allocation-free MulLinRS

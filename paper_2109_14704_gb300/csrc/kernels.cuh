@@ -591,6 +591,8 @@ __device__ __forceinline__ u32 bind_job(EvalArgs &a, const JobTable &t, int S, u
     a.plift = J.plift;
     a.lift2 = J.lift2;
     a.mx = J.mx;
+    a.evk = J.evk;
+    a.ctx = J.ctx;
     a.n = J.n;
     a.count = J.count;
     a.c_first = 0;
@@ -640,16 +642,18 @@ __device__ __forceinline__ DSource dsource(const EvalArgs &a, u32 c)
     return s;
 }
 
-template <int LOG_B, int LOG_C, int LOG_E, bool JOBS = false>
-__global__ void __launch_bounds__(NttShape<LOG_B, LOG_C, LOG_E>::T, NttShape<LOG_B, LOG_C, LOG_E>::MIN_CTAS)
-k_ks_digits(EvalArgs a0, JobsArg<JOBS> tab)
+// Stage bodies of the MulLinRS pipeline for one item, shared by the per-
+// degree kernels (one cluster per item: m = cluster rank, rbase = 0, valid)
+// and the multi-degree kernels (multi.cu: sub-clusters of 2^LOG_C CTAs at
+// cluster ranks rbase .. rbase + 2^LOG_C - 1; a sub-cluster without an item
+// of its own recomputes a valid one with every store switched off, so that
+// all CTAs of the cluster pass the same cluster barriers).
+
+// Digit INTT: c2[c][j] = INTT_{q_j}(d2[c][j]), item = c n + j.
+template <class Sh>
+__device__ __forceinline__ void ks_digits_body(const EvalArgs &a, u32 item, u32 m, u32 rbase, bool valid)
 {
-    EvalArgs a = a0;
-    using Sh = NttShape<LOG_B, LOG_C, LOG_E>;
     extern __shared__ __align__(16) u64 smem[];
-    const u32 m = (LOG_C > 0) ? cluster_ctarank() : 0u;
-    u32 item = blockIdx.x >> LOG_C;
-    if constexpr (JOBS) item = bind_job(a, tab, JS_DIGITS, item);
     const u32 c = item / a.n, j = item % a.n;
     const PrimeConst pc = a.ctx.pc[j];
     const DSource ds = dsource(a, c);
@@ -664,8 +668,22 @@ k_ks_digits(EvalArgs a0, JobsArg<JOBS> tab)
         x[e + 1] = v.y;
     }
     auto nold = [&](u32) -> u64 { return 0; };
-    auto st = [&](u32 P, u64 v) { out[P] = v; };
-    ntt_inv_block<Sh, true>(smem, m, 0, a.ctx.tw_inv + (size_t)j * Sh::N, pc, nold, st, x);
+    auto st = [&](u32 P, u64 v) {
+        if (valid) out[P] = v;
+    };
+    ntt_inv_block<Sh, true>(smem, m, rbase, a.ctx.tw_inv + (size_t)j * Sh::N, pc, nold, st, x);
+}
+
+template <int LOG_B, int LOG_C, int LOG_E, bool JOBS = false>
+__global__ void __launch_bounds__(NttShape<LOG_B, LOG_C, LOG_E>::T, NttShape<LOG_B, LOG_C, LOG_E>::MIN_CTAS)
+k_ks_digits(EvalArgs a0, JobsArg<JOBS> tab)
+{
+    EvalArgs a = a0;
+    using Sh = NttShape<LOG_B, LOG_C, LOG_E>;
+    const u32 m = (LOG_C > 0) ? cluster_ctarank() : 0u;
+    u32 item = blockIdx.x >> LOG_C;
+    if constexpr (JOBS) item = bind_job(a, tab, JS_DIGITS, item);
+    ks_digits_body<Sh>(a, item, m, 0, true);
 }
 
 template <int LOG_B, int LOG_C, int LOG_E>
@@ -757,24 +775,18 @@ k_ks_modup(EvalArgs a)
 // accumulating cluster; k_ks_mac then accumulates them with the key.
 // Clusters of the diagonal (j = t) exit at once: there the digit is already
 // in the NTT domain.
-template <int LOG_B, int LOG_C, int LOG_E, bool JOBS = false>
-__global__ void __launch_bounds__(NttShape<LOG_B, LOG_C, LOG_E>::T, NttShape<LOG_B, LOG_C, LOG_E>::MIN_CTAS)
-k_ks_expand(EvalArgs a0, JobsArg<JOBS> tab)
+// One transform of the expanded mod-up: X[g][t][j] = NTT_t(c2_j mod t),
+// j != t, ciphertext c_first + g.
+template <class Sh>
+__device__ __forceinline__ void ks_expand_body(const EvalArgs &a, u32 g, u32 t, u32 j, u32 m, u32 rbase, bool valid)
 {
-    EvalArgs a = a0;
-    using Sh = NttShape<LOG_B, LOG_C, LOG_E>;
     extern __shared__ __align__(16) u64 smem[];
     const u32 tid = threadIdx.x;
-    const u32 m = (LOG_C > 0) ? cluster_ctarank() : 0u;
-    u32 item = blockIdx.x >> LOG_C;
-    if constexpr (JOBS) item = bind_job(a, tab, JS_EXPAND, item);
     const u32 n = a.n;
-    const u32 j = item % n, t = (item / n) % (n + 1), g = item / (n * (n + 1));
-    if (j == t) return;
     const u32 tp = (t == n) ? a.ctx.n_data : t;
     const PrimeConst pc = a.ctx.pc[tp];
     const u64 *src = a.c2 + ((size_t)(a.c_first + g) * n + j) * Sh::N;
-    u64 *dst = a.mx + (size_t)item * Sh::N;
+    u64 *dst = a.mx + (((size_t)g * (n + 1) + t) * n + j) * Sh::N;
     const ulonglong2 *twf = a.ctx.tw_fwd + (size_t)tp * Sh::N;
     u64 x[Sh::E];
     auto nost = [&](u32, u64) {};
@@ -782,14 +794,31 @@ k_ks_expand(EvalArgs a0, JobsArg<JOBS> tab)
     // digit c2_j < q_j goes in as it is
     if (a.ctx.pc[j].p <= (pc.four_p << 1)) {
         auto ld = [&](int P) -> u64 { return rd(src + P); };
-        ntt_fwd_block<Sh, false>(smem, m, 0, twf, pc, ld, nost, x);
+        ntt_fwd_block<Sh, false>(smem, m, rbase, twf, pc, ld, nost, x);
     } else {
         auto ld = [&](int P) -> u64 { return barrett_reduce(0, rd(src + P), pc.p, pc.mu, pc.bits); };
-        ntt_fwd_block<Sh, false>(smem, m, 0, twf, pc, ld, nost, x);
+        ntt_fwd_block<Sh, false>(smem, m, rbase, twf, pc, ld, nost, x);
     }
+    if (valid) {
 #pragma unroll
-    for (int e = 0; e < Sh::E; e += 2)
-        *reinterpret_cast<ulonglong2 *>(dst + last_pos<Sh>(m, tid, e)) = make_ulonglong2(x[e], x[e + 1]);
+        for (int e = 0; e < Sh::E; e += 2)
+            *reinterpret_cast<ulonglong2 *>(dst + last_pos<Sh>(m, tid, e)) = make_ulonglong2(x[e], x[e + 1]);
+    }
+}
+
+template <int LOG_B, int LOG_C, int LOG_E, bool JOBS = false>
+__global__ void __launch_bounds__(NttShape<LOG_B, LOG_C, LOG_E>::T, NttShape<LOG_B, LOG_C, LOG_E>::MIN_CTAS)
+k_ks_expand(EvalArgs a0, JobsArg<JOBS> tab)
+{
+    EvalArgs a = a0;
+    using Sh = NttShape<LOG_B, LOG_C, LOG_E>;
+    const u32 m = (LOG_C > 0) ? cluster_ctarank() : 0u;
+    u32 item = blockIdx.x >> LOG_C;
+    if constexpr (JOBS) item = bind_job(a, tab, JS_EXPAND, item);
+    const u32 n = a.n;
+    const u32 j = item % n, t = (item / n) % (n + 1), g = item / (n * (n + 1));
+    if (j == t) return;   // the whole cluster: there the digit is already in the NTT domain
+    ks_expand_body<Sh>(a, g, t, j, m, 0, true);
 }
 
 #ifdef HE_MISC_KERNELS
@@ -965,18 +994,13 @@ k_rs(EvalArgs a)
 }
 
 // MulLinRS, limb q_l: relin output c_k[q_l] = d_k[l] + (acc - NTT(r)) P^-1,
-// then straight into INTT_{q_l} (values stay in registers) -> lift2.
-template <int LOG_B, int LOG_C, int LOG_E, bool JOBS = false>
-__global__ void __launch_bounds__(NttShape<LOG_B, LOG_C, LOG_E>::T, NttShape<LOG_B, LOG_C, LOG_E>::EVAL_MIN_CTAS)
-k_mrr_last(EvalArgs a0, JobsArg<JOBS> tab)
+// then straight into INTT_{q_l} (values stay in registers) -> lift2;
+// item = 2 c + k.
+template <class Sh>
+__device__ __forceinline__ void mrr_last_body(const EvalArgs &a, u32 item, u32 m, u32 rbase, bool valid)
 {
-    EvalArgs a = a0;
-    using Sh = NttShape<LOG_B, LOG_C, LOG_E>;
     extern __shared__ __align__(16) u64 smem[];
     const u32 tid = threadIdx.x;
-    const u32 m = (LOG_C > 0) ? cluster_ctarank() : 0u;
-    u32 item = blockIdx.x >> LOG_C;
-    if constexpr (JOBS) item = bind_job(a, tab, JS_LAST, item);
     const u32 n = a.n, l = n - 1;
     const u32 c = item / 2, k = item % 2;
     const PrimeConst pc = a.ctx.pc[l];
@@ -987,13 +1011,27 @@ k_mrr_last(EvalArgs a0, JobsArg<JOBS> tab)
     u64 x[Sh::E];
     auto ld = [&](u32 P) -> u64 { return centred_mod(rd(y + P), half_P, cst[2], pc); };
     auto nost = [&](u32, u64) {};
-    ntt_fwd_block<Sh, false>(smem, m, 0, a.ctx.tw_fwd + (size_t)l * Sh::N, pc, ld, nost, x);
+    ntt_fwd_block<Sh, false>(smem, m, rbase, a.ctx.tw_fwd + (size_t)l * Sh::N, pc, ld, nost, x);
     const u64 *accp = a.accq + (((size_t)c * 2 + k) * n + l) * Sh::N;
     sub_scale_pairs<Sh>(x, accp, cst[0], cst[1], pc, m, tid);   // acc holds d P
     u64 *dst = a.lift2 + ((size_t)c * 2 + k) * Sh::N;
-    auto st = [&](u32 P, u64 v) { dst[P] = v; };
+    auto st = [&](u32 P, u64 v) {
+        if (valid) dst[P] = v;
+    };
     auto nold = [&](u32) -> u64 { return 0; };
-    ntt_inv_block<Sh, true>(smem, m, 0, a.ctx.tw_inv + (size_t)l * Sh::N, pc, nold, st, x);
+    ntt_inv_block<Sh, true>(smem, m, rbase, a.ctx.tw_inv + (size_t)l * Sh::N, pc, nold, st, x);
+}
+
+template <int LOG_B, int LOG_C, int LOG_E, bool JOBS = false>
+__global__ void __launch_bounds__(NttShape<LOG_B, LOG_C, LOG_E>::T, NttShape<LOG_B, LOG_C, LOG_E>::EVAL_MIN_CTAS)
+k_mrr_last(EvalArgs a0, JobsArg<JOBS> tab)
+{
+    EvalArgs a = a0;
+    using Sh = NttShape<LOG_B, LOG_C, LOG_E>;
+    const u32 m = (LOG_C > 0) ? cluster_ctarank() : 0u;
+    u32 item = blockIdx.x >> LOG_C;
+    if constexpr (JOBS) item = bind_job(a, tab, JS_LAST, item);
+    mrr_last_body<Sh>(a, item, m, 0, true);
 }
 
 // MulLinRS, limbs i < l: mod-down by P, then rescale by q_l, as two launches
@@ -1006,17 +1044,12 @@ k_mrr_last(EvalArgs a0, JobsArg<JOBS> tab)
 //                   thread rewrites only the positions it read);
 //   k_mrr_rest_out: out[c][k][i] = (z_k[i] - NTT_i([y2_k]_{q_l})) q_l^-1.
 // Both transforms are left lazy (their outputs only enter Shoup products).
-template <int LOG_B, int LOG_C, int LOG_E, bool JOBS = false>
-__global__ void __launch_bounds__(NttShape<LOG_B, LOG_C, LOG_E>::T, NttShape<LOG_B, LOG_C, LOG_E>::MIN_CTAS)
-k_mrr_rest_z(EvalArgs a0, JobsArg<JOBS> tab)
+// item = 2 l c + l k + i (ciphertext c, component k, limb i < l).
+template <class Sh>
+__device__ __forceinline__ void mrr_rest_z_body(const EvalArgs &a, u32 item, u32 m, u32 rbase, bool valid)
 {
-    EvalArgs a = a0;
-    using Sh = NttShape<LOG_B, LOG_C, LOG_E>;
     extern __shared__ __align__(16) u64 smem[];
     const u32 tid = threadIdx.x;
-    const u32 m = (LOG_C > 0) ? cluster_ctarank() : 0u;
-    u32 item = blockIdx.x >> LOG_C;
-    if constexpr (JOBS) item = bind_job(a, tab, JS_REST, item);
     const u32 n = a.n, l = n - 1;
     const u32 c = item / (2 * l), k = (item / l) % 2, i = item % l;
     const PrimeConst pc = a.ctx.pc[i];
@@ -1027,23 +1060,17 @@ k_mrr_rest_z(EvalArgs a0, JobsArg<JOBS> tab)
     u64 x[Sh::E];
     auto nost = [&](u32, u64) {};
     auto ld = [&](int P) -> u64 { return centred_mod(rd(y + P), half_P, P_mod_q, pc); };
-    ntt_fwd_block<Sh, false>(smem, m, 0, a.ctx.tw_fwd + (size_t)i * Sh::N, pc, ld, nost, x);
+    ntt_fwd_block<Sh, false>(smem, m, rbase, a.ctx.tw_fwd + (size_t)i * Sh::N, pc, ld, nost, x);
     u64 *accp = a.accq + (((size_t)c * 2 + k) * n + i) * Sh::N;
     sub_scale_pairs<Sh>(x, accp, cP[0], cP[1], pc, m, tid);
-    store_pairs<Sh>(accp, x, m, tid);
+    if (valid) store_pairs<Sh>(accp, x, m, tid);
 }
 
-template <int LOG_B, int LOG_C, int LOG_E, bool JOBS = false>
-__global__ void __launch_bounds__(NttShape<LOG_B, LOG_C, LOG_E>::T, NttShape<LOG_B, LOG_C, LOG_E>::MIN_CTAS)
-k_mrr_rest_out(EvalArgs a0, JobsArg<JOBS> tab)
+template <class Sh>
+__device__ __forceinline__ void mrr_rest_out_body(const EvalArgs &a, u32 item, u32 m, u32 rbase, bool valid)
 {
-    EvalArgs a = a0;
-    using Sh = NttShape<LOG_B, LOG_C, LOG_E>;
     extern __shared__ __align__(16) u64 smem[];
     const u32 tid = threadIdx.x;
-    const u32 m = (LOG_C > 0) ? cluster_ctarank() : 0u;
-    u32 item = blockIdx.x >> LOG_C;
-    if constexpr (JOBS) item = bind_job(a, tab, JS_REST, item);
     const u32 n = a.n, l = n - 1;
     const u32 c = item / (2 * l), k = (item / l) % 2, i = item % l;
     const PrimeConst pc = a.ctx.pc[i];
@@ -1054,11 +1081,54 @@ k_mrr_rest_out(EvalArgs a0, JobsArg<JOBS> tab)
     u64 x[Sh::E];
     auto nost = [&](u32, u64) {};
     auto ld = [&](int P) -> u64 { return centred_mod(rd(y2 + P), half_l, ql_mod_q, pc); };
-    ntt_fwd_block<Sh, false>(smem, m, 0, a.ctx.tw_fwd + (size_t)i * Sh::N, pc, ld, nost, x);
+    ntt_fwd_block<Sh, false>(smem, m, rbase, a.ctx.tw_fwd + (size_t)i * Sh::N, pc, ld, nost, x);
     const u64 *zp = a.accq + (((size_t)c * 2 + k) * n + i) * Sh::N;
     u64 *out = a.out + (((size_t)c * 2 + k) * l + i) * Sh::N;
     sub_scale_pairs<Sh>(x, zp, cl[0], cl[1], pc, m, tid);
-    store_pairs<Sh>(out, x, m, tid);
+    if (valid) store_pairs<Sh>(out, x, m, tid);
+}
+
+// Inverse transform of one special-prime accumulator row of plift in place
+// (row = 2 c + k; inputs in [0, 4P), the key multiply-accumulate's range).
+// Every load precedes the cluster barrier before the cross-CTA stages (or,
+// in one CTA, the barrier of the first round exchange) and every store
+// follows it, so the rows can be transformed in place.
+template <class Sh>
+__device__ __forceinline__ void plift_intt_body(const EvalArgs &a, u32 row, u32 m, u32 rbase, bool valid)
+{
+    extern __shared__ __align__(16) u64 smem[];
+    const u32 tp = a.ctx.n_data;
+    u64 *y = a.plift + (size_t)row * Sh::N;
+    u64 x[Sh::E];
+    auto ld = [&](u32 P) -> u64 { return rd(y + P); };
+    auto st = [&](u32 P, u64 v) {
+        if (valid) y[P] = v;
+    };
+    ntt_inv_block<Sh, false>(smem, m, rbase, a.ctx.tw_inv + (size_t)tp * Sh::N, a.ctx.pc[tp], ld, st, x);
+}
+
+template <int LOG_B, int LOG_C, int LOG_E, bool JOBS = false>
+__global__ void __launch_bounds__(NttShape<LOG_B, LOG_C, LOG_E>::T, NttShape<LOG_B, LOG_C, LOG_E>::MIN_CTAS)
+k_mrr_rest_z(EvalArgs a0, JobsArg<JOBS> tab)
+{
+    EvalArgs a = a0;
+    using Sh = NttShape<LOG_B, LOG_C, LOG_E>;
+    const u32 m = (LOG_C > 0) ? cluster_ctarank() : 0u;
+    u32 item = blockIdx.x >> LOG_C;
+    if constexpr (JOBS) item = bind_job(a, tab, JS_REST, item);
+    mrr_rest_z_body<Sh>(a, item, m, 0, true);
+}
+
+template <int LOG_B, int LOG_C, int LOG_E, bool JOBS = false>
+__global__ void __launch_bounds__(NttShape<LOG_B, LOG_C, LOG_E>::T, NttShape<LOG_B, LOG_C, LOG_E>::MIN_CTAS)
+k_mrr_rest_out(EvalArgs a0, JobsArg<JOBS> tab)
+{
+    EvalArgs a = a0;
+    using Sh = NttShape<LOG_B, LOG_C, LOG_E>;
+    const u32 m = (LOG_C > 0) ? cluster_ctarank() : 0u;
+    u32 item = blockIdx.x >> LOG_C;
+    if constexpr (JOBS) item = bind_job(a, tab, JS_REST, item);
+    mrr_rest_out_body<Sh>(a, item, m, 0, true);
 }
 
 }  // namespace he

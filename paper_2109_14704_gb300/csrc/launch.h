@@ -98,15 +98,20 @@ struct EvalArgs {
 
 // Mixed-level batches (one context): each launch of the MulLinRS pipeline
 // covers every job; job i's items in stage S start at job[i].begin[S].
-enum JobStage { JS_DIGITS = 0, JS_EXPAND, JS_MAC, JS_LAST, JS_REST, JS_COUNT };
+// Multi-degree batches (a context and key per job, degrees 2^12 .. 2^15):
+// the transform stages count units (clusters of 8 CTAs, each running 8 >> c
+// items of degree 2^(12 + c) side by side) instead of items, and the special
+// prime's inverse transforms are a stage of their own (JS_PLIFT).
+enum JobStage { JS_DIGITS = 0, JS_EXPAND, JS_MAC, JS_LAST, JS_REST, JS_PLIFT, JS_COUNT };
 constexpr u32 kMaxJobs = 16;
 struct EvalJob {
     const u64 *ct_a, *ct_b;     // [count][2][n][N]
     u64 *out;                   // [count][2][n - 1][N]
     u64 *c2, *accq, *plift, *lift2, *mx;   // the job's scratch regions
+    const ulonglong2 *evk;      // the job's key
+    DevCtx ctx;                 // the job's context
     u32 n, count;
     u32 begin[JS_COUNT];
-    u32 pad;
 };
 struct JobTable {               // passed by value (kernel parameter space)
     EvalJob job[kMaxJobs];
@@ -115,6 +120,12 @@ struct JobTable {               // passed by value (kernel parameter space)
 struct NoJobs {};
 template <bool JOBS>
 using JobsArg = typename std::conditional<JOBS, JobTable, NoJobs>::type;
+
+// Stages of the multi-degree MulLinRS pipeline (multi.cu), one launch each
+// over `units` clusters; the key multiply-accumulate between the expansion
+// and the special-prime transforms is k_ks_mac over the same job table.
+enum MultiStage { MS_DIGITS = 0, MS_EXPAND, MS_PLIFT, MS_LAST, MS_REST_Z, MS_REST_OUT, MS_COUNT };
+cudaError_t launch_mrr_multi(MultiStage stage, const EvalArgs &a, const JobTable &t, u32 units, cudaStream_t s);
 
 enum EvalKernel {
     EK_KS_DIGITS = 0,

@@ -40,6 +40,12 @@ class MrrJob(ctypes.Structure):
                 ("count", ctypes.c_uint32), ("level", ctypes.c_uint32)]
 
 
+class MrrMultiJob(ctypes.Structure):
+    _fields_ = [("ct_out", ctypes.c_void_p), ("ct_a", ctypes.c_void_p), ("ct_b", ctypes.c_void_p),
+                ("count", ctypes.c_uint32), ("level", ctypes.c_uint32), ("ctx", ctypes.c_void_p),
+                ("key", ctypes.c_void_p)]
+
+
 class NttShape(ctypes.Structure):
     _fields_ = [("N", ctypes.c_uint32), ("log_block", ctypes.c_uint32), ("log_thread_words", ctypes.c_uint32),
                 ("persistent", ctypes.c_uint32)]
@@ -124,6 +130,9 @@ _SIGS = {
     "he_encrypt": (ctypes.c_int32, [_vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_uint32, _vp, ctypes.c_uint32, _vp,
                                     ctypes.c_size_t, _vp]),
     "he_mul_relin_rescale_batch_scratch_bytes": (ctypes.c_size_t, [_vp, ctypes.POINTER(MrrJob), ctypes.c_uint32]),
+    "he_mul_relin_rescale_multi_scratch_bytes": (ctypes.c_size_t, [ctypes.POINTER(MrrMultiJob), ctypes.c_uint32]),
+    "he_mul_relin_rescale_multi": (ctypes.c_int32, [ctypes.POINTER(MrrMultiJob), ctypes.c_uint32, _vp,
+                                                    ctypes.c_size_t, _vp]),
     "he_mul_relin_rescale_batch": (ctypes.c_int32, [ctypes.POINTER(MrrJob), ctypes.c_uint32, _vp, _vp, _vp,
                                                     ctypes.c_size_t, _vp]),
 }
@@ -506,6 +515,31 @@ def mul_relin_rescale_batch(jobs, key: RelinKey, ctx: Context, scratch, stream=N
         w_in, w_out = count * 2 * (level + 1) * ctx.N, count * 2 * level * ctx.N
         arr[i] = MrrJob(_ptr(out, w_out), _ptr(a, w_in), _ptr(b, w_in), count, level)
     _check(load().he_mul_relin_rescale_batch(arr, len(jobs), key.handle, ctx.handle, _ptr(scratch),
+                                             scratch.numel() * 8, _stream(stream)))
+
+
+def _multi_jobs(jobs, with_pointers: bool):
+    arr = (MrrMultiJob * max(1, len(jobs)))()
+    for i, (out, a, b, count, level, key, ctx) in enumerate(jobs):
+        if with_pointers:
+            w_in, w_out = count * 2 * (level + 1) * ctx.N, count * 2 * level * ctx.N
+            arr[i] = MrrMultiJob(_ptr(out, w_out), _ptr(a, w_in), _ptr(b, w_in), count, level, ctx.handle.value,
+                                 key.handle.value)
+        else:
+            arr[i] = MrrMultiJob(None, None, None, count, level, ctx.handle.value, key.handle.value)
+    return arr
+
+
+def mul_relin_rescale_multi_scratch_bytes(jobs) -> int:
+    """Scratch of mul_relin_rescale_multi for (count, level, key, ctx) jobs."""
+    return int(load().he_mul_relin_rescale_multi_scratch_bytes(
+        _multi_jobs([(None, None, None, c, l, k, x) for c, l, k, x in jobs], False), len(jobs)))
+
+
+def mul_relin_rescale_multi(jobs, scratch, stream=None):
+    """MulLinRS of jobs of different degrees, one launch per pipeline stage:
+    jobs are (ct_out, ct_a, ct_b, count, level, key, ctx) tuples."""
+    _check(load().he_mul_relin_rescale_multi(_multi_jobs(jobs, True), len(jobs), _ptr(scratch),
                                              scratch.numel() * 8, _stream(stream)))
 
 
