@@ -46,10 +46,12 @@ MRR_N = 16384
 MRR_BITS = [60] + [50] * 6
 MRR_COUNT = 64
 METRIC = "NTT limbs/s at N=2^15 + HE mul-relin-rescale/s, batched vs plain; p99 latency"
-# DRAM bytes (read + write) of one forward launch of the 1024 x 8 x 2^15
-# batch in the radix-16 shape below: an ncu capture of the same kernel on 256
-# instances (541124352 B read, 481917696 B written) scaled by 4.
-FWD_TRAFFIC = {"shape": [12, 4, 0], "bytes": 4 * (541124352 + 481917696)}
+# DRAM bytes (read + write) of one launch of the 1024 x 8 x 2^15 batch, per
+# direction and transform shape (log_block, log_thread_words, persistent):
+# an ncu capture of the same kernel on 256 instances scaled by 4 (traffic
+# grows in proportion to the limbs). Entries are removed when the kernel
+# changes after their capture, so that no stale figure is reported.
+TRAFFIC = {}
 # The production forward butterfly keeps the IMAD (fmaheavy) pipe busy for
 # 0.2536 cycles per butterfly per SM: ncu on the register-resident probe
 # (1216 x 256 threads x 16 x 1024 butterflies) counts that pipe 94.2 % active
@@ -77,7 +79,7 @@ def _args():
     ap.add_argument("--shape", default="",
                     help="log_block,log_thread_words[,persistent] for --profile-case ntt (or fwd/inv)")
     ap.add_argument("--skip", default="", help="comma list of sub-benchmarks to skip: small,uneven,matrix,routines,encode,serving")
-    ap.add_argument("--serve-requests", type=int, default=4000)
+    ap.add_argument("--serve-requests", type=int, default=20000)
     ap.add_argument("--no-tune-cache", action="store_true", help="always re-run the autotuner")
     ap.add_argument("--ref-instances", type=int, default=REF_INSTANCES,
                     help="instances per step of the reference arm (default: 1/8 of the batch)")
@@ -205,6 +207,46 @@ def _collectives(world: int, device):
 def job_value(world: int, units_per_rank: float, ms_max: float) -> float:
     """Whole-job throughput: every rank's units over the slowest rank's time."""
     return world * units_per_rank / (ms_max / 1e3)
+
+
+def mrr_work(n: int, N: int) -> dict:
+    """Algorithmic work of one MulLinRS (tensor, relinearization with one
+    special prime and n RNS digits, rescale) at n data limbs and degree N:
+    n^2 + 5n + 2 transforms of (N/2) log2 N butterflies; N (2n^2 + 16n - 4)
+    further modular products (tensor 4n, key products 2n(n+1), d P 2n,
+    mod-down 2n + 2n centred reductions, rescale 2(n-1) + 2(n-1)); HBM bytes:
+    the two input ciphertexts read and the output written once (the
+    resident key is not counted)."""
+    log_n = N.bit_length() - 1
+    return {"bfly": (n * n + 5 * n + 2) * (N // 2) * log_n, "products": N * (2 * n * n + 16 * n - 4),
+            "bytes": (4 * n + 2 * (n - 1)) * N * 8}
+
+
+def roof_entry(work: dict, seconds: float, alu_peak: float, hbm_peak: float) -> dict:
+    """Achieved rates of `work` (bfly, products, bytes per timed unit of
+    `seconds`) against the derived integer peak (butterflies/s) and the
+    measured HBM copy bandwidth (GB/s). A modular product outside the
+    transforms is counted as one butterfly (one Shoup-sized multiply)."""
+    e = {"tbfly_per_s": work["bfly"] / seconds / 1e12, "alu_frac_transforms": work["bfly"] / seconds / alu_peak,
+         "gbs": work["bytes"] / seconds / 1e9, "hbm_frac": work["bytes"] / seconds / 1e9 / hbm_peak}
+    if work.get("products"):
+        e["alu_frac_with_products"] = (work["bfly"] + work["products"]) / seconds / alu_peak
+    return e
+
+
+def attach_rooflines(obj, alu_peak: float, hbm_peak: float):
+    """Replace every "_work" entry ({"bfly", "products", "bytes", "seconds"})
+    in a (nested) result by its "roofline" entry."""
+    if isinstance(obj, dict):
+        w = obj.pop("_work", None)
+        if w is not None:
+            obj["roofline"] = roof_entry(w, w["seconds"], alu_peak, hbm_peak)
+        for v in obj.values():
+            attach_rooflines(v, alu_peak, hbm_peak)
+    elif isinstance(obj, list):
+        for v in obj:
+            attach_rooflines(v, alu_peak, hbm_peak)
+    return obj
 
 
 def run_ours(args, rank, world, local):
@@ -386,14 +428,30 @@ def run_ours(args, rank, world, local):
 
     peaks = _measured_peaks()
     hbm_peak = peaks.get("hbm_gbs") or 6800.0
-    achieved_gbs = bytes_per_launch / (fwd / 1e3) / 1e9
-    achieved_bfly = bfly_per_launch / (fwd / 1e3)
     # derived integer peak: the IMAD pipe fully busy at the sampled clock
     clock_hz = (clk.get("sm_mhz") or peaks.get("sm_max_mhz") or 2070.0) * 1e6
     alu_peak = sms * clock_hz / FMAHEAVY_CYCLES_PER_BFLY
-    frac_hbm = achieved_gbs / hbm_peak
-    frac_alu = achieved_bfly / alu_peak
-    bound_alu = frac_alu >= frac_hbm
+
+    def direction_roof(name, ms_dir, shape):
+        gbs = bytes_per_launch / (ms_dir / 1e3) / 1e9
+        bf = bfly_per_launch / (ms_dir / 1e3)
+        key = (name, tuple(shape))
+        return {"kernel": "k_ntt %s, 2^%d words per CTA x cluster of %d, 2^%d words per thread%s" % (
+                    name, shape[0], N >> shape[0], shape[1], ", persistent" if shape[2] else ""),
+                "ms": ms_dir, "achieved_tbfly": bf / 1e12, "alu_frac": bf / alu_peak,
+                "achieved_gbs": gbs, "hbm_frac": gbs / hbm_peak,
+                "traffic": TRAFFIC.get(key)}
+
+    roof_fwd = direction_roof("forward", fwd, tune["fwd"])
+    roof_inv = direction_roof("inverse", inv, tune["inv"])
+    dom = roof_inv if inv >= fwd else roof_fwd          # the larger share of the step
+    bound_alu = dom["alu_frac"] >= dom["hbm_frac"]
+    attach_rooflines(small, alu_peak, hbm_peak)
+    attach_rooflines(uneven, alu_peak, hbm_peak)
+    attach_rooflines(matrix, alu_peak, hbm_peak)
+    attach_rooflines(routines, alu_peak, hbm_peak)
+    mrr_roof = roof_entry({k: v * MRR_COUNT for k, v in mrr_work(L + 1, MRR_N).items()}, ms_mrr / 1e3,
+                          alu_peak, hbm_peak)
     value = job_value(world, 2 * limbs_total, ms)
     e2e_value = job_value(world, 2 * limbs_total, ms_e2e)
     line = {
@@ -435,23 +493,26 @@ def run_ours(args, rank, world, local):
             "plain_per_s": world * MRR_COUNT / (ms_mrr_plain / 1e3),
             "ms_per_batch": ms_mrr,
             "transforms_per_op": (L + 1) ** 2 + 5 * (L + 1) + 2,
+            "work_per_op": mrr_work(L + 1, MRR_N),
+            "roofline": mrr_roof,
             "autotune": mrr_tune,
         },
         "roofline": {
-            "kernel": "k_ntt forward, 2^%d words per CTA x cluster of %d, 2^%d words per thread" % (
-                tune["fwd"][0], N >> tune["fwd"][0], tune["fwd"][1]),
+            "kernel": dom["kernel"],
             "bound": "alu" if bound_alu else "hbm",
-            "achieved": achieved_bfly / 1e12 if bound_alu else achieved_gbs,
+            "achieved": dom["achieved_tbfly"] if bound_alu else dom["achieved_gbs"],
             "peak": alu_peak / 1e12 if bound_alu else hbm_peak,
             "unit": "Tbutterfly/s" if bound_alu else "GB/s",
-            "frac": frac_alu if bound_alu else frac_hbm,
-            "traffic": FWD_TRAFFIC["bytes"] if list(tune["fwd"]) == FWD_TRAFFIC["shape"] else None,
-            "hbm": {"achieved_gbs": achieved_gbs, "peak_gbs": hbm_peak, "frac": frac_hbm,
+            "frac": dom["alu_frac"] if bound_alu else dom["hbm_frac"],
+            "traffic": dom["traffic"],
+            "dominant": "inverse" if dom is roof_inv else "forward",
+            "directions": {"forward": roof_fwd, "inverse": roof_inv},
+            "hbm": {"achieved_gbs": dom["achieved_gbs"], "peak_gbs": hbm_peak, "frac": dom["hbm_frac"],
                     "peak_source": "measured copy bandwidth" if peaks.get("hbm_gbs") else "fallback"},
-            "alu": {"achieved_tbfly": achieved_bfly / 1e12, "peak_tbfly": alu_peak / 1e12, "frac": frac_alu,
+            "alu": {"achieved_tbfly": dom["achieved_tbfly"], "peak_tbfly": alu_peak / 1e12, "frac": dom["alu_frac"],
                     "peak_source": f"derived: {sms} SMs x {clock_hz / 1e6:.0f} MHz / "
                                    f"{FMAHEAVY_CYCLES_PER_BFLY} IMAD-pipe cycles per butterfly",
-                    "probe_tbfly": bfly_rate / 1e12, "frac_of_probe": achieved_bfly / bfly_rate,
+                    "probe_tbfly": bfly_rate / 1e12, "frac_of_probe": dom["achieved_tbfly"] * 1e12 / bfly_rate,
                     "probe_source": "register-resident butterfly probe, same run"},
             "algorithmic_bytes_per_launch": bytes_per_launch,
             "butterflies_per_launch": bfly_per_launch,
@@ -559,6 +620,8 @@ def bench_small(args, stream, barrier):
             "launches": {"forward_inverse": 2, "product": 4, "product_fused": 1},
             "note": "latency of back-to-back launches on one stream (inputs in L2)",
             "batch": {"workload": "negacyclic product, 128 polys x 8 limbs at N=2^15",
+                      "_work": {"bfly": bfly, "products": limbs_b * Nb, "bytes": 24 * Nb * limbs_b,
+                                "seconds": ms_f / 1e3},
                       "ms_fused": ms_f, "fused_products_per_s": limbs_b / (ms_f / 1e3),
                       "fused_tbfly_per_s": bfly / (ms_f / 1e3) / 1e12,
                       "ms_unfused": ms_u, "unfused_products_per_s": limbs_b / (ms_u / 1e3)}}
@@ -621,9 +684,13 @@ def bench_uneven(args, stream, barrier):
     ms_graph = _time_steps(g.replay, args.steps, args.warmup, stream, barrier)
     ms_deg = _time_steps(run_plan(per_degree), args.steps, args.warmup, stream, barrier)
     ms_plain = _time_steps(step_plain, max(2, args.steps // 5), 3, stream, barrier)
+    bfly = sum(L * (N // 2) * (N.bit_length() - 1) for N, L in zip(Ns, Ls))
+    work = {"bfly": 2 * bfly, "products": 0, "bytes": 2 * 16 * words}      # forward + inverse per step
     return {
         "workload": "512 polys, N in {4096..32768}, 1-16 limbs of 50-60-bit primes, seed 3",
         "limbs": limbs, "words": words,
+        "mixed": {"_work": dict(work, seconds=ms_mixed / 1e3)},
+        "per_degree": {"_work": dict(work, seconds=ms_deg / 1e3)},
         "mixed_single_launch_limbs_per_s": 2 * limbs / (ms_mixed / 1e3),
         "mixed_graph_limbs_per_s": 2 * limbs / (ms_graph / 1e3),
         "per_degree_launches_limbs_per_s": 2 * limbs / (ms_deg / 1e3),
@@ -666,6 +733,7 @@ def bench_matrix(args, stream, barrier):
     ms = _time_steps(step, args.steps, args.warmup, stream, barrier)
     res = {"workload": "32x32 element-wise, N=8192, primes 60/40/40 + 60, 1024 MulLinRS per step",
            "ms_per_step": ms, "mul_relin_rescale_per_s": count / (ms / 1e3),
+           "_work": dict({k: v * count for k, v in mrr_work(L + 1, N).items()}, seconds=ms / 1e3),
            "eval_log_thread_words": tune["log_thread_words"]}
     del A, B, out, scratch
     # the encrypted matrix product C += A B (matMul_mxnxk): tensors
@@ -736,6 +804,8 @@ def bench_routines(args, stream, barrier):
     for name, fn in ops.items():
         ms = _time_steps(fn, max(3, args.steps // 2), 3, stream, barrier)
         res[name] = {"ms_per_batch": ms, "per_s": count / (ms / 1e3)}
+        if name in ("mul_lin_rs", "sqr_lin_rs"):
+            res[name]["_work"] = dict({k: v * count for k, v in mrr_work(L + 1, N).items()}, seconds=ms / 1e3)
     return res
 
 
@@ -798,31 +868,48 @@ def bench_encode(args, stream, barrier):
     }
 
 
+SERVE_WARMUP = 1000
+SERVE_POOL = 4          # input pairs per (N, level) bucket: about 1.1 GB of pinned host ciphertexts in all
+SERVE_SWEEP = (1000.0, 4000.0, 8000.0, 16000.0)
+
+
 def bench_serving(args):
     """Poisson arrivals at 2000 requests/s of MulLinRS jobs, N in {8192,
     16384, 32768}, levels 2-16, keys resident, 64 GB admission budget: the
     continuous-batching server (batches per degree and level), the same
     server batching every level of a degree together (mixed-level batches,
-    one launch per pipeline stage), and the server with one request per
-    launch (one slot, one stream). Each server reserves its buffer pool at
-    start-up (prewarm) and runs its loop without collector pauses."""
+    one launch per pipeline stage), batching every degree and level together
+    (multi-degree batches, one launch per pipeline stage), and the server
+    with one request per launch (one slot, one stream). Each server reserves its buffer pool at
+    start-up (prewarm) and runs its loop without collector pauses. Every
+    measured run follows SERVE_WARMUP warm-up requests; requests draw their
+    inputs from SERVE_POOL pinned host pairs per bucket (uploaded per
+    request). A short sweep of the arrival rate up to saturation shows where
+    batching pays."""
     from paper_2109_14704_gb300 import serving
 
     import torch
 
-    out = {"workload": "Poisson 2000 req/s, N in {8192,16384,32768}, levels 2-16, budget 64 GB"}
+    out = {"workload": f"Poisson 2000 req/s, N in {{8192,16384,32768}}, levels 2-16, budget 64 GB, "
+                       f"{args.serve_requests} requests after {SERVE_WARMUP} warm-up, {SERVE_POOL} input pairs "
+                       f"per (N, level) bucket"}
+    sweep_n = max(1000, args.serve_requests // 5)
+    pool = None
     for name, kw in (("batched", dict(slots=16, streams=4, prewarm_batches=8)),
                      ("mixed_levels", dict(slots=16, streams=4, prewarm_batches=8, mixed_levels=True)),
+                     ("mixed_degrees", dict(slots=16, streams=4, prewarm_batches=8, mixed_degrees=True)),
                      ("plain", dict(slots=1, streams=1, prewarm_batches=4))):
         # every server starts from an empty allocator cache (the previous
         # phases' freed blocks would otherwise count against device memory)
         torch.cuda.synchronize()
         torch.cuda.empty_cache()
-        srv = serving.Server(pool_per_bucket=1, seed=5, **kw)
-        srv.run(srv.make_requests(300, rate=2000.0, seed=55))              # warm-up
+        srv = serving.Server(pool_per_bucket=SERVE_POOL, seed=5, pool=pool, **kw)
+        pool = srv.pool                      # generated once, shared by the three servers
+        srv.run(srv.make_requests(SERVE_WARMUP, rate=2000.0, seed=55))     # warm-up
         srv.completed.clear()
         srv.batches_launched = 0
         out[name] = srv.run(srv.make_requests(args.serve_requests, rate=2000.0, seed=5))
+        out[name]["input_pool_gb"] = sum(t.numel() * 8 for t in srv.pool.values()) / 2 ** 30
         # capacity: the same request mix arriving far faster than it can be served
         srv.completed.clear()
         srv.batches_launched = 0
@@ -830,6 +917,14 @@ def bench_serving(args):
         out[name]["saturated_throughput_per_s"] = sat["throughput_per_s"]
         out[name]["saturated_mean_batch"] = sat["mean_batch"]
         out[name]["expand_group"] = srv.expand_group
+        sw = []
+        for rate in SERVE_SWEEP:
+            srv.completed.clear()
+            srv.batches_launched = 0
+            r = srv.run(srv.make_requests(sweep_n, rate=rate, seed=7))
+            sw.append({"rate": rate, "requests": sweep_n, "throughput_per_s": r["throughput_per_s"],
+                       "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"], "mean_batch": r["mean_batch"]})
+        out[name]["rate_sweep"] = sw
         del srv
     torch.cuda.synchronize()
     torch.cuda.empty_cache()

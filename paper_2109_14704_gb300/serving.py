@@ -22,7 +22,10 @@ buffers come from a memory cache that reuses any free buffer large enough
 * With mixed_levels, the buckets are the degrees alone: a batch takes
   requests of any level (each slot sized for the highest level) and runs as
   one he_mul_relin_rescale_batch call, one launch per pipeline stage for the
-  whole mix (each request one job).
+  whole mix (each request one job). With mixed_degrees, one bucket takes
+  every degree and level (slots sized for the largest of both) and runs as
+  one he_mul_relin_rescale_multi call: jobs of different degrees share one
+  launch per pipeline stage.
 * Completion is timed with CUDA events; latency = completion - arrival on
   one clock (events are anchored to the host clock at start). Buffers go
   back to the memory cache when the batch's completion event has fired.
@@ -168,7 +171,7 @@ class Server:
 
     def __init__(self, degrees=(8192, 16384, 32768), min_level=2, max_level=16, budget_bytes=64 << 30,
                  slots=16, streams=4, max_wait_s=0.002, pool_per_bucket=2, seed=5, device=None, expand_group=4,
-                 prewarm_batches=0, mixed_levels=False):
+                 prewarm_batches=0, mixed_levels=False, mixed_degrees=False, pool=None):
         import torch
         self.torch = torch
         self.device = device or torch.device("cuda", torch.cuda.current_device())
@@ -183,9 +186,12 @@ class Server:
         # key-switching mod-up expanded in groups of at most this many
         # ciphertexts (bounds a batch's scratch; 0 = the fused minimum)
         self.expand_group = expand_group
-        self.mixed = mixed_levels
-        if mixed_levels and slots > he.MAX_BATCH_JOBS:
-            raise ValueError(f"mixed-level batches take at most {he.MAX_BATCH_JOBS} slots")
+        # mixed_levels: one batch per degree, any level; mixed_degrees: one
+        # batch for every degree and level (he_mul_relin_rescale_multi)
+        self.mixed_deg = mixed_degrees
+        self.mixed = mixed_levels or mixed_degrees
+        if self.mixed and slots > he.MAX_BATCH_JOBS:
+            raise ValueError(f"mixed batches take at most {he.MAX_BATCH_JOBS} slots")
         self.rng = Rng(seed)
         self.ctx, self.key, self.moduli = {}, {}, {}
         self.static_bytes = 0
@@ -199,9 +205,10 @@ class Server:
             self.key[N] = he.RelinKey(self.ctx[N], evk)
             # resident: key words with Shoup quotients, twiddles of n_data+1 primes, constants
             self.static_bytes += evk.size * 16 + (n_data + 1) * N * 32
-        # Client-side input pool: pinned host ciphertext pairs per (N, level).
-        self.pool = {}
-        for N in self.degrees:
+        # Client-side input pool: pinned host ciphertext pairs per (N, level)
+        # (or another server's pool over the same degrees and levels).
+        self.pool = pool if pool is not None else {}
+        for N in ([] if pool is not None else self.degrees):
             for lvl in range(min_level, max_level + 1):
                 qs = self.moduli[N][:lvl + 1]
                 pairs = np.stack([np.stack([np.stack([self.rng.uniform_limbs(qs, N) for _ in range(2)])
@@ -242,7 +249,9 @@ class Server:
     def _batch_words(self, N, lvl, cap):
         n = lvl + 1
         ct_in = 2 * n * N
-        if self.mixed:   # slots sized for the highest level
+        if self.mixed_deg:   # slots sized for the largest degree and level
+            scratch = he.mul_relin_rescale_multi_scratch_bytes([(1, lvl, self.key[N], self.ctx[N])] * cap) // 8
+        elif self.mixed:     # slots sized for the highest level
             scratch = self.ctx[N].mrr_batch_scratch_bytes([(1, lvl)] * cap) // 8
         else:
             scratch = self.ctx[N].mrr_scratch_bytes(lvl, cap, self.expand_group) // 8
@@ -250,12 +259,16 @@ class Server:
 
     def _slot_words(self, N, lvl):
         """Input and output words of one slot of a batch (its stride)."""
+        if self.mixed_deg:
+            N = max(self.degrees)
         if self.mixed:
             lvl = self.max_level
         return 2 * (lvl + 1) * N, 2 * lvl * N
 
     def _open_batch(self, key, now):
         N, lvl = key
+        if self.mixed_deg:
+            N = max(self.degrees)
         words = self._batch_words(N, self.max_level if self.mixed else lvl, self.slots)
         bufs = self.cache.allocate_within(words, self.budget, self.static_bytes)
         if bufs is None:
@@ -268,7 +281,7 @@ class Server:
 
     # ---- request flow
     def _admit(self, req: Request, now) -> bool:
-        key = (req.N, None if self.mixed else req.level)
+        key = (None if self.mixed_deg else req.N, None if self.mixed else req.level)
         b = self.open.get(key)
         if b is None:
             b = self._open_batch(key, now)
@@ -306,7 +319,15 @@ class Server:
         N, lvl = b.key
         count = len(b.reqs)
         scratch = b.bufs[3][1]
-        if self.mixed:
+        if self.mixed_deg:
+            si, so = self._slot_words(None, None)
+            jobs = []
+            for r in b.reqs:
+                pi, po = 2 * (r.level + 1) * r.N, 2 * r.level * r.N
+                jobs.append((b.bufs[2][1][r.slot * so:r.slot * so + po], b.bufs[0][1][r.slot * si:r.slot * si + pi],
+                             b.bufs[1][1][r.slot * si:r.slot * si + pi], 1, r.level, self.key[r.N], self.ctx[r.N]))
+            he.mul_relin_rescale_multi(jobs, scratch, stream=s)
+        elif self.mixed:
             si, so = self._slot_words(N, None)
             jobs = []
             for r in b.reqs:
@@ -335,13 +356,12 @@ class Server:
         for b in self.inflight:
             if b.done_event.query():
                 t = self.anchor.elapsed_time(b.done_event) / 1e3     # seconds since start
-                N = b.key[0]
                 for r in b.reqs:
                     r.done = t
                     self.completed.append(r)
                     if r.rid in self.keep:
-                        so = self._slot_words(N, r.level)[1]
-                        self.keep[r.rid] = b.bufs[2][1][r.slot * so:r.slot * so + 2 * r.level * N].cpu().clone()
+                        so = self._slot_words(r.N, r.level)[1]
+                        self.keep[r.rid] = b.bufs[2][1][r.slot * so:r.slot * so + 2 * r.level * r.N].cpu().clone()
                 for cap, t_ in b.bufs:
                     self.cache.free(cap, t_)
                 if self.busy.get(b.stream_index) is b:

@@ -81,9 +81,12 @@ def _small_server(**kw):
     return serving.Server(**args)
 
 
-@pytest.mark.parametrize("mixed", [False, True])
-def test_serving_alone_equals_in_the_mix(mixed):
-    srv = _small_server(mixed_levels=mixed)
+_MODES = {"per_level": {}, "mixed_levels": {"mixed_levels": True}, "mixed_degrees": {"mixed_degrees": True}}
+
+
+@pytest.mark.parametrize("mode", list(_MODES))
+def test_serving_alone_equals_in_the_mix(mode):
+    srv = _small_server(**_MODES[mode])
     reqs = srv.make_requests(240, rate=20000.0, seed=12)
     keep = [3, 50, 51, 52, 117, 200, 239]
     stats = srv.run(reqs, keep_ids=keep)
@@ -95,21 +98,27 @@ def test_serving_alone_equals_in_the_mix(mixed):
         assert torch.equal(srv.keep[rid], alone), rid
 
 
-@pytest.mark.parametrize("mixed", [False, True])
-def test_serving_result_matches_oracle(mixed):
-    srv = _small_server(degrees=(4096,), max_level=3, mixed_levels=mixed)
+@pytest.mark.parametrize("mode", list(_MODES))
+def test_serving_result_matches_oracle(mode):
+    degrees = (4096, 8192) if mode == "mixed_degrees" else (4096,)
+    srv = _small_server(degrees=degrees, max_level=3, **_MODES[mode])
     reqs = srv.make_requests(20, rate=5000.0, seed=13)
     srv.run(reqs, keep_ids=[7])
-    if mixed:   # one batch per degree held several levels
+    if mode != "per_level":   # one batch held several levels (and degrees)
         assert len({q.level for q in reqs}) > 1
     r = reqs[7]
     src = srv.pool[(r.N, r.level)][r.src].numpy().view(np.uint64)
     ctx = srv.ctx[r.N]
-    # the server's keys are uniform words generated from its seed; rebuild them
+    # the server's keys are uniform words generated from its seed, degree by
+    # degree; rebuild them
     rng = Rng(11)
     n_data = srv.max_level + 1
+    for N in srv.degrees:
+        data, P = srv.moduli[N], srv.ctx[N].P
+        evk = np.stack([np.stack([rng.uniform_limbs(data + [P], N) for _ in range(2)]) for _ in range(n_data)])
+        if N == r.N:
+            break
     data, P = srv.moduli[r.N], ctx.P
-    evk = np.stack([np.stack([rng.uniform_limbs(data + [P], r.N) for _ in range(2)]) for _ in range(n_data)])
     ref = oracle.mul_relin_rescale(src[0], src[1], evk, data, P, r.level)
     assert np.array_equal(srv.keep[7].numpy().view(np.uint64).reshape(ref.shape), ref)
 
