@@ -122,22 +122,39 @@ k_ntt_persistent(NttLaunch a)
 }
 
 // Mixed-degree form: clusters of 8 CTAs of 2^12 words each take units of a
-// list (plans launch one cluster per unit; a smaller grid walks the list); a unit of degree 2^(12+c) holds up to 8 >> c limbs, each
-// transformed by a sub-cluster of 2^c CTAs (cluster ranks rbase .. rbase +
-// 2^c - 1). One launch covers every degree from 2^12 to 2^15. Sub-clusters
-// without a limb in the last unit of a degree recompute the unit's first
-// limb with stores switched off, so that every CTA of the cluster passes the
-// same cluster barriers.
+// list (plans launch one cluster per unit; a smaller grid walks the list); a
+// unit of degree 2^(12+c) holds up to 8 >> c limbs, each transformed by a
+// sub-cluster of 2^c CTAs (cluster ranks rbase .. rbase + 2^c - 1). One
+// launch covers every degree from 2^12 to 2^15. Sub-clusters without a limb
+// in the last unit of a degree recompute the unit's first limb with stores
+// switched off, so that every CTA of the cluster passes the same cluster
+// barriers. Not inlined: each shape gets its own register allocation (one
+// kernel body holding all four shapes spilled up to 656 bytes at 64
+// registers; this way 12-44 bytes, 172 for the smallest inverse).
 template <class Sh, bool INV>
-__device__ __forceinline__ void mixed_unit(u64 *smem, u32 rank, const MixedUnit &un, const LimbJob *jobs)
+__device__ __noinline__ void mixed_unit(u64 *smem, u32 rank, const MixedUnit &un, const LimbJob *jobs)
 {
-    const u32 sub = rank >> Sh::LOG_C;
-    const u32 m = rank & (Sh::C - 1);
-    const u32 rbase = sub << Sh::LOG_C;
-    const bool valid = sub < un.n_jobs;
-    const LimbJob j = jobs[un.first_job + (valid ? sub : 0u)];
-    const PrimeConst pc = *j.pc;
-    ntt_limb<Sh, INV>(smem, m, rbase, j.data, INV ? j.tw_inv : j.tw_fwd, pc, valid);
+    if constexpr (Sh::LOG_C == 3) {
+        // the whole cluster transforms the unit's one limb
+        const LimbJob j = jobs[un.first_job];
+        const PrimeConst pc = *j.pc;
+        ntt_limb<Sh, INV>(smem, rank, 0, j.data, INV ? j.tw_inv : j.tw_fwd, pc);
+    } else if constexpr (Sh::LOG_C == 0) {
+        // one CTA per limb and no cluster barrier inside the transform: a
+        // CTA without a limb has nothing to do
+        if (rank >= un.n_jobs) return;
+        const LimbJob j = jobs[un.first_job + rank];
+        const PrimeConst pc = *j.pc;
+        ntt_limb<Sh, INV>(smem, 0, 0, j.data, INV ? j.tw_inv : j.tw_fwd, pc);
+    } else {
+        const u32 sub = rank >> Sh::LOG_C;
+        const u32 m = rank & (Sh::C - 1);
+        const u32 rbase = sub << Sh::LOG_C;
+        const bool valid = sub < un.n_jobs;
+        const LimbJob j = jobs[un.first_job + (valid ? sub : 0u)];
+        const PrimeConst pc = *j.pc;
+        ntt_limb<Sh, INV>(smem, m, rbase, j.data, INV ? j.tw_inv : j.tw_fwd, pc, valid);
+    }
 }
 
 template <bool INV>
