@@ -62,6 +62,7 @@ FMAHEAVY_CYCLES_PER_BFLY = 0.2536
 UNIT = "limb-NTT/s"
 CPU_RUNS = 5                          # the CPU baseline is the median of this many runs
 REF_INSTANCES = NTT_INSTANCES // 8    # reference arm: 1/8 of the batch per step
+TUNE_REPS = 10                        # autotuner: median of this many timed runs per candidate
 
 
 def _args():
@@ -282,7 +283,7 @@ def run_ours(args, rank, world, local):
         he.ntt_inv(d, N, NTT_LIMBS, NTT_INSTANCES, tables, stream=stream)
 
     # pick the transform shape for this batch (checked, timed, applied)
-    tune = autotune.tune_uniform(N, NTT_LIMBS, NTT_INSTANCES, moduli=qs, reps=5, warmup=2,
+    tune = autotune.tune_uniform(N, NTT_LIMBS, NTT_INSTANCES, moduli=qs, reps=TUNE_REPS, warmup=3,
                                  cache_path=None if args.no_tune_cache else autotune.DEFAULT_CACHE)
     d.copy_(pinned)
 
@@ -351,7 +352,7 @@ def run_ours(args, rank, world, local):
 
     ca = torch.from_numpy(cts().view(np.int64)).to(dev)
     cb = torch.from_numpy(cts().view(np.int64)).to(dev)
-    mrr_tune = autotune.tune_mul_relin_rescale(ctx, key, L, MRR_COUNT, reps=5, warmup=2)
+    mrr_tune = autotune.tune_mul_relin_rescale(ctx, key, L, MRR_COUNT, reps=TUNE_REPS, warmup=3)
     out = torch.empty((MRR_COUNT, 2, L, MRR_N), dtype=torch.int64, device=dev)
     scratch = torch.empty(ctx.mrr_scratch_bytes(L, MRR_COUNT) // 8, dtype=torch.int64, device=dev)
 
@@ -435,9 +436,10 @@ def run_ours(args, rank, world, local):
     def direction_roof(name, ms_dir, shape):
         gbs = bytes_per_launch / (ms_dir / 1e3) / 1e9
         bf = bfly_per_launch / (ms_dir / 1e3)
-        key = (name, tuple(shape))
-        return {"kernel": "k_ntt %s, 2^%d words per CTA x cluster of %d, 2^%d words per thread%s" % (
-                    name, shape[0], N >> shape[0], shape[1], ", persistent" if shape[2] else ""),
+        key = (name, tuple(shape[:4]))
+        return {"kernel": "k_ntt %s, 2^%d words per CTA x cluster of %d, 2^%d words per thread%s%s" % (
+                    name, shape[0], N >> shape[0], shape[1], ", persistent" if shape[2] else "",
+                    ", %d CTAs per SM" % shape[3] if len(shape) > 3 and shape[3] else ""),
                 "ms": ms_dir, "achieved_tbfly": bf / 1e12, "alu_frac": bf / alu_peak,
                 "achieved_gbs": gbs, "hbm_frac": gbs / hbm_peak,
                 "traffic": TRAFFIC.get(key)}
@@ -477,8 +479,9 @@ def run_ours(args, rank, world, local):
             "inv_limbs_per_s": world * limbs_total / (inv / 1e3),
             "fwd_ms": fwd, "inv_ms": inv, "speedup_vs_naive": ms_naive / ms,
         },
-        "autotune": {"forward": dict(zip(("log_block", "log_thread_words", "persistent"), tune["fwd"])),
-                     "inverse": dict(zip(("log_block", "log_thread_words", "persistent"), tune["inv"])),
+        "autotune": {"forward": dict(zip(("log_block", "log_thread_words", "persistent", "ctas_per_sm"), tune["fwd"])),
+                     "inverse": dict(zip(("log_block", "log_thread_words", "persistent", "ctas_per_sm"), tune["inv"])),
+                     "reps": TUNE_REPS,
                      "candidates": [{"shape": c["shape"], "ms_fwd": c.get("ms_fwd"), "ms_inv": c.get("ms_inv")}
                                     for c in tune["candidates"]]},
         "small_ntt": small,
@@ -653,7 +656,7 @@ def bench_uneven(args, stream, barrier):
     limbs = sum(Ls)
     words = sum(N * L for N, L in zip(Ns, Ls))
     mixed = he.NttPlan(entries)
-    per_degree = he.NttPlan(entries, shapes={N: he.ntt_shapes(N)[0] for N in degrees})
+    per_degree = he.NttPlan(entries, shapes={N: he.ntt_shapes(N)[0][:2] for N in degrees})
 
     def run_plan(plan):
         def step():
@@ -725,7 +728,7 @@ def bench_matrix(args, stream, barrier):
     out = torch.empty((count, 2, L, N), dtype=torch.int64, device="cuda")
     scratch = torch.empty(ctx.mrr_scratch_bytes(L, count) // 8, dtype=torch.int64, device="cuda")
     from paper_2109_14704_gb300 import autotune
-    tune = autotune.tune_mul_relin_rescale(ctx, key, L, count, reps=3, warmup=1)
+    tune = autotune.tune_mul_relin_rescale(ctx, key, L, count, reps=TUNE_REPS, warmup=3)
 
     def step():
         he.mul_relin_rescale(out, A, B, count, key, ctx, L, scratch, stream=stream)

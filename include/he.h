@@ -123,22 +123,25 @@ he_status he_ntt_inv_naive(uint64_t *poly, uint32_t N, uint32_t limbs, uint32_t 
                            const uint64_t *moduli_host, const he_ntt_tables *tw,
                            he_stream_t stream);
 
-/* Transform shapes built for degree N: writes up to `cap` pairs
- * (log_block, log_thread_words) to pairs_out (host), the default first, and
- * the number built to *n_out. log_block: 2^log_block words per CTA, the
- * transform of one limb split over a cluster of N / 2^log_block CTAs;
- * log_thread_words: 2^log_thread_words words per thread, i.e. radix-2^k
- * register rounds (the paper's radix and SLM-stage choices, Sec. III-B). */
-he_status he_ntt_shapes(uint32_t N, uint32_t *pairs_out, uint32_t cap, uint32_t *n_out);
+/* Transform shapes built for degree N: writes up to `cap` triples
+ * (log_block, log_thread_words, ctas_per_sm) to shapes_out (host, 3 x cap
+ * words), the default first, and the number built to *n_out. log_block:
+ * 2^log_block words per CTA, the transform of one limb split over a cluster
+ * of N / 2^log_block CTAs; log_thread_words: 2^log_thread_words words per
+ * thread, i.e. radix-2^k register rounds (the paper's radix and SLM-stage
+ * choices, Sec. III-B); ctas_per_sm: the CTAs per SM the transform kernels
+ * are compiled for, i.e. their register budget (0 = the shape's default). */
+he_status he_ntt_shapes(uint32_t N, uint32_t *shapes_out, uint32_t cap, uint32_t *n_out);
 
 /* Shape used from now on by he_ntt_fwd (direction 1), he_ntt_inv (2) or
- * both (0) at degree N (process wide; 0, 0, 0 restores the built-in
+ * both (0) at degree N (process wide; all zero restores the built-in
  * default). persistent != 0 launches a fixed grid of as many clusters as fit
- * on the GPU, each walking over the limbs, instead of one cluster per limb.
- * The autotuner's choices are applied here. Returns HE_EUNSUPPORTED for a
- * shape that is not built. */
+ * on the GPU, each walking over the limbs, instead of one cluster per limb;
+ * ctas_per_sm selects a build of the shape for that register budget (0 =
+ * default; he_ntt_shapes lists the builds). The autotuner's choices are
+ * applied here. Returns HE_EUNSUPPORTED for a shape that is not built. */
 he_status he_ntt_set_shape(uint32_t N, uint32_t direction, uint32_t log_block, uint32_t log_thread_words,
-                           uint32_t persistent);
+                           uint32_t persistent, uint32_t ctas_per_sm);
 
 /* Dyadic product out[l][i] = a[l][i] * b[l][i] mod q_l for `count`
  * polynomials of `limbs` limbs (Sec. II-B, the elementwise product of the
@@ -488,6 +491,7 @@ typedef struct he_ntt_shape {
     uint32_t log_block;
     uint32_t log_thread_words;
     uint32_t persistent;
+    uint32_t ctas_per_sm;       /* 0: the shape's default register budget */
 } he_ntt_shape;
 
 /* A plan (Sec. III-B parallelism over limbs and instances) that transforms

@@ -3,11 +3,12 @@
 For a batch shape (N, limbs, count) it times every transform shape the
 library built for that degree (he_ntt_shapes: words per CTA, i.e. how many
 stages run across the CTAs of a cluster versus inside one CTA's shared
-memory, and words per thread, i.e. radix-8 or radix-16 register rounds --
-the paper tuned the same knobs by hand: radix, SLM threshold and register
-slots, Sec. III-B, Sec. IV-A), each launched either as one cluster per limb
-or as a persistent grid walking the limbs, and keeps the fastest for each
-direction. Each candidate is first checked once: its
+memory; words per thread, i.e. radix-8 or radix-16 register rounds and with
+them the threads per CTA; and the CTAs per SM the kernels are compiled for,
+i.e. their register budget -- the paper tuned the same knobs by hand:
+radix, SLM threshold and register slots, Sec. III-B, Sec. IV-A), each
+launched either as one cluster per limb or as a persistent grid walking the
+limbs, and keeps the fastest for each direction. Each candidate is first checked once: its
 forward output must equal the default shape's output bit for bit and its
 inverse must restore the input exactly. Candidates are timed with CUDA
 events (forward + inverse, median of `reps` after warm-up); the fastest wins,
@@ -84,7 +85,7 @@ def tune_uniform(N: int, limbs: int, count: int, moduli=None, reps: int = 10, wa
     persistent) on `count` polynomials of `limbs` limbs at degree N."""
     import torch
 
-    key = f"{_device_key()}|uniform2|N={N}|limbs={limbs}|count={count}"
+    key = f"{_device_key()}|uniform3|N={N}|limbs={limbs}|count={count}"
     cache = _load_cache(cache_path) if cache_path else {}
     if not force and key in cache:
         res = cache[key]
@@ -107,21 +108,22 @@ def tune_uniform(N: int, limbs: int, count: int, moduli=None, reps: int = 10, wa
     ref = d.clone()
 
     cands = []
-    configs = [(lb, le, pers) for pers in (0, 1) for (lb, le) in shapes]
+    # shape = [log_block, log_thread_words, persistent, ctas_per_sm]
+    configs = [(lb, le, pers, occ) for pers in (0, 1) for (lb, le, occ) in shapes]
     try:
-        for idx, (lb, le, pers) in enumerate(configs):
-            he.ntt_set_shape(N, lb, le, pers)
+        for idx, (lb, le, pers, occ) in enumerate(configs):
+            he.ntt_set_shape(N, lb, le, pers, ctas_per_sm=occ)
             d.copy_(x_dev)
             he.ntt_fwd(d, N, limbs, count, tables)
             ok_fwd = bool(torch.equal(d, ref))
             he.ntt_inv(d, N, limbs, count, tables)
             ok_inv = bool(torch.equal(d, x_dev))
             if not (ok_fwd and ok_inv):
-                cands.append({"index": idx, "shape": [lb, le, pers], "ok": False})
+                cands.append({"index": idx, "shape": [lb, le, pers, occ], "ok": False})
                 continue
             ms_f = _time(lambda: he.ntt_fwd(d, N, limbs, count, tables), reps, warmup)
             ms_i = _time(lambda: he.ntt_inv(d, N, limbs, count, tables), reps, warmup)
-            cands.append({"index": idx, "shape": [lb, le, pers], "ok": True, "ms_fwd": ms_f, "ms_inv": ms_i})
+            cands.append({"index": idx, "shape": [lb, le, pers, occ], "ok": True, "ms_fwd": ms_f, "ms_inv": ms_i})
     finally:
         he.ntt_set_shape(N, 0, 0, 0)
     good = [c for c in cands if c["ok"]]
@@ -142,8 +144,9 @@ def tune_uniform(N: int, limbs: int, count: int, moduli=None, reps: int = 10, wa
 
 
 def _apply(N, res):
-    he.ntt_set_shape(N, *res["fwd"], direction=he.FORWARD)
-    he.ntt_set_shape(N, *res["inv"], direction=he.INVERSE)
+    for direction, key in ((he.FORWARD, "fwd"), (he.INVERSE, "inv")):
+        lb, le, pers, occ = (list(res[key]) + [0])[:4]
+        he.ntt_set_shape(N, lb, le, pers, direction=direction, ctas_per_sm=occ)
 
 
 def tune_plan(polys, reps: int = 10, warmup: int = 3, shapes_per_degree: dict | None = None) -> dict:
@@ -158,7 +161,7 @@ def tune_plan(polys, reps: int = 10, warmup: int = 3, shapes_per_degree: dict | 
     options = []
     if all(4096 <= N <= 32768 for N in degrees):
         options.append({})
-    per_degree = {N: tuple((shapes_per_degree or {}).get(N, he.ntt_shapes(N)[0])) for N in degrees}
+    per_degree = {N: tuple((shapes_per_degree or {}).get(N, he.ntt_shapes(N)[0][:2])) for N in degrees}
     options.append(per_degree)
     saved = [p[0].clone() for p in polys]
     results = []

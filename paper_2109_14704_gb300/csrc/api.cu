@@ -345,36 +345,47 @@ static he::NttLaunch uniform_launch(uint64_t *poly, uint32_t limbs, uint32_t cou
 // limb), set by he_ntt_set_shape (e.g. from the autotuner).
 static std::atomic<int> g_shape_b[2][17], g_shape_e[2][17], g_shape_persistent[2][17];   // [inverse][log N]
 
-extern "C" he_status he_ntt_shapes(uint32_t N, uint32_t *pairs_out, uint32_t cap, uint32_t *n_out)
+// Internally a shape's thread-words code carries the CTAs per SM its
+// transform kernels are compiled for in the bits above 4 (inst.cuh).
+static int thread_words_code(uint32_t log_thread_words, uint32_t ctas_per_sm)
+{
+    return (int)(log_thread_words | (ctas_per_sm << 4));
+}
+
+extern "C" he_status he_ntt_shapes(uint32_t N, uint32_t *shapes_out, uint32_t cap, uint32_t *n_out)
 {
     int log_n;
     if (he_status s = check_degree(N, &log_n)) return s;
     if (!n_out) return fail(HE_EINVAL, "n_out is NULL");
     const he::DegreeOps *ops = he::degree_ops(log_n);
     *n_out = (uint32_t)ops->n_shapes;
-    if (cap && !pairs_out) return fail(HE_EINVAL, "pairs_out is NULL");
+    if (cap && !shapes_out) return fail(HE_EINVAL, "shapes_out is NULL");
     for (int i = 0; i < ops->n_shapes && (uint32_t)i < cap; i++) {
-        pairs_out[2 * i] = (uint32_t)ops->shapes[i][0];
-        pairs_out[2 * i + 1] = (uint32_t)ops->shapes[i][1];
+        shapes_out[3 * i] = (uint32_t)ops->shapes[i][0];
+        shapes_out[3 * i + 1] = (uint32_t)ops->shapes[i][1] & 15u;
+        shapes_out[3 * i + 2] = (uint32_t)ops->shapes[i][1] >> 4;
     }
     return HE_OK;
 }
 
 extern "C" he_status he_ntt_set_shape(uint32_t N, uint32_t direction, uint32_t log_block,
-                                      uint32_t log_thread_words, uint32_t persistent)
+                                      uint32_t log_thread_words, uint32_t persistent, uint32_t ctas_per_sm)
 {
     int log_n;
     if (he_status s = check_degree(N, &log_n)) return s;
     if (direction > 2) return fail(HE_EINVAL, "direction must be 0 (both), 1 (forward) or 2 (inverse)");
-    if (log_block || log_thread_words) {
-        if (!he::degree_ops(log_n)->has_shape((int)log_block, (int)log_thread_words))
-            return fail(HE_EUNSUPPORTED, "no kernel with 2^%u words per CTA and 2^%u per thread for N = %u",
-                        log_block, log_thread_words, N);
+    if (log_thread_words > 15 || ctas_per_sm > 32) return fail(HE_EINVAL, "log_thread_words or ctas_per_sm out of range");
+    const int code = thread_words_code(log_thread_words, ctas_per_sm);
+    if (log_block || code) {
+        if (!he::degree_ops(log_n)->has_shape((int)log_block, code))
+            return fail(HE_EUNSUPPORTED,
+                        "no kernel with 2^%u words per CTA, 2^%u per thread and %u CTAs per SM for N = %u", log_block,
+                        log_thread_words, ctas_per_sm, N);
     }
     for (int inv = 0; inv < 2; inv++) {
         if ((direction == 1 && inv) || (direction == 2 && !inv)) continue;
         g_shape_b[inv][log_n].store((int)log_block);
-        g_shape_e[inv][log_n].store((int)log_thread_words);
+        g_shape_e[inv][log_n].store(code);
         g_shape_persistent[inv][log_n].store(persistent ? 1 : 0);
     }
     return HE_OK;
@@ -1574,9 +1585,13 @@ extern "C" he_status he_ntt_plan_create(const he_poly_desc *descs_host, uint32_t
         int log_n;
         if (he_status st = check_degree(shapes_host[s].N, &log_n)) return st;
         const he::DegreeOps *ops = he::degree_ops(log_n);
-        if (!ops->has_shape((int)shapes_host[s].log_block, (int)shapes_host[s].log_thread_words))
-            return fail(HE_EUNSUPPORTED, "no kernel with 2^%u words per CTA and 2^%u per thread for N = 2^%d",
-                        shapes_host[s].log_block, shapes_host[s].log_thread_words, log_n);
+        if (shapes_host[s].log_thread_words > 15 || shapes_host[s].ctas_per_sm > 32)
+            return fail(HE_EINVAL, "shape %u: log_thread_words or ctas_per_sm out of range", s);
+        if (!ops->has_shape((int)shapes_host[s].log_block,
+                            thread_words_code(shapes_host[s].log_thread_words, shapes_host[s].ctas_per_sm)))
+            return fail(HE_EUNSUPPORTED,
+                        "no kernel with 2^%u words per CTA, 2^%u per thread and %u CTAs per SM for N = 2^%d",
+                        shapes_host[s].log_block, shapes_host[s].log_thread_words, shapes_host[s].ctas_per_sm, log_n);
     }
     he_plan *plan = new he_plan;
     bool mixed = n_shapes == 0 && !by_degree.empty();
@@ -1623,7 +1638,8 @@ extern "C" he_status he_ntt_plan_create(const he_poly_desc *descs_host, uint32_t
         for (u32 s = 0; s < n_shapes; s++)
             if (shapes_host[s].N == (1u << g.log_n) && shapes_host[s].log_block) {
                 g.log_b = (int)shapes_host[s].log_block;
-                g.log_e = shapes_host[s].log_thread_words ? (int)shapes_host[s].log_thread_words : 4;
+                g.log_e = thread_words_code(shapes_host[s].log_thread_words ? shapes_host[s].log_thread_words : 4,
+                                            shapes_host[s].ctas_per_sm);
                 persistent = shapes_host[s].persistent != 0;
             }
         g.items = (u32)kv.second.size();

@@ -41,7 +41,10 @@ static cudaError_t smem_attr(K kernel, u32 bytes, std::once_flag &flag, cudaErro
     return err;
 }
 
-template <int LOG_B, int LOG_C, int LOG_E = 4>
+// OCC: CTAs per SM of the plain and persistent transform kernels (their
+// register budget; 0 = the shape's default); the other kernels of a shape do
+// not depend on it.
+template <int LOG_B, int LOG_C, int LOG_E = 4, int OCC = 0>
 struct ShapeOps {
     using Sh = NttShape<LOG_B, LOG_C, LOG_E>;
 
@@ -50,8 +53,8 @@ struct ShapeOps {
     {
         static std::once_flag f;
         static cudaError_t e = cudaSuccess;
-        if (cudaError_t r = smem_attr(k_ntt<LOG_B, LOG_C, LOG_E, INV>, Sh::SMEM_BYTES, f, e)) return r;
-        return launch_k(k_ntt<LOG_B, LOG_C, LOG_E, INV>, a.items * Sh::C, Sh::T, Sh::SMEM_BYTES, Sh::C, s, a);
+        if (cudaError_t r = smem_attr(k_ntt<LOG_B, LOG_C, LOG_E, INV, OCC>, Sh::SMEM_BYTES, f, e)) return r;
+        return launch_k(k_ntt<LOG_B, LOG_C, LOG_E, INV, OCC>, a.items * Sh::C, Sh::T, Sh::SMEM_BYTES, Sh::C, s, a);
     }
 
     template <bool INV>
@@ -59,8 +62,8 @@ struct ShapeOps {
     {
         static std::once_flag f;
         static cudaError_t e = cudaSuccess;
-        if (cudaError_t r = smem_attr(k_ntt_persistent<LOG_B, LOG_C, LOG_E, INV>, Sh::SMEM_BYTES, f, e)) return r;
-        return launch_k(k_ntt_persistent<LOG_B, LOG_C, LOG_E, INV>, clusters * Sh::C, Sh::T, Sh::SMEM_BYTES, Sh::C,
+        if (cudaError_t r = smem_attr(k_ntt_persistent<LOG_B, LOG_C, LOG_E, INV, OCC>, Sh::SMEM_BYTES, f, e)) return r;
+        return launch_k(k_ntt_persistent<LOG_B, LOG_C, LOG_E, INV, OCC>, clusters * Sh::C, Sh::T, Sh::SMEM_BYTES, Sh::C,
                         s, a);
     }
 
@@ -88,7 +91,7 @@ struct ShapeOps {
     {
         static std::once_flag f;
         static cudaError_t e = cudaSuccess;
-        if (smem_attr(k_ntt_persistent<LOG_B, LOG_C, LOG_E, INV>, Sh::SMEM_BYTES, f, e) != cudaSuccess) return 0;
+        if (smem_attr(k_ntt_persistent<LOG_B, LOG_C, LOG_E, INV, OCC>, Sh::SMEM_BYTES, f, e) != cudaSuccess) return 0;
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(Sh::C * 1024, 1, 1);
         cfg.blockDim = dim3(Sh::T, 1, 1);
@@ -101,7 +104,7 @@ struct ShapeOps {
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         int n = 0;
-        if (cudaOccupancyMaxActiveClusters(&n, k_ntt_persistent<LOG_B, LOG_C, LOG_E, INV>, &cfg) != cudaSuccess) {
+        if (cudaOccupancyMaxActiveClusters(&n, k_ntt_persistent<LOG_B, LOG_C, LOG_E, INV, OCC>, &cfg) != cudaSuccess) {
             cudaGetLastError();
             return 0;
         }
@@ -156,9 +159,13 @@ struct ShapeOps {
 
 // Shapes built per degree: 2^LB words per CTA (at most 8 CTAs per cluster)
 // and 2^LE words per thread. The first listed is the default (and the one
-// the evaluation kernels use).
+// the evaluation kernels use). Internally a shape's thread-words code is
+// LE | OCC << 4, OCC the CTAs per SM its transform kernels are compiled for
+// (0: the shape's default budget).
 #define HE_SHAPE_FN(LOG_N_, LB, LE)                                                                \
     if (log_b == LB && log_e == LE) return fn(::he::ShapeOps<LB, LOG_N_ - LB, LE>{});
+#define HE_SHAPE_FN_OCC(LOG_N_, LB, LE, OCC)                                                       \
+    if (log_b == LB && log_e == ((LE) | ((OCC) << 4))) return fn(::he::ShapeOps<LB, LOG_N_ - LB, LE, OCC>{});
 
 namespace he {
 
@@ -176,7 +183,7 @@ struct DegreeImpl;
             -> decltype(fn(ShapeOps<DEF_B, LOG_N_ - DEF_B, DEF_E>{}))                              \
         {                                                                                          \
             if (log_b == 0) log_b = DEF_B;                                                         \
-            if (log_e == 0) log_e = DEF_E;                                                         \
+            if ((log_e & 15) == 0) log_e |= DEF_E;                                                 \
             __VA_ARGS__                                                                            \
             return decltype(fn(ShapeOps<DEF_B, LOG_N_ - DEF_B, DEF_E>{}))();                       \
         }                                                                                          \

@@ -80,8 +80,8 @@ __device__ __forceinline__ void prefetch_limb_block(const NttLaunch &a, u32 item
 // One cluster per limb. With a.prefetch = the number of co-resident
 // clusters, limb item + a.prefetch is the one a cluster started about one
 // limb-time from now will take.
-template <int LOG_B, int LOG_C, int LOG_E, bool INV>
-__global__ void __launch_bounds__(NttShape<LOG_B, LOG_C, LOG_E>::T, NttShape<LOG_B, LOG_C, LOG_E>::MIN_CTAS)
+template <int LOG_B, int LOG_C, int LOG_E, bool INV, int OCC = 0>
+__global__ void __launch_bounds__(NttShape<LOG_B, LOG_C, LOG_E>::T, NttShape<LOG_B, LOG_C, LOG_E, OCC>::MIN_CTAS)
 k_ntt(NttLaunch a)
 {
     using Sh = NttShape<LOG_B, LOG_C, LOG_E>;
@@ -99,8 +99,8 @@ k_ntt(NttLaunch a)
 
 // Persistent form: a fixed grid of clusters walks the limbs (job list or
 // uniform batch).
-template <int LOG_B, int LOG_C, int LOG_E, bool INV>
-__global__ void __launch_bounds__(NttShape<LOG_B, LOG_C, LOG_E>::T, NttShape<LOG_B, LOG_C, LOG_E>::MIN_CTAS)
+template <int LOG_B, int LOG_C, int LOG_E, bool INV, int OCC = 0>
+__global__ void __launch_bounds__(NttShape<LOG_B, LOG_C, LOG_E>::T, NttShape<LOG_B, LOG_C, LOG_E, OCC>::MIN_CTAS)
 k_ntt_persistent(NttLaunch a)
 {
     using Sh = NttShape<LOG_B, LOG_C, LOG_E>;

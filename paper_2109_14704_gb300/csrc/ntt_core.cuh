@@ -119,7 +119,9 @@ __device__ __forceinline__ void ld_tw2(const ulonglong2 *tw, int idx, ulonglong2
         : "l"(tw + idx));
 }
 
-template <int LOG_B_, int LOG_C_, int LOG_E_ = 4>
+// OCC_: CTAs per SM the transform kernels are compiled for (their register
+// budget); 0 = the shape's default below.
+template <int LOG_B_, int LOG_C_, int LOG_E_ = 4, int OCC_ = 0>
 struct NttShape {
     static constexpr int LOG_B = LOG_B_;
     static constexpr int LOG_C = LOG_C_;
@@ -146,7 +148,8 @@ struct NttShape {
     // registers, four 256-thread CTAs, beats 128 by 7-18%), even with the
     // few spills these budgets cost
     static constexpr int REGS = LOG_E == 4 ? 64 : 42;
-    static constexpr int MIN_CTAS = (65536 / (int)(T * REGS)) > 0 ? 65536 / (int)(T * REGS) : 1;
+    static constexpr int MIN_CTAS =
+        OCC_ > 0 ? OCC_ : ((65536 / (int)(T * REGS)) > 0 ? 65536 / (int)(T * REGS) : 1);
     // evaluation kernels carry more state per thread: 128 registers
     static constexpr int EVAL_MIN_CTAS = (65536 / (int)(T * 128)) > 0 ? 65536 / (int)(T * 128) : 1;
     // the fused product (three transforms, a second shared-memory block):

@@ -48,7 +48,7 @@ class MrrMultiJob(ctypes.Structure):
 
 class NttShape(ctypes.Structure):
     _fields_ = [("N", ctypes.c_uint32), ("log_block", ctypes.c_uint32), ("log_thread_words", ctypes.c_uint32),
-                ("persistent", ctypes.c_uint32)]
+                ("persistent", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32)]
 
 
 _SIGS = {
@@ -94,7 +94,7 @@ _SIGS = {
     "he_ntt_shapes": (ctypes.c_int32, [ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32), ctypes.c_uint32,
                                        ctypes.POINTER(ctypes.c_uint32)]),
     "he_ntt_set_shape": (ctypes.c_int32, [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
-                                          ctypes.c_uint32]),
+                                          ctypes.c_uint32, ctypes.c_uint32]),
     "he_butterfly_probe": (ctypes.c_int32, [_vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, _vp]),
     "he_butterfly_apply": (ctypes.c_int32, [_vp, _vp, _vp, _vp, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32, _vp]),
     "he_sqr_relin_rescale": (ctypes.c_int32, [_vp, _vp, ctypes.c_uint32, _vp, _vp, ctypes.c_uint32, _vp,
@@ -285,23 +285,24 @@ class NttTables:
             pass
 
 
-def ntt_shapes(N: int) -> list[tuple[int, int]]:
-    """Transform shapes (log_block, log_thread_words) built for degree N,
-    default first."""
+def ntt_shapes(N: int) -> list[tuple[int, int, int]]:
+    """Transform shapes (log_block, log_thread_words, ctas_per_sm) built for
+    degree N, default first (ctas_per_sm 0: the shape's default register
+    budget)."""
     n = ctypes.c_uint32()
-    buf = (ctypes.c_uint32 * 32)()
+    buf = (ctypes.c_uint32 * 48)()
     _check(load().he_ntt_shapes(N, buf, 16, ctypes.byref(n)))
-    return [(buf[2 * i], buf[2 * i + 1]) for i in range(min(n.value, 16))]
+    return [(buf[3 * i], buf[3 * i + 1], buf[3 * i + 2]) for i in range(min(n.value, 16))]
 
 
 FORWARD, INVERSE, BOTH = 1, 2, 0
 
 
 def ntt_set_shape(N: int, log_block: int = 0, log_thread_words: int = 0, persistent: int = 0,
-                  direction: int = BOTH):
+                  direction: int = BOTH, ctas_per_sm: int = 0):
     """Shape used by ntt_fwd (direction 1) / ntt_inv (2) / both (0) at
-    degree N (0, 0, 0 = default)."""
-    _check(load().he_ntt_set_shape(N, direction, log_block, log_thread_words, int(persistent)))
+    degree N (all zero = default)."""
+    _check(load().he_ntt_set_shape(N, direction, log_block, log_thread_words, int(persistent), ctas_per_sm))
 
 
 def _moduli_arg(tables: NttTables, limbs: int, moduli):
@@ -645,8 +646,9 @@ class Encoder:
 
 class NttPlan:
     """he_plan over a list of (tensor, tables, N, limbs, first_prime).
-    `shapes` maps N to log_block, (log_block, log_thread_words) or
-    (log_block, log_thread_words, persistent)."""
+    `shapes` maps N to log_block, (log_block, log_thread_words),
+    (log_block, log_thread_words, persistent) or (log_block,
+    log_thread_words, persistent, ctas_per_sm)."""
 
     def __init__(self, polys, shapes=None):
         arr = (PolyDesc * max(len(polys), 1))()
@@ -661,8 +663,9 @@ class NttPlan:
         shapes = shapes or {}
         sh = (NttShape * max(len(shapes), 1))()
         for i, (N, shape) in enumerate(shapes.items()):
-            lb, le, pe = (shape, 4, 0) if isinstance(shape, int) else (tuple(shape) + (0,))[:3]
+            lb, le, pe, oc = (shape, 4, 0, 0) if isinstance(shape, int) else (tuple(shape) + (0, 0))[:4]
             sh[i].N, sh[i].log_block, sh[i].log_thread_words, sh[i].persistent = N, lb, le, pe
+            sh[i].ctas_per_sm = oc
         h = _vp()
         _check(load().he_ntt_plan_create(arr, len(polys), sh, len(shapes), ctypes.byref(h)))
         self.handle = h

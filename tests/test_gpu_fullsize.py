@@ -30,7 +30,7 @@ def test_uneven_batch_full_size(per_degree):
     xs = [r.uniform_limbs(pool[f:f + L], N) for N, L, f in zip(Ns, Ls, Fs)]
     ds = [torch.from_numpy(x.view(np.int64).copy()).cuda() for x in xs]
     entries = [(ds[i], tables[N], N, L, f) for i, (N, L, f) in enumerate(zip(Ns, Ls, Fs))]
-    shapes = {N: he.ntt_shapes(N)[0] for N in degrees} if per_degree else None
+    shapes = {N: he.ntt_shapes(N)[0][:2] for N in degrees} if per_degree else None
     plan = he.NttPlan(entries, shapes=shapes)
     assert plan.launches == (4 if per_degree else 1)
     plan.fwd()

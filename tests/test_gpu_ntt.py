@@ -72,6 +72,32 @@ def test_ntt_parity_alternate_shapes(log_n, log_b, log_e):
     assert np.array_equal(host(d), x)
 
 
+@pytest.mark.parametrize("log_n", [10, 11, 12, 13, 14, 15, 16])
+def test_ntt_parity_every_tuner_candidate(log_n):
+    """Every candidate the autotuner may apply -- each built shape (words per
+    CTA, words per thread, CTAs per SM) launched as one cluster per limb and
+    as a persistent grid -- through he_ntt_fwd / he_ntt_inv, against the
+    oracle, with a ragged limb count."""
+    N = 1 << log_n
+    qs = _moduli(N, 3)
+    tables = he.NttTables(N, qs)
+    x = np.stack([Rng(700 + log_n + p).uniform_limbs(qs, N) for p in range(3)])
+    ref = [oracle.ntt_fwd(x[p], qs) for p in range(3)]
+    try:
+        for lb, le, occ in he.ntt_shapes(N):
+            for pers in (0, 1):
+                he.ntt_set_shape(N, lb, le, pers, ctas_per_sm=occ)
+                d = dev(x)
+                he.ntt_fwd(d, N, 3, 3, tables)
+                got = host(d)
+                for p in range(3):
+                    assert np.array_equal(got[p], ref[p]), (lb, le, occ, pers, p)
+                he.ntt_inv(d, N, 3, 3, tables)
+                assert np.array_equal(host(d), x), (lb, le, occ, pers)
+    finally:
+        he.ntt_set_shape(N, 0, 0, 0)
+
+
 def test_mixed_degree_plan_single_launch():
     """Uneven batch (N from 2^12 to 2^15, 1 to 16 limbs from a pool of
     50-60-bit primes = 1 mod 2^16) in one launch per direction, with ragged

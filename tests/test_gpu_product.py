@@ -47,9 +47,9 @@ def test_every_shape(log_n):
     shape built for the degree."""
     N = 1 << log_n
     try:
-        for lb, le in he.ntt_shapes(N):
-            he.ntt_set_shape(N, lb, le, direction=he.FORWARD)
-            _check(N, 2, 2, 600 + lb + 7 * le)
+        for lb, le, occ in he.ntt_shapes(N):
+            he.ntt_set_shape(N, lb, le, direction=he.FORWARD, ctas_per_sm=occ)
+            _check(N, 2, 2, 600 + lb + 7 * le + 13 * occ)
     finally:
         he.ntt_set_shape(N, 0, 0, direction=he.FORWARD)
 

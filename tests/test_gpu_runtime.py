@@ -21,7 +21,8 @@ def test_autotune_uniform(tmp_path):
     res = autotune.tune_uniform(N, limbs, count, reps=3, warmup=1, cache_path=cache)
     shapes = he.ntt_shapes(N)
     for d in ("fwd", "inv"):
-        assert tuple(res[d][:2]) in shapes and res[d][2] in (0, 1)
+        lb, le, pers, occ = res[d]
+        assert (lb, le, occ) in shapes and pers in (0, 1)
     assert all(c["ok"] for c in res["candidates"]) and len(res["candidates"]) == 2 * len(shapes)
     assert res["ms_fwd"] == min(c["ms_fwd"] for c in res["candidates"])
     assert res["ms_inv"] == min(c["ms_inv"] for c in res["candidates"])
