@@ -466,6 +466,29 @@ he_status he_encrypt(uint64_t *ct_out, const uint64_t *pt, const uint64_t *pk, c
                      const int8_t *e0, const int8_t *e1, uint32_t count, const he_context *ctx,
                      uint32_t level, void *scratch, size_t scratch_bytes, he_stream_t stream);
 
+/* The encryption randomness drawn on the device (Sec. II-A Encrypt: the
+ * ternary mask v and the errors e0, e1 of each message), count x N signed
+ * 8-bit values each (device). Generator: SplitMix64 in counter form (Steele,
+ * Lea and Flood 2014), output k of stream `seed` = mix(seed + (k + 1) *
+ * 0x9E3779B97F4A7C15) with mix(z): z = (z ^ z >> 30) * 0xBF58476D1CE4E5B9;
+ * z = (z ^ z >> 27) * 0x94D049BB133111EB; z ^ z >> 31. Draw w (0: v, 1: e0,
+ * 2: e1) of message c at coefficient i uses output (3 c + w) N + i, r:
+ * v = (r mod 3) - 1; e = popcount(r & (2^20 - 1)) - popcount((r >> 20) &
+ * (2^20 - 1)), the centred binomial distribution of parameter 20 (variance
+ * 10, |e| <= 20; the paper asks only for Gaussian-distributed errors).
+ * Integer-only, so any implementation of this definition reproduces the
+ * draws bit for bit. HE_EINVAL for a bad degree or NULL pointer. */
+he_status he_sample_encryption_draws(int8_t *v, int8_t *e0, int8_t *e1, uint32_t count, uint32_t N,
+                                     uint64_t seed, he_stream_t stream);
+
+/* he_encrypt with its randomness drawn on the device from `seed`: the same
+ * ciphertexts as he_encrypt given he_sample_encryption_draws(seed)'s draws
+ * (the draws are generated inside the residue kernel, never stored). Same
+ * arguments and checks as he_encrypt otherwise. */
+he_status he_encrypt_seeded(uint64_t *ct_out, const uint64_t *pt, const uint64_t *pk, uint64_t seed,
+                            uint32_t count, const he_context *ctx, uint32_t level, void *scratch,
+                            size_t scratch_bytes, he_stream_t stream);
+
 /* ---- batched plans (Sec. III-B parallelism over limbs and instances) -------- */
 
 /* One polynomial of a batched NTT: `limbs` limbs of degree N at `data`

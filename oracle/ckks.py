@@ -174,12 +174,69 @@ def _mulmod_vec(x: np.ndarray, c: int, q: int) -> np.ndarray:
 
 def encrypt(m_int: np.ndarray, keys: Keys, rng, level: int | None = None) -> np.ndarray:
     """Encrypt (Sec. II-A): c = (v pk0 + m + e0, v pk1 + e1) mod q_L, as
-    [2][L+1][N] in the NTT domain (optionally truncated to `level`)."""
-    mods = keys.data_moduli
+    [2][L+1][N] in the NTT domain (optionally truncated to `level`), with v
+    ternary and e0, e1 rounded Gaussians drawn from `rng`."""
     N = keys.N
-    v = to_residues(rng.ternary(N), mods)
-    e0 = to_residues(rng.gaussian(N), mods)
-    e1 = to_residues(rng.gaussian(N), mods)
+    return encrypt_with_draws(m_int, keys, rng.ternary(N), rng.gaussian(N), rng.gaussian(N), level)
+
+
+# ---- the device's encryption randomness, restated -----------------------------
+# A counter-based generator and two integer mappings, written here from their
+# definitions (SplitMix64: Steele, Lea and Flood, "Fast splittable
+# pseudorandom number generators", 2014; the centred binomial distribution),
+# so that draws made on the device can be reproduced without sharing code.
+
+_GAMMA = 0x9E3779B97F4A7C15
+_M64 = (1 << 64) - 1
+
+
+def splitmix64_outputs(seed: int, counters: np.ndarray) -> np.ndarray:
+    """Output k of the SplitMix64 stream with key `seed`, for every k in
+    `counters` (uint64): z = seed + (k + 1) gamma, then the two xor-shift-
+    multiply steps and a final xor-shift, all mod 2^64."""
+    k = np.asarray(counters, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed & _M64) + (k + np.uint64(1)) * np.uint64(_GAMMA)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+    return z ^ (z >> np.uint64(31))
+
+
+def _popcount(x: np.ndarray) -> np.ndarray:
+    x = x.astype(np.uint64)
+    c = np.zeros(x.shape, dtype=np.int64)
+    for b in range(64):
+        c += ((x >> np.uint64(b)) & np.uint64(1)).astype(np.int64)
+    return c
+
+
+def encryption_draws(seed: int, count: int, N: int):
+    """(v, e0, e1), each int64 [count][N]: draw w (0 v, 1 e0, 2 e1) of message
+    c at coefficient i takes output (3c + w) N + i of the stream: v = r mod 3
+    - 1 (ternary); e = popcount of the low 20 bits minus popcount of the next
+    20 bits (centred binomial, parameter 20, variance 10)."""
+    out = []
+    i = np.arange(N, dtype=np.uint64)
+    for w in range(3):
+        rows = []
+        for c in range(count):
+            r = splitmix64_outputs(seed, np.uint64((3 * c + w) * N) + i)
+            if w == 0:
+                rows.append((r % np.uint64(3)).astype(np.int64) - 1)
+            else:
+                mask = np.uint64((1 << 20) - 1)
+                rows.append(_popcount(r & mask) - _popcount((r >> np.uint64(20)) & mask))
+        out.append(np.stack(rows) if rows else np.zeros((0, N), dtype=np.int64))
+    return tuple(out)
+
+
+def encrypt_with_draws(m_int: np.ndarray, keys: Keys, v_int, e0_int, e1_int, level: int | None = None) -> np.ndarray:
+    """Encrypt (Sec. II-A) with the given mask and errors (integer
+    coefficient vectors): c = (v pk0 + m + e0, v pk1 + e1)."""
+    mods = keys.data_moduli
+    v = to_residues(np.asarray(v_int, dtype=np.int64), mods)
+    e0 = to_residues(np.asarray(e0_int, dtype=np.int64), mods)
+    e1 = to_residues(np.asarray(e1_int, dtype=np.int64), mods)
     m = to_residues(m_int, mods)
     v_ntt = _o.ntt_fwd(v, mods)
     c0 = _o.dyadic(v_ntt, keys.pk[0], mods)

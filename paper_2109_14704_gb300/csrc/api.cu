@@ -1390,15 +1390,16 @@ extern "C" size_t he_encrypt_scratch_bytes(const he_context *ctx, uint32_t level
     return ctx ? (size_t)count * 3 * (level + 1) * ctx->N * 8 : 0;
 }
 
-extern "C" he_status he_encrypt(uint64_t *ct_out, const uint64_t *pt, const uint64_t *pk, const int8_t *v,
-                                const int8_t *e0, const int8_t *e1, uint32_t count, const he_context *ctx,
-                                uint32_t level, void *scratch, size_t scratch_bytes, he_stream_t stream)
+// Encryption with the draws given (v non-NULL) or generated from `seed`.
+static he_status encrypt_common(uint64_t *ct_out, const uint64_t *pt, const uint64_t *pk, const int8_t *v,
+                                const int8_t *e0, const int8_t *e1, uint64_t seed, uint32_t count,
+                                const he_context *ctx, uint32_t level, void *scratch, size_t scratch_bytes,
+                                he_stream_t stream)
 {
     if (he_status s = check_level(ctx, level, false)) return s;
     if (he_status s = check_ptr(ct_out, "ct_out")) return s;
     if (he_status s = check_ptr(pt, "pt")) return s;
     if (he_status s = check_ptr(pk, "pk")) return s;
-    if (!v || !e0 || !e1) return fail(HE_EINVAL, "v, e0 or e1 is NULL");
     if (count == 0) return HE_OK;
     if (he_status s = check_ptr(scratch, "scratch")) return s;
     if (scratch_bytes < he_encrypt_scratch_bytes(ctx, level, count)) return fail(HE_EINVAL, "scratch too small");
@@ -1407,12 +1408,46 @@ extern "C" he_status he_encrypt(uint64_t *ct_out, const uint64_t *pt, const uint
     cudaStream_t s = (cudaStream_t)stream;
     u64 *noise = (u64 *)scratch;
     const u64 words = (u64)count * 3 * n * ctx->N;
-    he::k_enc_noise<<<stream_grid(words, 256), 256, 0, s>>>(noise, v, e0, e1, (u32)ctx->log_n, n, count,
-                                                             ctx->tables->d_pc);
+    if (v)
+        he::k_enc_noise<<<stream_grid(words, 256), 256, 0, s>>>(noise, v, e0, e1, (u32)ctx->log_n, n, count,
+                                                                 ctx->tables->d_pc);
+    else
+        he::k_enc_noise_seeded<<<stream_grid(words, 256), 256, 0, s>>>(noise, seed, (u32)ctx->log_n, n, count,
+                                                                        ctx->tables->d_pc);
     HE_CUDA(cudaGetLastError());
     if (he_status r = ntt_launch(uniform_launch(noise, n, 3 * count, ctx->tables), ctx->log_n, false, s)) return r;
     he::k_enc_combine<<<stream_grid((u64)count * n * ctx->N, 256), 256, 0, s>>>(
         ct_out, noise, pt, pk, (u32)ctx->log_n, n, count, ctx->n_data, ctx->tables->d_pc);
+    HE_CUDA(cudaGetLastError());
+    return HE_OK;
+}
+
+extern "C" he_status he_encrypt(uint64_t *ct_out, const uint64_t *pt, const uint64_t *pk, const int8_t *v,
+                                const int8_t *e0, const int8_t *e1, uint32_t count, const he_context *ctx,
+                                uint32_t level, void *scratch, size_t scratch_bytes, he_stream_t stream)
+{
+    if (!v || !e0 || !e1) return fail(HE_EINVAL, "v, e0 or e1 is NULL");
+    return encrypt_common(ct_out, pt, pk, v, e0, e1, 0, count, ctx, level, scratch, scratch_bytes, stream);
+}
+
+extern "C" he_status he_encrypt_seeded(uint64_t *ct_out, const uint64_t *pt, const uint64_t *pk, uint64_t seed,
+                                       uint32_t count, const he_context *ctx, uint32_t level, void *scratch,
+                                       size_t scratch_bytes, he_stream_t stream)
+{
+    return encrypt_common(ct_out, pt, pk, nullptr, nullptr, nullptr, seed, count, ctx, level, scratch, scratch_bytes,
+                          stream);
+}
+
+extern "C" he_status he_sample_encryption_draws(int8_t *v, int8_t *e0, int8_t *e1, uint32_t count, uint32_t N,
+                                                uint64_t seed, he_stream_t stream)
+{
+    int log_n;
+    if (he_status s = check_degree(N, &log_n)) return s;
+    if (!v || !e0 || !e1) return fail(HE_EINVAL, "v, e0 or e1 is NULL");
+    if (count == 0) return HE_OK;
+    if ((u64)count * N > (1ull << 40)) return fail(HE_EINVAL, "batch too large");
+    he::k_enc_draws<<<stream_grid((u64)count * N, 256), 256, 0, (cudaStream_t)stream>>>(v, e0, e1, seed,
+                                                                                        (u32)log_n, count);
     HE_CUDA(cudaGetLastError());
     return HE_OK;
 }

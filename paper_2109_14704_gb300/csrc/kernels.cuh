@@ -495,6 +495,58 @@ __global__ void k_enc_noise(u64 *out, const int8_t *v, const int8_t *e0, const i
     }
 }
 
+// Randomness of encryption drawn on the device (Sec. II-A Encrypt: a
+// uniform ternary mask v and Gaussian-like errors e0, e1). Generator:
+// SplitMix64 in counter form (Steele, Lea and Flood 2014): output k of the
+// stream with key `seed` is mix(seed + (k + 1) * 0x9E3779B97F4A7C15), with
+// mix(z): z = (z ^ z >> 30) * 0xBF58476D1CE4E5B9; z = (z ^ z >> 27) *
+// 0x94D049BB133111EB; z ^ z >> 31. Draw w (0: v, 1: e0, 2: e1) of message c
+// at coefficient i uses output k = (3 c + w) N + i:
+//   v  = (r mod 3) - 1                        (bias below 2^-63)
+//   e  = popcount(r & (2^20 - 1)) - popcount((r >> 20) & (2^20 - 1)),
+// the centred binomial distribution of parameter 20 (variance 10, standard
+// deviation 3.16, |e| <= 20): integer-only, so that any implementation
+// following this definition reproduces the draws bit for bit.
+__device__ __forceinline__ u64 splitmix64_at(u64 seed, u64 k)
+{
+    u64 z = seed + (k + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ int enc_draw(u64 seed, u32 w, u64 c, u64 i, u32 log_n)
+{
+    const u64 r = splitmix64_at(seed, ((3 * c + w) << log_n) + i);
+    if (w == 0) return (int)(r % 3u) - 1;
+    return __popcll(r & 0xFFFFFull) - __popcll((r >> 20) & 0xFFFFFull);
+}
+
+// The draws themselves, as signed 8-bit values [count][N] each.
+__global__ void k_enc_draws(int8_t *v, int8_t *e0, int8_t *e1, u64 seed, u32 log_n, u32 count)
+{
+    const u64 N = 1ull << log_n, total = (u64)count * N;
+    for (u64 e = (u64)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (u64)gridDim.x * blockDim.x) {
+        const u64 c = e >> log_n, i = e & (N - 1);
+        v[e] = (int8_t)enc_draw(seed, 0, c, i, log_n);
+        e0[e] = (int8_t)enc_draw(seed, 1, c, i, log_n);
+        e1[e] = (int8_t)enc_draw(seed, 2, c, i, log_n);
+    }
+}
+
+// As k_enc_noise, with the draws generated in place from the seed.
+__global__ void k_enc_noise_seeded(u64 *out, u64 seed, u32 log_n, u32 n, u32 count, const PrimeConst *pcs)
+{
+    const u64 N = 1ull << log_n, words = (u64)count * 3 * n * N;
+    for (u64 e = (u64)blockIdx.x * blockDim.x + threadIdx.x; e < words; e += (u64)gridDim.x * blockDim.x) {
+        const u64 i = e & (N - 1), row = e >> log_n;
+        const u32 l = (u32)(row % n), w = (u32)((row / n) % 3);
+        const u64 c = row / (3 * (u64)n);
+        const int x = enc_draw(seed, w, c, i, log_n);
+        out[e] = x >= 0 ? (u64)x : pcs[l].p - (u64)(-x);
+    }
+}
+
 // Public-key encryption (Sec. II-A) from the transformed randomness:
 // c0 = v pk0 + pt + e0, c1 = v pk1 + e1 (NTT domain, limb by limb).
 // noise [count][3][n][N] (v, e0, e1 transformed), pt [count][n][N],

@@ -127,6 +127,10 @@ _SIGS = {
     "he_negacyclic_mul": (ctypes.c_int32, [_vp, _vp, _vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, _u64p,
                                            _vp, _vp]),
     "he_encrypt_scratch_bytes": (ctypes.c_size_t, [_vp, ctypes.c_uint32, ctypes.c_uint32]),
+    "he_sample_encryption_draws": (ctypes.c_int32, [_vp, _vp, _vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64,
+                                                    _vp]),
+    "he_encrypt_seeded": (ctypes.c_int32, [_vp, _vp, _vp, ctypes.c_uint64, ctypes.c_uint32, _vp, ctypes.c_uint32, _vp,
+                                           ctypes.c_size_t, _vp]),
     "he_encrypt": (ctypes.c_int32, [_vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_uint32, _vp, ctypes.c_uint32, _vp,
                                     ctypes.c_size_t, _vp]),
     "he_mul_relin_rescale_batch_scratch_bytes": (ctypes.c_size_t, [_vp, ctypes.POINTER(MrrJob), ctypes.c_uint32]),
@@ -502,6 +506,22 @@ def encrypt(ct_out, pt, pk, v, e0, e1, count: int, ctx: Context, level: int, scr
     _check(load().he_encrypt(_ptr(ct_out, count * 2 * n * N), _ptr(pt, count * n * N), _ptr(pk, 2 * ctx.n_data * N),
                              _i8ptr(v, count * N), _i8ptr(e0, count * N), _i8ptr(e1, count * N), count, ctx.handle,
                              level, _ptr(scratch), scratch.numel() * 8, _stream(stream)))
+
+
+def sample_encryption_draws(v, e0, e1, count: int, N: int, seed: int, stream=None):
+    """The encryption randomness drawn on the device from `seed` (int8
+    tensors [count][N]: ternary mask, two centred-binomial errors)."""
+    _check(load().he_sample_encryption_draws(_i8ptr(v, count * N), _i8ptr(e0, count * N), _i8ptr(e1, count * N),
+                                             count, N, seed & ((1 << 64) - 1), _stream(stream)))
+
+
+def encrypt_seeded(ct_out, pt, pk, seed: int, count: int, ctx: Context, level: int, scratch, stream=None):
+    """Public-key encryption with the randomness drawn on the device from
+    `seed` (the draws of sample_encryption_draws)."""
+    N, n = ctx.N, level + 1
+    _check(load().he_encrypt_seeded(_ptr(ct_out, count * 2 * n * N), _ptr(pt, count * n * N),
+                                    _ptr(pk, 2 * ctx.n_data * N), seed & ((1 << 64) - 1), count, ctx.handle, level,
+                                    _ptr(scratch), scratch.numel() * 8, _stream(stream)))
 
 
 # Jobs of a mixed-level batch that one pass of he_mul_relin_rescale_batch takes.

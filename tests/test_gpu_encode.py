@@ -293,3 +293,47 @@ def test_device_ckks_pipeline():
                empty(enc.decode_scratch_bytes(L - 1, 1) // 8))
     exact = za * zb
     assert _err(z.cpu().numpy()[0], exact) < 1e-5
+
+
+@pytest.mark.parametrize("N,count,seed", [(4096, 3, 1), (32768, 2, 0xFFFFFFFFFFFFFFFF), (1024, 5, 77)])
+def test_device_sampled_draws_match_oracle(N, count, seed):
+    """The encryption randomness drawn on the device (SplitMix64 counter
+    form, ternary mask, centred-binomial errors) equals the oracle's
+    restatement of the same definition bit for bit."""
+    v, e0, e1 = (torch.empty((count, N), dtype=torch.int8, device="cuda") for _ in range(3))
+    he.sample_encryption_draws(v, e0, e1, count, N, seed)
+    ref = ckks.encryption_draws(seed, count, N)
+    for got, want in zip((v, e0, e1), ref):
+        torch.cuda.synchronize()
+        assert np.array_equal(got.cpu().numpy().astype(np.int64), want)
+
+
+@pytest.mark.parametrize("level", [3, 1])
+def test_encrypt_seeded_matches_oracle(level):
+    """Encryption with the randomness drawn on the device equals the oracle's
+    encryption with the oracle's draws for the same seed, bit for bit, and
+    decrypts to the message (the errors are small)."""
+    N, data, ctx, enc = _setup("n4k")
+    keys = ckks.keygen(N, data, ctx.P, Rng(930))
+    qs = data[:level + 1]
+    count, seed = 3, 0x1234_5678_9ABC_DEF0
+    m = [ckks.encode_real(Rng(931 + c).complex_slots(N // 2), N, 2.0 ** 40) for c in range(count)]
+    v, e0, e1 = ckks.encryption_draws(seed, count, N)
+    ref = [ckks.encrypt_with_draws(m[c], keys, v[c], e0[c], e1[c], level) for c in range(count)]
+    pt = dev(np.stack([oracle.ntt_fwd(ckks.to_residues(m[c], qs), qs) for c in range(count)]))
+    ct = empty(count, 2, level + 1, N)
+    he.encrypt_seeded(ct, pt, dev(keys.pk), seed, count, ctx, level,
+                      empty(ctx.encrypt_scratch_bytes(level, count) // 8))
+    got = host(ct)
+    for c in range(count):
+        assert np.array_equal(got[c], ref[c]), c
+        # m' - m = v e + e0 + e1 s: far below the scale
+        diff = ckks.crt_centered(ckks.decrypt_residues(got[c], keys), qs) - np.asarray(m[c], dtype=object)
+        assert max(abs(int(x)) for x in diff) < 2 ** 20
+    # the same seed through he_sample_encryption_draws + he_encrypt
+    dv, d0, d1 = (torch.empty((count, N), dtype=torch.int8, device="cuda") for _ in range(3))
+    he.sample_encryption_draws(dv, d0, d1, count, N, seed)
+    ct2 = empty(count, 2, level + 1, N)
+    he.encrypt(ct2, pt, dev(keys.pk), dv, d0, d1, count, ctx, level,
+               empty(ctx.encrypt_scratch_bytes(level, count) // 8))
+    assert np.array_equal(host(ct2), got)
