@@ -56,6 +56,19 @@ __device__ __forceinline__ u32 swz<3>(u32 l)
     return l ^ (((r ^ ((r >> 1) << 2)) * 9u) & 15u);
 }
 
+// threadIdx.x, with the launch's block size made known to the compiler: the
+// transforms always run T = B / E threads a CTA, so round 0's group index
+// (tid >> log2 T) folds to 0 and its twiddle addresses become CTA-uniform.
+// Used by the inverse transform, where it measured 1.5 % faster (the forward
+// transform measured 2 % slower with it).
+template <u32 T>
+__device__ __forceinline__ u32 thread_index()
+{
+    const u32 t = threadIdx.x;
+    __builtin_assume(t < T);
+    return t;
+}
+
 __device__ __forceinline__ u32 cluster_ctarank()
 {
     u32 r;
@@ -527,7 +540,7 @@ template <class Sh, bool HAVE_X, class Load, class Store>
 __device__ __forceinline__ void ntt_inv_block(u64 *s, u32 m, u32 rbase, const ulonglong2 *tw, const PrimeConst &pc,
                                               Load load, Store store, u64 (&x)[Sh::E])
 {
-    const u32 tid = threadIdx.x;
+    const u32 tid = thread_index<Sh::T>();
     if constexpr (!HAVE_X) {
 #pragma unroll
         for (int e = 0; e < Sh::E; e++) x[e] = load(last_pos<Sh>(m, tid, e));
