@@ -51,7 +51,10 @@ METRIC = "NTT limbs/s at N=2^15 + HE mul-relin-rescale/s, batched vs plain; p99 
 # an ncu capture of the same kernel on 256 instances scaled by 4 (traffic
 # grows in proportion to the limbs). Entries are removed when the kernel
 # changes after their capture, so that no stale figure is reported.
-TRAFFIC = {}
+TRAFFIC = {
+    ("forward", (12, 4, 0, 0)): 4 * (542013952 + 482040320),
+    ("inverse", (12, 4, 0, 0)): 4 * (544009728 + 477379328),
+}
 # The production forward butterfly keeps the IMAD (fmaheavy) pipe busy for
 # 0.2536 cycles per butterfly per SM: ncu on the register-resident probe
 # (1216 x 256 threads x 16 x 1024 butterflies) counts that pipe 94.2 % active
@@ -73,7 +76,7 @@ def _args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle sample")
-    ap.add_argument("--profile-case", choices=["ntt", "mrr", "probe", "encode", "product"],
+    ap.add_argument("--profile-case", choices=["ntt", "mrr", "mrr_multi", "probe", "encode", "product"],
                     help="run one small case of a kernel family and exit (for profilers)")
     ap.add_argument("--instances", type=int, default=64,
                     help="NTT instances of --profile-case ntt, ciphertext pairs of --profile-case mrr")
@@ -1084,6 +1087,30 @@ def profile_case(args):
             ctx.set_eval_shape(int(args.shape))
         for _ in range(args.steps):
             he.mul_relin_rescale(out, ca, cb, count, key, ctx, L, scratch)
+    elif args.profile_case == "mrr_multi":
+        # the serving mix as one multi-degree batch: 16 jobs, N cycling over
+        # 2^13, 2^14, 2^15, levels drawn from 2..16, args.instances pairs each
+        rm = Rng(3)
+        ctxs, keys = {}, {}
+        for N in (8192, 16384, 32768):
+            data, P = he.chain_primes(N, [60] + [50] * 16, 60)
+            ctxs[N] = he.Context(N, data, P)
+            evk = np.stack([np.stack([rm.uniform_limbs(data + [P], N) for _ in range(2)]) for _ in range(17)])
+            keys[N] = he.RelinKey(ctxs[N], evk)
+        levels = [int(v) for v in rm.choice(list(range(2, 17)), 16)]
+        jobs = []
+        for j, lv in enumerate(levels):
+            N = (8192, 16384, 32768)[j % 3]
+            ctx = ctxs[N]
+            qs = ctx.data_moduli[:lv + 1]
+            mk = lambda: torch.from_numpy(np.stack([np.stack([rm.uniform_limbs(qs, N) for _ in range(2)])
+                                                     for _ in range(args.instances)]).view(np.int64)).to(dev)
+            out = torch.empty((args.instances, 2, lv, N), dtype=torch.int64, device=dev)
+            jobs.append((out, mk(), mk(), args.instances, lv, keys[N], ctx))
+        scratch = torch.empty(he.mul_relin_rescale_multi_scratch_bytes([(j[3], j[4], j[5], j[6]) for j in jobs]) // 8,
+                              dtype=torch.int64, device=dev)
+        for _ in range(args.steps):
+            he.mul_relin_rescale_multi(jobs, scratch)
     elif args.profile_case == "product":
         N = 1 << NTT_LOG_N
         qs = _ntt_moduli()
