@@ -17,7 +17,8 @@
  *           overflow a 64-bit word).
  * Layout.   Limb-major and contiguous: a polynomial with L limbs is
  *           poly[l * N + i]; a ciphertext with n limbs and c components is
- *           ct[(k * n + l) * N + i]. Device buffers must be 16-byte aligned.
+ *           ct[(k * n + l) * N + i]. Device buffers must be 32-byte aligned
+ *           (the transforms move runs of words with 256-bit accesses).
  * Domains.  Ciphertexts and keys are in the NTT domain, in the bit-reversed
  *           evaluation order of he_ntt_fwd.
  * Ranges.   Inputs must be canonical (in [0, q)); outputs are always
@@ -199,7 +200,7 @@ he_status he_ct_mul(uint64_t *out3, const uint64_t *ct_a, const uint64_t *ct_b,
  * c[2] split into its RNS digits [c[2]]_{q_j} in [0, q_j) and the division by
  * P rounded half up. ct_in3 is [3][l+1][N], ct_out2 is [2][l+1][N].
  *
- * Scratch (device, 16-byte aligned, contents irrelevant) of key switching,
+ * Scratch (device, 32-byte aligned, contents irrelevant) of key switching,
  * with n = l + 1 limbs: at least (3 n + 2) N words (Relin) or
  * (3 n + 4) N words per pair (MulLinRS); then the mod-up runs as one fused
  * kernel per (ciphertext, target prime). With room for (n + 1) n N more
@@ -349,7 +350,7 @@ size_t he_mul_relin_rescale_batch_scratch_bytes(const he_context *ctx, const he_
  * kernels read a table of the jobs (at most 16 per pass; more jobs take
  * further passes) and map each CTA or thread to its job. Jobs may have
  * different levels and counts; jobs with count 0 are skipped. Outputs must
- * not overlap inputs or each other. scratch: device, 16-byte aligned,
+ * not overlap inputs or each other. scratch: device, 32-byte aligned,
  * he_mul_relin_rescale_batch_scratch_bytes. HE_EINVAL for a bad level (< 1
  * or beyond the chain), pointer, key, short scratch, or a batch whose item
  * count exceeds the launch limits. */
@@ -388,7 +389,7 @@ size_t he_mul_relin_rescale_multi_scratch_bytes(const he_mrr_multi_job *jobs_hos
  * 16 jobs per pass, more take further passes. The transform stages run
  * clusters of 8 CTAs of 2^12 words, each holding 8 >> c items of a job of
  * degree 2^(12 + c). Outputs must not overlap inputs or each other.
- * scratch: device, 16-byte aligned, he_mul_relin_rescale_multi_scratch_bytes.
+ * scratch: device, 32-byte aligned, he_mul_relin_rescale_multi_scratch_bytes.
  * HE_EINVAL for a bad context, key, level (< 1 or beyond the chain),
  * pointer, short scratch, or a batch beyond the launch limits. */
 he_status he_mul_relin_rescale_multi(const he_mrr_multi_job *jobs_host, uint32_t n_jobs, void *scratch,
@@ -443,7 +444,7 @@ he_status he_decode(const he_encoder *enc, double *slots_out, const uint64_t *pt
  * (round to nearest even) of the centred integer whose residues modulo
  * q_0..q_level are coeffs[(c * (level + 1) + l) * N + i] (coefficient
  * domain, canonical). out and coeffs are device buffers, 8-byte aligned
- * and 16-byte aligned respectively. */
+ * and 32-byte aligned respectively. */
 he_status he_crt_compose(const he_encoder *enc, double *out, const uint64_t *coeffs, uint32_t count,
                          uint32_t level, he_stream_t stream);
 
@@ -550,7 +551,7 @@ uint32_t he_plan_launches(const he_plan *plan);
  * the device-to-host copy of a third run at the same time (the paper's
  * asynchronous pipeline: transfers and kernels queued without host
  * synchronisation, over several queues).
- *   work / work_bytes: device scratch owned by the caller, 16-byte aligned,
+ *   work / work_bytes: device scratch owned by the caller, 32-byte aligned,
  *     room for at least one polynomial (limbs * N * 8 bytes); more room
  *     (e.g. 4 x 32 polynomials) gives larger chunks and full overlap.
  *   in_host, out_host: equal (in place) or disjoint, count * limbs * N

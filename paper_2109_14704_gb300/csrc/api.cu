@@ -322,7 +322,7 @@ static he_status check_poly_args(const void *poly, uint32_t N, uint32_t limbs, c
             return fail(HE_EINVAL, "modulus %u (%llu) differs from the tables' prime (%llu)", l,
                         (unsigned long long)moduli_host[l], (unsigned long long)tw->moduli[l]);
     if (!poly) return fail(HE_EINVAL, "data pointer is NULL");
-    if ((uintptr_t)poly & 15) return fail(HE_EINVAL, "data pointer is not 16-byte aligned");
+    if ((uintptr_t)poly & 31) return fail(HE_EINVAL, "data pointer is not 32-byte aligned");
     return HE_OK;
 }
 
@@ -493,8 +493,8 @@ extern "C" he_status he_dyadic_mul(uint64_t *out, const uint64_t *a, const uint6
 {
     int log_n;
     if (he_status s = check_poly_args(out, N, limbs, moduli_host, tw, &log_n)) return s;
-    if (!a || !b || ((uintptr_t)a & 15) || ((uintptr_t)b & 15))
-        return fail(HE_EINVAL, "inputs must be non-NULL and 16-byte aligned");
+    if (!a || !b || ((uintptr_t)a & 31) || ((uintptr_t)b & 31))
+        return fail(HE_EINVAL, "inputs must be non-NULL and 32-byte aligned");
     const u64 items = (u64)limbs * count;
     if (!items) return HE_OK;
     he::k_dyadic<<<stream_grid(items * N / 2, 256), 256, 0, (cudaStream_t)stream>>>(
@@ -509,8 +509,8 @@ extern "C" he_status he_negacyclic_mul(uint64_t *c, const uint64_t *a, const uin
 {
     int log_n;
     if (he_status s = check_poly_args(c, N, limbs, moduli_host, tw, &log_n)) return s;
-    if (!a || !b || ((uintptr_t)a & 15) || ((uintptr_t)b & 15))
-        return fail(HE_EINVAL, "inputs must be non-NULL and 16-byte aligned");
+    if (!a || !b || ((uintptr_t)a & 31) || ((uintptr_t)b & 31))
+        return fail(HE_EINVAL, "inputs must be non-NULL and 32-byte aligned");
     const u64 items = (u64)limbs * count;
     if (!items) return HE_OK;
     if (items * (N / 4096 + 1) > 0x7fffffffull) return fail(HE_EINVAL, "batch too large");
@@ -687,7 +687,7 @@ static he::DevCtx dev_ctx(const he_context *c)
 static he_status check_ptr(const void *p, const char *name)
 {
     if (!p) return fail(HE_EINVAL, "%s is NULL", name);
-    if ((uintptr_t)p & 15) return fail(HE_EINVAL, "%s is not 16-byte aligned", name);
+    if ((uintptr_t)p & 31) return fail(HE_EINVAL, "%s is not 32-byte aligned", name);
     return HE_OK;
 }
 
@@ -1604,8 +1604,8 @@ extern "C" he_status he_ntt_plan_create(const he_poly_desc *descs_host, uint32_t
         if ((u64)d.first_prime + d.limbs > d.tables->K)
             return fail(HE_EINVAL, "descriptor %u: primes %u..%u beyond the tables' %u", i, d.first_prime,
                         d.first_prime + d.limbs, d.tables->K);
-        if (d.limbs && (!d.data || ((uintptr_t)d.data & 15)))
-            return fail(HE_EINVAL, "descriptor %u: data NULL or not 16-byte aligned", i);
+        if (d.limbs && (!d.data || ((uintptr_t)d.data & 31)))
+            return fail(HE_EINVAL, "descriptor %u: data NULL or not 32-byte aligned", i);
         for (u32 l = 0; l < d.limbs; l++) {
             he::LimbJob j;
             const u32 pr = d.first_prime + l;

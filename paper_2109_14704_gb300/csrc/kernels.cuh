@@ -13,7 +13,7 @@ namespace he {
 
 // Forward or inverse transform of one limb stored at `data` (in place). The
 // forward transform's last round and the inverse transform's first round
-// give each thread runs of consecutive words, which move as 16-byte pairs
+// give each thread runs of consecutive words, which move as 32-byte quarters
 // (streaming cache hints: every word is read and written once per launch);
 // the cross-CTA columns move as single coalesced words. Stores are skipped
 // when !valid (idle sub-clusters of the mixed-degree kernel).
@@ -29,16 +29,13 @@ __device__ __forceinline__ void ntt_limb(u64 *smem, u32 m, u32 rbase, u64 *data,
         ntt_fwd_block<Sh>(smem, m, rbase, tw, pc, ld, nost, x);
         if (valid) {
 #pragma unroll
-            for (int e = 0; e < Sh::E; e += 2)
-                __stcs(reinterpret_cast<ulonglong2 *>(data + last_pos<Sh>(m, tid, e)), make_ulonglong2(x[e], x[e + 1]));
+            for (int e = 0; e < Sh::E; e += 4)
+                st4_cs(data + last_pos<Sh>(m, tid, e), x[e], x[e + 1], x[e + 2], x[e + 3]);
         }
     } else {
 #pragma unroll
-        for (int e = 0; e < Sh::E; e += 2) {
-            const ulonglong2 v = __ldcs(reinterpret_cast<const ulonglong2 *>(data + last_pos<Sh>(m, tid, e)));
-            x[e] = v.x;
-            x[e + 1] = v.y;
-        }
+        for (int e = 0; e < Sh::E; e += 4)
+            ld4_cs(data + last_pos<Sh>(m, tid, e), x[e], x[e + 1], x[e + 2], x[e + 3]);
         auto nold = [&](u32) -> u64 { return 0; };
         auto st = [&](int P, u64 v) {
             if (valid) __stcs(reinterpret_cast<unsigned long long *>(data + P), (unsigned long long)v);
@@ -605,33 +602,29 @@ __device__ __forceinline__ u64 lazy_sub(u64 a, u64 x, u64 twelve_p) { return a +
 
 // Epilogue of a lazy forward transform (ntt_fwd_block with CANON = false):
 //   r(e) = (src[P] - x[e]) C mod p,  P = last_pos(e),  C' = Shoup(C),
-// for every word the thread holds, into x. Positions e and e + 1 of the last
-// round are consecutive and 16-byte aligned, so src moves as 16-byte pairs,
-// all of them loaded before the caller stores anything (src may be the
-// output: with alternating loads and stores each store would evict lines
-// the next loads need).
+// for every word the thread holds, into x. Positions e .. e + 3 (e = 0 mod
+// 4) of the last round are consecutive and 32-byte aligned, so src moves in
+// 32-byte quarters, all of them loaded before the caller stores anything
+// (src may be the output: with alternating loads and stores each store
+// would evict lines the next loads need).
 template <class Sh>
-__device__ __forceinline__ void sub_scale_pairs(u64 (&x)[Sh::E], const u64 *src, u64 C, u64 C_sh,
-                                                const PrimeConst &pc, u32 m, u32 tid)
+__device__ __forceinline__ void sub_scale_run(u64 (&x)[Sh::E], const u64 *src, u64 C, u64 C_sh,
+                                              const PrimeConst &pc, u32 m, u32 tid)
 {
     const u64 twelve_p = 3 * pc.four_p;
-    ulonglong2 v[Sh::E / 2];
+    u64 v[Sh::E];
 #pragma unroll
-    for (int e = 0; e < Sh::E; e += 2) v[e / 2] = *reinterpret_cast<const ulonglong2 *>(src + last_pos<Sh>(m, tid, e));
+    for (int e = 0; e < Sh::E; e += 4) ld4(src + last_pos<Sh>(m, tid, e), v[e], v[e + 1], v[e + 2], v[e + 3]);
 #pragma unroll
-    for (int e = 0; e < Sh::E; e += 2) {
-        x[e] = mul_shoup(lazy_sub(v[e / 2].x, x[e], twelve_p), C, C_sh, pc.p);
-        x[e + 1] = mul_shoup(lazy_sub(v[e / 2].y, x[e + 1], twelve_p), C, C_sh, pc.p);
-    }
+    for (int e = 0; e < Sh::E; e++) x[e] = mul_shoup(lazy_sub(v[e], x[e], twelve_p), C, C_sh, pc.p);
 }
 
-// x[] to dst at the thread's last-round positions, as 16-byte pairs.
+// x[] to dst at the thread's last-round positions, in 32-byte quarters.
 template <class Sh>
-__device__ __forceinline__ void store_pairs(u64 *dst, const u64 (&x)[Sh::E], u32 m, u32 tid)
+__device__ __forceinline__ void store_run(u64 *dst, const u64 (&x)[Sh::E], u32 m, u32 tid)
 {
 #pragma unroll
-    for (int e = 0; e < Sh::E; e += 2)
-        *reinterpret_cast<ulonglong2 *>(dst + last_pos<Sh>(m, tid, e)) = make_ulonglong2(x[e], x[e + 1]);
+    for (int e = 0; e < Sh::E; e += 4) st4(dst + last_pos<Sh>(m, tid, e), x[e], x[e + 1], x[e + 2], x[e + 3]);
 }
 
 // Read-only load (the kernel never writes what it reads through this).
@@ -699,6 +692,32 @@ struct DSource {
         r.y = mul_mod(a.y, b.y, pc);
         return r;
     }
+    // d_k at the four positions P .. P + 3 (P = 0 mod 4) into r[0..3], from
+    // 32-byte loads.
+    __device__ __forceinline__ void d4(int k, u32 limb, u32 log_n, u32 P, const PrimeConst &pc, u64 *r) const
+    {
+        const size_t off = ((size_t)limb << log_n) + P;
+        if (ct3) {
+            ld4_nc(ct3 + k * per + off, r[0], r[1], r[2], r[3]);
+            return;
+        }
+        u64 a[4], b[4];
+        if (k == 1) {
+            u64 a1[4], b1[4];
+            ld4_nc(ct_a + off, a[0], a[1], a[2], a[3]);
+            ld4_nc(ct_b + per + off, b1[0], b1[1], b1[2], b1[3]);
+            ld4_nc(ct_a + per + off, a1[0], a1[1], a1[2], a1[3]);
+            ld4_nc(ct_b + off, b[0], b[1], b[2], b[3]);
+#pragma unroll
+            for (int i = 0; i < 4; i++) r[i] = mad2_mod(a[i], b1[i], a1[i], b[i], pc);
+            return;
+        }
+        const size_t o = (k == 0) ? off : per + off;
+        ld4_nc(ct_a + o, a[0], a[1], a[2], a[3]);
+        ld4_nc(ct_b + o, b[0], b[1], b[2], b[3]);
+#pragma unroll
+        for (int i = 0; i < 4; i++) r[i] = mul_mod(a[i], b[i], pc);
+    }
 };
 
 __device__ __forceinline__ DSource dsource(const EvalArgs &a, u32 c)
@@ -729,13 +748,9 @@ __device__ __forceinline__ void ks_digits_body(const EvalArgs &a, u32 item, u32 
     u64 *out = a.c2 + ((size_t)c * a.n + j) * Sh::N;
     const u32 tid = threadIdx.x;
     u64 x[Sh::E];
-    // d2 at the thread's inverse-input positions (consecutive pairs)
+    // d2 at the thread's inverse-input positions (consecutive quarters)
 #pragma unroll
-    for (int e = 0; e < Sh::E; e += 2) {
-        const ulonglong2 v = ds.d2(2, j, Sh::LOG_N, (u32)last_pos<Sh>(m, tid, e), pc);
-        x[e] = v.x;
-        x[e + 1] = v.y;
-    }
+    for (int e = 0; e < Sh::E; e += 4) ds.d4(2, j, Sh::LOG_N, (u32)last_pos<Sh>(m, tid, e), pc, x + e);
     auto nold = [&](u32) -> u64 { return 0; };
     auto st = [&](u32 P, u64 v) {
         if (valid) out[P] = v;
@@ -868,11 +883,7 @@ __device__ __forceinline__ void ks_expand_body(const EvalArgs &a, u32 g, u32 t, 
         auto ld = [&](int P) -> u64 { return barrett_reduce(0, rd(src + P), pc.p, pc.mu, pc.bits); };
         ntt_fwd_block<Sh, false>(smem, m, rbase, twf, pc, ld, nost, x);
     }
-    if (valid) {
-#pragma unroll
-        for (int e = 0; e < Sh::E; e += 2)
-            *reinterpret_cast<ulonglong2 *>(dst + last_pos<Sh>(m, tid, e)) = make_ulonglong2(x[e], x[e + 1]);
-    }
+    if (valid) store_run<Sh>(dst, x, m, tid);
 }
 
 template <int LOG_B, int LOG_C, int LOG_E, bool JOBS = false>
@@ -923,10 +934,7 @@ __device__ __forceinline__ void ks_mac_item(const EvalArgs &a, u32 groups, u32 q
     for (u32 j = 0; j < n; j++, key += key_j, mx += N) {
         ulonglong2 w[2][2];
 #pragma unroll
-        for (int k = 0; k < 2; k++) {
-            w[k][0] = __ldg(key + k * key_k);
-            w[k][1] = __ldg(key + k * key_k + 1);
-        }
+        for (int k = 0; k < 2; k++) ld_tw2(key + k * key_k, 0, w[k][0], w[k][1]);   // positions P, P + 1
 #pragma unroll
         for (u32 gi = 0; gi < MAC_CTS; gi++) {
             if (gi >= ng) break;
@@ -1012,8 +1020,8 @@ k_ks_moddown(EvalArgs a)
     ntt_fwd_block<Sh, false>(smem, m, 0, a.ctx.tw_fwd + (size_t)i * Sh::N, pc, ld, st, x);
     const u64 *accp = a.accq + (((size_t)c * 2 + k) * n + i) * Sh::N;
     u64 *out = a.out + (((size_t)c * 2 + k) * n + i) * Sh::N;
-    sub_scale_pairs<Sh>(x, accp, cst[0], cst[1], pc, m, tid);   // acc holds d P
-    store_pairs<Sh>(out, x, m, tid);
+    sub_scale_run<Sh>(x, accp, cst[0], cst[1], pc, m, tid);   // acc holds d P
+    store_run<Sh>(out, x, m, tid);
 }
 
 // RS, first half: y_k = INTT_{q_l}(c_k[q_l]) -> lift2 (coefficient domain).
@@ -1058,8 +1066,8 @@ k_rs(EvalArgs a)
     ntt_fwd_block<Sh, false>(smem, m, 0, a.ctx.tw_fwd + (size_t)i * Sh::N, pc, ld, st, x);
     const u64 *src = a.ct2 + (((size_t)c * 2 + k) * n + i) * Sh::N;
     u64 *out = a.out + (((size_t)c * 2 + k) * l + i) * Sh::N;
-    sub_scale_pairs<Sh>(x, src, cst[0], cst[1], pc, m, tid);
-    store_pairs<Sh>(out, x, m, tid);
+    sub_scale_run<Sh>(x, src, cst[0], cst[1], pc, m, tid);
+    store_run<Sh>(out, x, m, tid);
 }
 
 // MulLinRS, limb q_l: relin output c_k[q_l] = d_k[l] + (acc - NTT(r)) P^-1,
@@ -1082,7 +1090,7 @@ __device__ __forceinline__ void mrr_last_body(const EvalArgs &a, u32 item, u32 m
     auto nost = [&](u32, u64) {};
     ntt_fwd_block<Sh, false>(smem, m, rbase, a.ctx.tw_fwd + (size_t)l * Sh::N, pc, ld, nost, x);
     const u64 *accp = a.accq + (((size_t)c * 2 + k) * n + l) * Sh::N;
-    sub_scale_pairs<Sh>(x, accp, cst[0], cst[1], pc, m, tid);   // acc holds d P
+    sub_scale_run<Sh>(x, accp, cst[0], cst[1], pc, m, tid);   // acc holds d P
     u64 *dst = a.lift2 + ((size_t)c * 2 + k) * Sh::N;
     auto st = [&](u32 P, u64 v) {
         if (valid) dst[P] = v;
@@ -1131,8 +1139,8 @@ __device__ __forceinline__ void mrr_rest_z_body(const EvalArgs &a, u32 item, u32
     auto ld = [&](int P) -> u64 { return centred_mod(rd(y + P), half_P, P_mod_q, pc); };
     ntt_fwd_block<Sh, false>(smem, m, rbase, a.ctx.tw_fwd + (size_t)i * Sh::N, pc, ld, nost, x);
     u64 *accp = a.accq + (((size_t)c * 2 + k) * n + i) * Sh::N;
-    sub_scale_pairs<Sh>(x, accp, cP[0], cP[1], pc, m, tid);
-    if (valid) store_pairs<Sh>(accp, x, m, tid);
+    sub_scale_run<Sh>(x, accp, cP[0], cP[1], pc, m, tid);
+    if (valid) store_run<Sh>(accp, x, m, tid);
 }
 
 template <class Sh>
@@ -1153,8 +1161,8 @@ __device__ __forceinline__ void mrr_rest_out_body(const EvalArgs &a, u32 item, u
     ntt_fwd_block<Sh, false>(smem, m, rbase, a.ctx.tw_fwd + (size_t)i * Sh::N, pc, ld, nost, x);
     const u64 *zp = a.accq + (((size_t)c * 2 + k) * n + i) * Sh::N;
     u64 *out = a.out + (((size_t)c * 2 + k) * l + i) * Sh::N;
-    sub_scale_pairs<Sh>(x, zp, cl[0], cl[1], pc, m, tid);
-    if (valid) store_pairs<Sh>(out, x, m, tid);
+    sub_scale_run<Sh>(x, zp, cl[0], cl[1], pc, m, tid);
+    if (valid) store_run<Sh>(out, x, m, tid);
 }
 
 // Inverse transform of one special-prime accumulator row of plift in place

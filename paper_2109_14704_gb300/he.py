@@ -5,7 +5,7 @@ kernels; there is no CPU fallback. If the library cannot be built or loaded,
 every call raises.
 
 Device buffers are torch tensors of dtype int64 or uint64 holding the 64-bit
-words (the bits are used as is), contiguous and 16-byte aligned.
+words (the bits are used as is), contiguous and 32-byte aligned.
 """
 from __future__ import annotations
 

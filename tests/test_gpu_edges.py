@@ -106,3 +106,34 @@ def test_binding_rejects_short_buffers(env):
         he.encrypt(short, short, short, torch.zeros(N, dtype=torch.int8, device="cuda"),
                    torch.zeros(N, dtype=torch.int8, device="cuda"), torch.zeros(N, dtype=torch.int8, device="cuda"),
                    1, ctx, 2, sc)
+
+
+def test_buffers_must_be_32_byte_aligned(env):
+    """Runs of four consecutive words move with 256-bit accesses, so the
+    boundary requires 32-byte aligned device buffers: a buffer 16 bytes off
+    that is refused before anything is launched, and nothing is written."""
+    data, P, ctx, key, tables, r = env
+    L = 2
+    flat = _sentinel(L * N + 2)
+    off = flat[2:]                                    # 16 bytes past an aligned start
+    assert off.data_ptr() % 32 == 16
+    ct = dev(np.stack([np.stack([r.uniform_limbs(data, N) for _ in range(2)])]))
+    ct_flat = _sentinel(2 * (L + 1) * N + 2)
+    ct_off = ct_flat[2:].view(1, 2, L + 1, N)
+    out_flat = _sentinel(2 * L * N + 2)
+    out_off = out_flat[2:].view(1, 2, L, N)
+    sc = empty(ctx.mrr_scratch_bytes(L, 1) // 8)
+    sc_off = empty(ctx.mrr_scratch_bytes(L, 1) // 8 + 2)[2:]
+    cases = [
+        lambda: he.ntt_fwd(off, N, L, 1, tables),
+        lambda: he.ntt_inv(off, N, L, 1, tables),
+        lambda: he.dyadic_mul(empty(L * N), off, off, N, L, 1, tables),
+        lambda: he.mul_relin_rescale(out_off, ct, ct, 1, key, ctx, L, sc),
+        lambda: he.mul_relin_rescale(empty(1, 2, L, N), ct_off, ct, 1, key, ctx, L, sc),
+        lambda: he.mul_relin_rescale(empty(1, 2, L, N), ct, ct, 1, key, ctx, L, sc_off),
+    ]
+    for i, f in enumerate(cases):
+        with pytest.raises(he.HeError, match="32-byte"):
+            f()
+    torch.cuda.synchronize()
+    assert _untouched(flat) and _untouched(ct_flat) and _untouched(out_flat)
