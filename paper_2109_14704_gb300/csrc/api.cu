@@ -267,10 +267,14 @@ extern "C" he_status he_ntt_tables_create(uint32_t N, uint32_t limbs, const uint
             pw[i] = h_mul(pw[i - 1], psi, q);
             pwi[i] = h_mul(pwi[i - 1], psi_inv, q);
         }
+        inv[(size_t)l * N] = make_ulonglong2(1, shoup(1, q));   // k = 0: unused
         for (u32 k = 0; k < N; k++) {
             const u64 w = pw[bit_reverse(k, log_n)], wi = pwi[bit_reverse(k, log_n)];
             fwd[(size_t)l * N + k] = make_ulonglong2(w, shoup(w, q));
-            inv[(size_t)l * N + k] = make_ulonglong2(wi, shoup(wi, q));
+            if (k) {
+                const int S = 31 - __builtin_clz(k);
+                inv[(size_t)l * N + he::inv_tw_pos((int)log_n, S, (int)(k - (1u << S)))] = make_ulonglong2(wi, shoup(wi, q));
+            }
         }
         pcs[l] = prime_const(q, N, inv[(size_t)l * N + 1].x);
     }

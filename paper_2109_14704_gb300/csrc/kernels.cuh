@@ -251,7 +251,7 @@ __global__ void k_ntt_naive_stage(NttLaunch a, u32 log_n, u32 S, bool inv)
     } else if (S == 0) {
         gs_last(x, y, pc);
     } else {
-        const ulonglong2 w = a.tw_inv[(size_t)pr * N + (1u << S) + g];
+        const ulonglong2 w = a.tw_inv[(size_t)pr * N + inv_tw_pos((int)log_n, (int)S, (int)g)];
         gs_butterfly(x, y, w.x, w.y, pc);
     }
     data[j] = x;
