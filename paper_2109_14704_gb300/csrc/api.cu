@@ -396,6 +396,48 @@ extern "C" he_status he_ntt_set_shape(uint32_t N, uint32_t direction, uint32_t l
 }
 
 // One launch of a batch of limb transforms in the shape set for the degree.
+// cuTensorMapEncodeTiled, fetched through the runtime's driver entry points
+// (the library does not link the driver library); null if unavailable.
+typedef CUresult (*PfnEncodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static PfnEncodeTiled encode_tiled()
+{
+    static std::once_flag once;
+    static PfnEncodeTiled fn = nullptr;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PfnEncodeTiled)f;
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// Tensor map of a uniform batch for the forward transform's bulk stores:
+// the items N words at base as rows of 16 words (128 bytes, the row stride),
+// boxes of 32 rows (one warp's output), 128-byte swizzle. false (plain
+// stores) if the encoder is unavailable, base is not 128-byte aligned, or
+// the batch has 2^32 rows or more.
+static bool batch_tmap(he::NttLaunch &a, u32 N)
+{
+    PfnEncodeTiled enc = encode_tiled();
+    if (!enc || a.jobs || ((uintptr_t)a.base & 127)) return false;
+    const cuuint64_t rows = (cuuint64_t)a.items * N / 16;
+    if (rows < 32 || rows >= (1ull << 32)) return false;
+    const cuuint64_t dims[2] = {16, rows};
+    const cuuint64_t strides[1] = {128};
+    const cuuint32_t box[2] = {16, 32};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(&a.tmap, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, a.base, dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 static he_status ntt_launch(const he::NttLaunch &a0, int log_n, bool inv, cudaStream_t stream)
 {
     const he::DegreeOps *ops = he::degree_ops(log_n);
@@ -410,6 +452,7 @@ static he_status ntt_launch(const he::NttLaunch &a0, int log_n, bool inv, cudaSt
     if (g_shape_persistent[inv][log_n].load()) {
         HE_CUDA(ops->ntt_persistent(a, lb, le, inv, std::min<u32>(a.items, resident), stream));
     } else {
+        a.tma_store = (!inv && le == 4 && batch_tmap(a, 1u << log_n)) ? 1u : 0u;
         HE_CUDA(ops->ntt(a, lb, le, inv, stream));
     }
     return HE_OK;

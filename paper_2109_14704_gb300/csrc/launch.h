@@ -1,6 +1,7 @@
 // launch.h -- argument blocks of the kernels and the per-degree launcher
 // table (host and device visible). Internal to the library.
 #pragma once
+#include <cuda.h>   // CUtensorMap (the type only; nothing links the driver library)
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -21,6 +22,9 @@ struct LimbJob {
 
 // A uniform batch (items = count * limbs limbs of one degree, limb l of each
 // polynomial using prime first_prime + l of one table set), or a job list.
+// tma_store: the forward transform writes its output with bulk tensor
+// stores through tmap, the batch viewed as rows of 16 words (128 bytes),
+// boxes of 32 rows, 128-byte swizzle (uniform batches, 16 words a thread).
 struct NttLaunch {
     u64 *base;
     u32 limbs;
@@ -31,6 +35,8 @@ struct NttLaunch {
     const ulonglong2 *tw_inv;
     const PrimeConst *pc;       // [prime]
     const LimbJob *jobs;        // non-null: per-item jobs instead of base/limbs
+    u32 tma_store;
+    CUtensorMap tmap;
 };
 
 // Fused negacyclic product c = a b mod (X^N + 1, q) of items = count * limbs

@@ -48,6 +48,30 @@ def test_ntt_parity_every_degree(log_n):
         assert np.array_equal(got[p], oracle.ntt_inv(y[p], qs)), p
 
 
+@pytest.mark.parametrize("log_n", [10, 12, 15])
+@pytest.mark.parametrize("offset_words", [0, 4])
+def test_forward_store_forms(log_n, offset_words):
+    """The forward transform of a uniform batch leaves by bulk tensor stores
+    when the batch is 128-byte aligned and by plain stores otherwise (a
+    32-byte aligned view 4 words into its buffer); both equal the oracle, and
+    the words around the batch are untouched."""
+    N = 1 << log_n
+    limbs, count = 3, 3
+    qs = _moduli(N, limbs)
+    tables = he.NttTables(N, qs)
+    x = np.stack([Rng(log_n * 100 + p).uniform_limbs(qs, N) for p in range(count)])
+    buf = torch.full((count * limbs * N + 8,), 777, dtype=torch.int64, device="cuda")
+    d = buf[offset_words:offset_words + count * limbs * N].view(count, limbs, N)
+    assert d.data_ptr() % 128 == (0 if offset_words == 0 else 32)
+    d.copy_(dev(x))
+    he.ntt_fwd(d, N, limbs, count, tables)
+    got = host(d)
+    for p in range(count):
+        assert np.array_equal(got[p], oracle.ntt_fwd(x[p], qs)), p
+    rest = torch.cat([buf[:offset_words], buf[offset_words + count * limbs * N:]])
+    assert bool((rest == 777).all().item())
+
+
 SHAPES = [(10, 10, 3), (11, 11, 3), (11, 10, 4), (12, 12, 3), (12, 11, 4), (12, 10, 4), (13, 13, 4),
           (13, 12, 3), (13, 11, 4), (14, 13, 4), (14, 12, 3), (14, 12, 4), (15, 13, 4), (15, 12, 3),
           (15, 13, 3), (16, 13, 3)]
