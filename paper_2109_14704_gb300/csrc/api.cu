@@ -191,6 +191,7 @@ static he::PrimeConst prime_const(u64 q, u32 N, u64 w1)
     c.ninv_sh = shoup(c.ninv, q);
     c.w1ninv = h_mul(w1, c.ninv, q);
     c.w1ninv_sh = shoup(c.w1ninv, q);
+    c.one_sh = shoup(1, q);
     return c;
 }
 

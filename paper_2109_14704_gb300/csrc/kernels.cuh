@@ -633,10 +633,10 @@ __global__ void k_enc_combine(u64 *ct, const u64 *noise, const u64 *pt, const u6
 // k_mrr_rest_out).
 
 // Centred residue of y in [0, m) (|r| <= (m-1)/2) reduced mod q:
-// y mod q, or y mod q - m mod q when y > (m-1)/2. Needs y < 2 q^2.
+// y mod q, or y mod q - m mod q when y > (m-1)/2 (any word y).
 __device__ __forceinline__ u64 centred_mod(u64 y, u64 half_m, u64 m_mod_q, const PrimeConst &pc)
 {
-    u64 r = barrett_reduce(0, y, pc.p, pc.mu, pc.bits);
+    const u64 r = reduce_word_canon(y, pc);
     return y > half_m ? sub_mod(r, m_mod_q, pc.p) : r;
 }
 
@@ -847,8 +847,7 @@ k_ks_modup(EvalArgs a)
                 ntt_fwd_block<Sh, false>(smem, m, 0, twf, pc, ld, st, x);
             } else {
                 auto ld = [&](u32 P) -> u64 {
-                    return barrett_reduce(0, __ldg(reinterpret_cast<const unsigned long long *>(src + P)), pc.p,
-                                          pc.mu, pc.bits);
+                    return reduce_word(__ldg(reinterpret_cast<const unsigned long long *>(src + P)), pc);
                 };
                 ntt_fwd_block<Sh, false>(smem, m, 0, twf, pc, ld, st, x);
             }
@@ -920,14 +919,16 @@ __device__ __forceinline__ void ks_expand_body(const EvalArgs &a, u32 g, u32 t, 
     u64 x[Sh::E];
     auto nost = [&](u32, u64) {};
     // any input below 8t congruent to the digit will do: when q_j <= 8t the
-    // digit c2_j < q_j goes in as it is
-    if (a.ctx.pc[j].p <= (pc.four_p << 1)) {
-        auto ld = [&](int P) -> u64 { return rd(src + P); };
-        ntt_fwd_block<Sh, false>(smem, m, rbase, twf, pc, ld, nost, x);
-    } else {
-        auto ld = [&](int P) -> u64 { return barrett_reduce(0, rd(src + P), pc.p, pc.mu, pc.bits); };
-        ntt_fwd_block<Sh, false>(smem, m, rbase, twf, pc, ld, nost, x);
-    }
+    // digit c2_j < q_j goes in as it is, otherwise reduce_word brings it
+    // below 4t. One transform for both (the flag is uniform over the
+    // item): two instances of the transform in one kernel spilled 132 bytes
+    // at 64 registers, one spills 8 (measured 1.8 % off the MulLinRS batch).
+    const bool reduce = a.ctx.pc[j].p > (pc.four_p << 1);
+    auto ld = [&](int P) -> u64 {
+        const u64 v = rd(src + P);
+        return reduce ? reduce_word(v, pc) : v;
+    };
+    ntt_fwd_block<Sh, false>(smem, m, rbase, twf, pc, ld, nost, x);
     if (valid) store_run<Sh>(dst, x, m, tid);
 }
 

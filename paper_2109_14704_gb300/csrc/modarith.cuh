@@ -30,6 +30,7 @@ struct PrimeConst {
     u64 ninv_sh;     // its Shoup quotient
     u64 w1ninv;      // psi^-brv(1) * N^-1 mod p (last inverse stage)
     u64 w1ninv_sh;
+    u64 one_sh;      // floor(2^64 / p): the Shoup quotient of 1 (reduce_word)
     u32 bits;        // b
     u32 h4;          // ceil(4p / 2^32): high-word threshold of the lazy reduction
 };
@@ -83,6 +84,22 @@ __device__ __forceinline__ u64 shoup_quotient_approx(u64 w_sh, u64 y)
 __device__ __forceinline__ u64 mul_shoup_lazy4(u64 y, u64 w, u64 w_sh, u64 neg_p)
 {
     return w * y + shoup_quotient_approx(w_sh, y) * neg_p;
+}
+
+// Any word x reduced mod p: mul_shoup_lazy4 with W = 1 (W' = floor(2^64 / p))
+// gives x - Q' p in [0, 4p), five 32 x 32 products (1 Y needs none) and few
+// registers; reduce_word_canon adds two conditional subtractions for [0, p).
+// Cheaper than Barrett of a single word, and it kept the mod-up transforms
+// (which reduce a 60-bit digit for a smaller target on every load) from
+// spilling.
+__device__ __forceinline__ u64 reduce_word(u64 x, const PrimeConst &c)
+{
+    return mul_shoup_lazy4(x, 1, c.one_sh, c.neg_p);
+}
+
+__device__ __forceinline__ u64 reduce_word_canon(u64 x, const PrimeConst &c)
+{
+    return reduce_once(reduce_once(reduce_word(x, c), c.two_p), c.p);
 }
 
 // W Y mod p in [0, 4p) as mul_shoup_lazy4, with the multiply-add chains
