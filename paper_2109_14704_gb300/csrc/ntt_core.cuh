@@ -86,11 +86,28 @@ __device__ __forceinline__ void cluster_sync_all()
 // shared memory that a peer is about to overwrite (or release by exiting).
 // Those reads have returned their values before the arrive is issued, so the
 // arrive needs no release ordering (and no memory fence before it); waits on
-// it still acquire.
+// it still acquire. The callers make sure of that: their stores of the
+// values read precede it as memory operations (the inverse transform's
+// end, ntt_barrier between transforms), or they use cluster_sync_war_after.
 __device__ __forceinline__ void cluster_sync_war()
 {
     asm volatile("barrier.cluster.arrive.relaxed.aligned;\n\t"
                  "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// cluster_sync_war for a thread whose last reads of peers' shared memory
+// produced x[] (remote loads, then register arithmetic): the arrive takes
+// a fold of every word as an operand, so the compiler cannot sink the
+// arithmetic past it and, a warp issuing in order, the arrive cannot issue
+// before the remote loads have returned.
+template <int E>
+__device__ __forceinline__ void cluster_sync_war_after(const u64 (&x)[E])
+{
+    u64 f = x[0];
+#pragma unroll
+    for (int e = 1; e < E; e++) f |= x[e];
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;\n\t"
+                 "barrier.cluster.wait.acquire.aligned;" ::"l"(f) : "memory");
 }
 
 __device__ __forceinline__ u32 smem_u32(const void *p) { return (u32)__cvta_generic_to_shared(p); }
@@ -393,7 +410,7 @@ __device__ __forceinline__ void fwd_round(u64 (&x)[Sh::E], u64 *s, u32 tid, u32 
     using Rd = RoundOf<Sh, RI>;
     if constexpr (RI > 0) {
         // pull form: the peers have pulled their words out of this block
-        if constexpr (RI == 1 && Sh::LOG_C > 0 && Sh::FWD_PULL) cluster_sync_war();
+        if constexpr (RI == 1 && Sh::LOG_C > 0 && Sh::FWD_PULL) cluster_sync_war_after(x);
         round_store_smem<Sh, RoundOf<Sh, RI - 1>>(x, s, tid);
         round_link_sync<Sh, RI - 1>(tid);
         round_load_smem<Sh, Rd>(x, s, tid);
