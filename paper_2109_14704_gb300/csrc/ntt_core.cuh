@@ -86,9 +86,10 @@ __device__ __forceinline__ void cluster_sync_all()
 // shared memory that a peer is about to overwrite (or release by exiting).
 // Those reads have returned their values before the arrive is issued, so the
 // arrive needs no release ordering (and no memory fence before it); waits on
-// it still acquire. The callers make sure of that: their stores of the
-// values read precede it as memory operations (the inverse transform's
-// end, ntt_barrier between transforms), or they use cluster_sync_war_after.
+// it still acquire. The callers make sure of that: ntt_barrier between two
+// transforms follows the first one's closing barrier (which already waited
+// for its remote reads); the transforms' own barriers after remote reads
+// tie the arrive to the words read (cluster_sync_war_fold / _after).
 __device__ __forceinline__ void cluster_sync_war()
 {
     asm volatile("barrier.cluster.arrive.relaxed.aligned;\n\t"
@@ -100,14 +101,19 @@ __device__ __forceinline__ void cluster_sync_war()
 // a fold of every word as an operand, so the compiler cannot sink the
 // arithmetic past it and, a warp issuing in order, the arrive cannot issue
 // before the remote loads have returned.
+__device__ __forceinline__ void cluster_sync_war_fold(u64 f)
+{
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;\n\t"
+                 "barrier.cluster.wait.acquire.aligned;" ::"l"(f) : "memory");
+}
+
 template <int E>
 __device__ __forceinline__ void cluster_sync_war_after(const u64 (&x)[E])
 {
     u64 f = x[0];
 #pragma unroll
     for (int e = 1; e < E; e++) f |= x[e];
-    asm volatile("barrier.cluster.arrive.relaxed.aligned;\n\t"
-                 "barrier.cluster.wait.acquire.aligned;" ::"l"(f) : "memory");
+    cluster_sync_war_fold(f);
 }
 
 __device__ __forceinline__ u32 smem_u32(const void *p) { return (u32)__cvta_generic_to_shared(p); }
@@ -498,7 +504,7 @@ __device__ __forceinline__ void ntt_fwd_block(u64 *s, u32 m, u32 rbase, const ul
                     const u32 slot = (m << LOG_W) + ((u32)P & ((1u << LOG_W) - 1));
                     x[i * (1 << R0::R) + u] = ld_cluster(map_to_rank(s_base + slot * 8u, rbase + ((u32)P >> LOG_W)));
                 }
-            if constexpr (Sh::NROUND == 1) cluster_sync_war();   // peers pulled from this block
+            if constexpr (Sh::NROUND == 1) cluster_sync_war_after(x);   // peers pulled from this block
         } else {
             round_load_smem<Sh, R0>(x, s, tid);
         }
@@ -634,6 +640,7 @@ __device__ __forceinline__ void ntt_inv_block(u64 *s, u32 m, u32 rbase, const ul
         constexpr u32 C = Sh::C;
         constexpr int COLS = Sh::E / (int)C;
         const u32 s_base = smem_u32(s);
+        u64 fold = 0;   // every word read from the peers, for the final barrier
 #pragma unroll
         for (int c = 0; c < COLS; c++) {
             const int j = (int)(m * (Sh::B / C)) + c * (int)Sh::T + (int)tid;
@@ -641,6 +648,8 @@ __device__ __forceinline__ void ntt_inv_block(u64 *s, u32 m, u32 rbase, const ul
             u64 v[C];
 #pragma unroll
             for (u32 t = 0; t < C; t++) v[t] = ld_cluster(map_to_rank(a, rbase + t));
+#pragma unroll
+            for (u32 t = 0; t < C; t++) fold |= v[t];
 #pragma unroll
             for (int SS = 0; SS < Sh::LOG_C; SS++) {
                 const int S = Sh::LOG_C - 1 - SS;
@@ -664,7 +673,10 @@ __device__ __forceinline__ void ntt_inv_block(u64 *s, u32 m, u32 rbase, const ul
 #pragma unroll
             for (u32 t = 0; t < C; t++) store((int)t * (int)Sh::B + j, v[t]);
         }
-        cluster_sync_war();  // peers may still read this CTA's shared memory
+        // peers may still read this CTA's shared memory; the arrive waits
+        // for this thread's own remote reads (the fold), also where the
+        // stores are switched off
+        cluster_sync_war_fold(fold);
     }
 }
 
