@@ -52,8 +52,8 @@ METRIC = "NTT limbs/s at N=2^15 + HE mul-relin-rescale/s, batched vs plain; p99 
 # grows in proportion to the limbs). Entries are removed when the kernel
 # changes after their capture, so that no stale figure is reported.
 TRAFFIC = {
-    ("forward", (12, 4, 0, 0)): 4 * (541901824 + 476654848),
-    ("inverse", (12, 4, 0, 0)): 4 * (542833408 + 480049664),
+    ("forward", (12, 4, 0, 0)): 4 * (542030000 + 475360000),
+    ("inverse", (12, 4, 0, 0)): 4 * (542990000 + 476230000),
 }
 # The production forward butterfly keeps the IMAD (fmaheavy) pipe busy for
 # 0.2536 cycles per butterfly per SM: ncu on the register-resident probe
@@ -187,6 +187,26 @@ def _time_steps(fn, steps, warmup, stream, barrier):
     return t0.elapsed_time(t1) / steps
 
 
+def _distribution(ms_list) -> dict:
+    """Median, p99, extremes and count of single-step times (ms)."""
+    import numpy as np
+    xs = sorted(ms_list)
+    return {"median_ms": statistics.median(xs), "p99_ms": float(np.percentile(xs, 99)), "min_ms": xs[0],
+            "max_ms": xs[-1], "reps": len(xs)}
+
+
+def _step_times(fn, reps, stream) -> list:
+    """Each call timed alone with CUDA events on the launching stream."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for a, b in ev:
+        a.record(stream)
+        fn()
+        b.record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
 def _collectives(world: int, device):
     """(barrier, max_over_ranks) over the initialised process group (any
     backend; `device` holds the reduction tensor), or no-ops for one rank.
@@ -296,9 +316,11 @@ def run_ours(args, rank, world, local):
     ms = _time_steps(step_batched, args.steps, args.warmup, stream, barrier)
     ms = max_over_ranks(ms)
 
-    # per-kernel durations for the roofline (events on the launching stream)
+    # per-kernel durations for the roofline (events on the launching stream),
+    # and from them the distribution of single steps (median and p99 over at
+    # least 20; inputs of 2 GiB, larger than L2)
     fwd_ms, inv_ms = [], []
-    for _ in range(max(3, min(args.steps, 10))):
+    for _ in range(max(20, args.steps)):
         e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
         e[0].record(stream)
         he.ntt_fwd(d, N, NTT_LIMBS, NTT_INSTANCES, tables, stream=stream)
@@ -310,6 +332,7 @@ def run_ours(args, rank, world, local):
         inv_ms.append(e[1].elapsed_time(e[2]))
     fwd = statistics.mean(fwd_ms)
     inv = statistics.mean(inv_ms)
+    step_dist = _distribution([a + b for a, b in zip(fwd_ms, inv_ms)])
 
     # CUDA-graph form of the batched step
     g = torch.cuda.CUDAGraph()
@@ -363,6 +386,7 @@ def run_ours(args, rank, world, local):
         he.mul_relin_rescale(out, ca, cb, MRR_COUNT, key, ctx, L, scratch, stream=stream)
 
     ms_mrr = max_over_ranks(_time_steps(mrr_batched, args.steps, args.warmup, stream, barrier))
+    mrr_dist = _distribution(_step_times(mrr_batched, max(20, args.steps), stream))
     s1 = scratch[: ctx.mrr_scratch_bytes(L, 1) // 8]
 
     def mrr_plain():
@@ -500,6 +524,7 @@ def run_ours(args, rank, world, local):
             "fwd_limbs_per_s": world * limbs_total / (fwd / 1e3),
             "inv_limbs_per_s": world * limbs_total / (inv / 1e3),
             "fwd_ms": fwd, "inv_ms": inv, "speedup_vs_naive": ms_naive / ms,
+            "step_distribution": step_dist,
         },
         "autotune": {"forward": dict(zip(("log_block", "log_thread_words", "persistent", "ctas_per_sm"), tune["fwd"])),
                      "inverse": dict(zip(("log_block", "log_thread_words", "persistent", "ctas_per_sm"), tune["inv"])),
@@ -517,6 +542,7 @@ def run_ours(args, rank, world, local):
             "batched_per_s": world * MRR_COUNT / (ms_mrr / 1e3),
             "plain_per_s": world * MRR_COUNT / (ms_mrr_plain / 1e3),
             "ms_per_batch": ms_mrr,
+            "batch_distribution": mrr_dist,
             "transforms_per_op": (L + 1) ** 2 + 5 * (L + 1) + 2,
             "work_per_op": mrr_work(L + 1, MRR_N),
             "roofline": mrr_roof,
