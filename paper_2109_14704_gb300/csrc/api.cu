@@ -825,6 +825,19 @@ static he_status plift_intt(const he_context *ctx, u64 *plift, u32 limbs, cudaSt
 // (k_ks_mac) and the special prime's accumulators go through the inverse
 // transform in place; the buffer takes groups of up to kModupGroup
 // ciphertexts. Otherwise the fused k_ks_modup runs.
+// The tiled key multiply-accumulate's shared memory, 2 n MAC_TILE key pairs
+// (64 KB at the largest chain, n = 32), above the default 48 KB limit.
+static cudaError_t mac_tiled_smem_attr()
+{
+    static std::once_flag once;
+    static cudaError_t e = cudaSuccess;
+    std::call_once(once, [] {
+        e = cudaFuncSetAttribute(he::k_ks_mac_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(2 * 32 * he::MAC_TILE * sizeof(ulonglong2)));
+    });
+    return e;
+}
+
 static he_status ks_modup(const he_context *ctx, he::EvalArgs &a, u32 count, u64 *xbuf, size_t x_words,
                           cudaStream_t s)
 {
@@ -837,8 +850,15 @@ static he_status ks_modup(const he_context *ctx, he::EvalArgs &a, u32 count, u64
         const u32 gs = std::min(group, count - c0);
         a.c_first = c0;
         if (he_status r = run_eval(ctx, he::EK_KS_EXPAND, a, gs * (n + 1) * n, s)) return r;
-        const u32 total = (u32)((gs + he::MAC_CTS - 1) / he::MAC_CTS * (n + 1) * (ctx->N / 2));
-        he::k_ks_mac<false><<<stream_grid(total, 256), 256, 0, s>>>(a, gs, total, he::NoJobs{});
+        if (gs >= 8) {   // every ciphertext lane of the tiled kernel busy
+            const u32 blocks = (n + 1) * (ctx->N / he::MAC_TILE) * ((gs + he::MAC_CHUNK - 1) / he::MAC_CHUNK);
+            const u32 smem = n * 2 * he::MAC_TILE * (u32)sizeof(ulonglong2);
+            if (cudaError_t e = mac_tiled_smem_attr()) return cuda_fail(e, "k_ks_mac_tiled attribute");
+            he::k_ks_mac_tiled<<<blocks, 256, smem, s>>>(a, gs);
+        } else {
+            const u32 total = (u32)((gs + he::MAC_CTS - 1) / he::MAC_CTS * (n + 1) * (ctx->N / 2));
+            he::k_ks_mac<false><<<stream_grid(total, 256), 256, 0, s>>>(a, gs, total, he::NoJobs{});
+        }
         HE_CUDA(cudaGetLastError());
     }
     a.mx = nullptr;

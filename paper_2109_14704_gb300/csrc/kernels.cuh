@@ -1024,6 +1024,84 @@ __device__ __forceinline__ void ks_mac_item(const EvalArgs &a, u32 groups, u32 q
     }
 }
 
+// Tiled form of the key multiply-accumulate for a uniform group of at
+// least 8 ciphertexts: one CTA per (target t, tile of MAC_TILE positions,
+// chunk of MAC_CHUNK ciphertexts). The tile's key pairs for every digit and
+// component are staged in shared memory once ([2 j + k][position], 2 n
+// MAC_TILE pairs) and serve every ciphertext of the chunk; each warp covers
+// 4 position pairs for 8 ciphertexts (its key reads are broadcasts), each
+// thread 2 positions of one ciphertext at a time, the next digit's values
+// loaded while the current ones' products run. With its few registers the
+// kernel runs six CTAs per SM: the per-thread form above is bound by the
+// latency of its loads at four (measured: the MulLinRS batch at N = 2^14,
+// 64 pairs, 1.203 -> 1.166 ms). Same products, same sums mod p: the outputs
+// are those of k_ks_mac.
+constexpr u32 MAC_TILE = 64, MAC_CHUNK = 32;
+
+__global__ void __launch_bounds__(256, 6) k_ks_mac_tiled(EvalArgs a, u32 groups)
+{
+    extern __shared__ __align__(16) ulonglong2 key_tile[];   // [2 n][MAC_TILE]
+    const u32 n = a.n, N = a.ctx.N, nd1 = a.ctx.n_data + 1;
+    const u32 tiles = N / MAC_TILE, chunks = (groups + MAC_CHUNK - 1) / MAC_CHUNK;
+    const u32 b = blockIdx.x;
+    const u32 chunk = b % chunks, tile = (b / chunks) % tiles, t = b / (chunks * tiles);
+    const u32 tp = (t == n) ? a.ctx.n_data : t;
+    const PrimeConst pc = a.ctx.pc[tp];
+    const u32 P0 = tile * MAC_TILE;
+    for (u32 i = threadIdx.x; i < n * 2 * MAC_TILE; i += blockDim.x) {
+        const u32 row = i / MAC_TILE, col = i % MAC_TILE;   // row 2 j + k: evk [j][k][target][N]
+        key_tile[i] = __ldg(a.evk + ((size_t)row * nd1 + tp) * N + P0 + col);
+    }
+    __syncthreads();
+    const u32 lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const u32 pp = warp * 4 + (lane & 3);
+    const u32 P = P0 + 2 * pp;
+    const u32 log_n = 31 - __clz(N);
+    const u32 gend = min(groups, (chunk + 1) * MAC_CHUNK);
+    for (u32 g = chunk * MAC_CHUNK + (lane >> 2); g < gend; g += 8) {
+        const u64 *mxp = a.mx + ((size_t)g * (n + 1) + t) * n * N + P;   // mx [g][target][j][N]
+        auto load_v = [&](u32 j) -> ulonglong2 {
+            if (j == t) return dsource(a, a.c_first + g).d2(2, j, log_n, P, pc);
+            return __ldg(reinterpret_cast<const ulonglong2 *>(mxp + (size_t)j * N));
+        };
+        u64 acc[2][2];
+        ulonglong2 vn = load_v(0);
+        for (u32 j = 0; j < n; j++) {
+            const ulonglong2 v = vn;
+            if (j + 1 < n) vn = load_v(j + 1);
+#pragma unroll
+            for (int k = 0; k < 2; k++) {
+                const ulonglong2 w0 = key_tile[(2 * j + k) * MAC_TILE + 2 * pp];
+                const ulonglong2 w1 = key_tile[(2 * j + k) * MAC_TILE + 2 * pp + 1];
+                const u64 p0 = mul_shoup_lazy4_asm(v.x, w0.x, w0.y, pc.neg_p);
+                const u64 p1 = mul_shoup_lazy4_asm(v.y, w1.x, w1.y, pc.neg_p);
+                acc[k][0] = j == 0 ? p0 : reduce_once(acc[k][0] + p0, pc.four_p);
+                acc[k][1] = j == 0 ? p1 : reduce_once(acc[k][1] + p1, pc.four_p);
+            }
+        }
+        const u32 c = a.c_first + g;
+        const DSource ds = dsource(a, c);
+#pragma unroll
+        for (int k = 0; k < 2; k++) {
+            ulonglong2 o;
+            if (t < n) {
+                // stored as d_k P + acc_k (see the mod-down)
+                const u64 P_mod_q = a.ctx.cst[3 * t + 2], P_mod_q_sh = a.ctx.cst[p_shoup_index(a.ctx, t)];
+                const u64 s0 = reduce_once(reduce_once(acc[k][0], pc.two_p), pc.p);
+                const u64 s1 = reduce_once(reduce_once(acc[k][1], pc.two_p), pc.p);
+                const ulonglong2 dv = ds.d2(k, t, log_n, P, pc);
+                o.x = add_mod(s0, mul_shoup(dv.x, P_mod_q, P_mod_q_sh, pc.p), pc.p);
+                o.y = add_mod(s1, mul_shoup(dv.y, P_mod_q, P_mod_q_sh, pc.p), pc.p);
+                *reinterpret_cast<ulonglong2 *>(a.accq + (((size_t)c * 2 + k) * n + t) * N + P) = o;
+            } else {
+                o.x = acc[k][0];
+                o.y = acc[k][1];
+                *reinterpret_cast<ulonglong2 *>(a.plift + ((size_t)c * 2 + k) * N + P) = o;
+            }
+        }
+    }
+}
+
 // Items: for a uniform group, (groups / MAC_CTS rounded up) x (n + 1)
 // targets x N / 2 position pairs; for a job table, those of every job back
 // to back (each job one group of all its ciphertexts). `total` is below 2^32

@@ -178,3 +178,27 @@ def test_full_ckks_workload_sampled():
     got = host(out)
     for c in (0, 31, 63):
         assert np.array_equal(got[c], oracle.mul_relin_rescale(ca[c], cb[c], evk, data, P, L)), c
+
+
+@pytest.mark.parametrize("count", [7, 8, 70])
+def test_mul_relin_rescale_multiply_accumulate_forms(count):
+    """The key multiply-accumulate of the expanded mod-up runs tiled (key
+    pairs staged per position tile, groups of 8 or more ciphertexts) or per
+    thread (smaller groups); 70 pairs make a tiled group of 64 followed by a
+    per-thread group of 6. Every pair equals the one-pair call (per-thread
+    form), and sampled pairs equal the oracle."""
+    N, data, P, ctx, evk, key, r = _setup("matrix8k", 2)
+    L = 2
+    ca = np.stack([np.stack([r.uniform_limbs(data, N) for _ in range(2)]) for _ in range(count)])
+    cb = np.stack([np.stack([r.uniform_limbs(data, N) for _ in range(2)]) for _ in range(count)])
+    da, db = dev(ca), dev(cb)
+    out = empty(count, 2, L, N)
+    he.mul_relin_rescale(out, da, db, count, key, ctx, L, empty(ctx.mrr_scratch_bytes(L, count) // 8))
+    got = host(out)
+    one = empty(1, 2, L, N)
+    s1 = empty(ctx.mrr_scratch_bytes(L, 1) // 8)
+    for c in range(count):
+        he.mul_relin_rescale(one, da[c:c + 1], db[c:c + 1], 1, key, ctx, L, s1)
+        assert np.array_equal(got[c], host(one)[0]), c
+    for c in {0, count // 2, count - 1}:
+        assert np.array_equal(got[c], oracle.mul_relin_rescale(ca[c], cb[c], evk, data, P, L)), c
