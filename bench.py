@@ -82,7 +82,8 @@ def _args():
                     help="NTT instances of --profile-case ntt, ciphertext pairs of --profile-case mrr")
     ap.add_argument("--shape", default="",
                     help="log_block,log_thread_words[,persistent] for --profile-case ntt (or fwd/inv)")
-    ap.add_argument("--skip", default="", help="comma list of sub-benchmarks to skip: small,uneven,matrix,routines,encode,serving")
+    ap.add_argument("--skip", default="",
+                    help="comma list of sub-benchmarks to skip: small,degrees,uneven,matrix,routines,encode,serving")
     ap.add_argument("--serve-requests", type=int, default=20000)
     ap.add_argument("--no-tune-cache", action="store_true", help="always re-run the autotuner")
     ap.add_argument("--ref-instances", type=int, default=REF_INSTANCES,
@@ -396,6 +397,7 @@ def run_ours(args, rank, world, local):
     ms_mrr_plain = max_over_ranks(_time_steps(mrr_plain, max(2, args.steps // 5), 3, stream, barrier))
 
     small = bench_small(args, stream, barrier) if "small" not in args.skip else None
+    degrees = bench_degrees(args, stream, barrier) if "degrees" not in args.skip else None
     uneven = bench_uneven(args, stream, barrier) if "uneven" not in args.skip else None
     matrix = bench_matrix(args, stream, barrier) if "matrix" not in args.skip else None
     routines = bench_routines(args, stream, barrier) if "routines" not in args.skip else None
@@ -495,6 +497,7 @@ def run_ours(args, rank, world, local):
     dom = roof_inv if inv >= fwd else roof_fwd          # the larger share of the step
     bound_alu = dom["alu_frac"] >= dom["hbm_frac"]
     attach_rooflines(small, alu_peak, hbm_peak)
+    attach_rooflines(degrees, alu_peak, hbm_peak)
     attach_rooflines(uneven, alu_peak, hbm_peak)
     attach_rooflines(matrix, alu_peak, hbm_peak)
     attach_rooflines(routines, alu_peak, hbm_peak)
@@ -532,6 +535,7 @@ def run_ours(args, rank, world, local):
                      "candidates": [{"shape": c["shape"], "ms_fwd": c.get("ms_fwd"), "ms_inv": c.get("ms_inv")}
                                     for c in tune["candidates"]]},
         "small_ntt": small,
+        "ntt_by_degree": degrees,
         "uneven_batch": uneven,
         "matrix_mul_relin_rescale": matrix,
         "routines": routines,
@@ -597,6 +601,52 @@ def _measured_peaks() -> dict:
 
 
 # ------------------------------------------------------ other workloads
+
+def bench_degrees(args, stream, barrier):
+    """The batched transform at every supported degree, N = 2^10 .. 2^16:
+    polynomials of 8 limbs (four 60-bit and four 50-bit primes), as many as
+    make 2^25 words (256 MiB per direction, larger than L2), forward then
+    inverse in place, one launch per direction, the degree's default shape
+    (2^15 runs the shape the autotuner applied earlier in the run). Inputs
+    are uniform residues drawn on the device (the timing does not depend on
+    them; the GPU tests check every degree against the oracle)."""
+    import torch
+
+    from paper_2109_14704_gb300 import he
+
+    limbs, words = 8, 1 << 25
+    rows = []
+    for log_n in range(10, 17):
+        N = 1 << log_n
+        qs = he.primes_generate(60, 2 * N, 4) + he.primes_generate(50, 2 * N, 4)
+        tables = he.NttTables(N, qs)
+        count = words // (limbs * N)
+        g = torch.Generator(device="cuda")
+        g.manual_seed(log_n)
+        d = torch.randint(0, 1 << 62, (count, limbs, N), dtype=torch.int64, device="cuda", generator=g)
+        d %= torch.tensor(qs, dtype=torch.int64, device="cuda").view(1, limbs, 1)
+        fwd_ms, inv_ms = [], []
+        for it in range(8):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record(stream)
+            he.ntt_fwd(d, N, limbs, count, tables, stream=stream)
+            e[1].record(stream)
+            he.ntt_inv(d, N, limbs, count, tables, stream=stream)
+            e[2].record(stream)
+            torch.cuda.synchronize()
+            if it >= 3:
+                fwd_ms.append(e[0].elapsed_time(e[1]))
+                inv_ms.append(e[1].elapsed_time(e[2]))
+        fwd, inv = statistics.median(fwd_ms), statistics.median(inv_ms)
+        items = count * limbs
+        rows.append({"N": N, "polys": count, "limbs": items, "shape_default": list(he.ntt_shapes(N)[0][:2]),
+                     "fwd_ms": fwd, "inv_ms": inv, "limbs_per_s": 2 * items / ((fwd + inv) / 1e3),
+                     "_work": {"bfly": 2 * items * (N // 2) * log_n, "bytes": 2 * 16 * N * items,
+                               "seconds": (fwd + inv) / 1e3}})
+        del d, tables
+    return {"workload": "batched forward + inverse, 8 limbs per polynomial, 2^25 words per direction, "
+                        "N = 2^10 .. 2^16", "degrees": rows}
+
 
 def bench_small(args, stream, barrier):
     """The plain single transform (N = 4096, two 60-bit primes, two
