@@ -31,12 +31,16 @@ static cudaError_t launch_k(K kernel, u32 grid, u32 block, u32 smem, u32 cluster
     return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
-// Raise the dynamic shared-memory limit of a kernel once per process.
+// Raise the dynamic shared-memory limit of a kernel once per process, and
+// allow its launch in clusters of more than 8 CTAs (the non-portable size,
+// up to 16 on this GPU) where the shape needs it.
 template <class K>
-static cudaError_t smem_attr(K kernel, u32 bytes, std::once_flag &flag, cudaError_t &err)
+static cudaError_t smem_attr(K kernel, u32 bytes, std::once_flag &flag, cudaError_t &err, u32 cluster = 0)
 {
     std::call_once(flag, [&] {
         err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        if (err == cudaSuccess && cluster > 8)
+            err = cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     });
     return err;
 }
@@ -53,7 +57,7 @@ struct ShapeOps {
     {
         static std::once_flag f;
         static cudaError_t e = cudaSuccess;
-        if (cudaError_t r = smem_attr(k_ntt<LOG_B, LOG_C, LOG_E, INV, OCC>, Sh::SMEM_BYTES, f, e)) return r;
+        if (cudaError_t r = smem_attr(k_ntt<LOG_B, LOG_C, LOG_E, INV, OCC>, Sh::SMEM_BYTES, f, e, Sh::C)) return r;
         return launch_k(k_ntt<LOG_B, LOG_C, LOG_E, INV, OCC>, a.items * Sh::C, Sh::T, Sh::SMEM_BYTES, Sh::C, s, a);
     }
 
@@ -62,7 +66,7 @@ struct ShapeOps {
     {
         static std::once_flag f;
         static cudaError_t e = cudaSuccess;
-        if (cudaError_t r = smem_attr(k_ntt_persistent<LOG_B, LOG_C, LOG_E, INV, OCC>, Sh::SMEM_BYTES, f, e)) return r;
+        if (cudaError_t r = smem_attr(k_ntt_persistent<LOG_B, LOG_C, LOG_E, INV, OCC>, Sh::SMEM_BYTES, f, e, Sh::C)) return r;
         return launch_k(k_ntt_persistent<LOG_B, LOG_C, LOG_E, INV, OCC>, clusters * Sh::C, Sh::T, Sh::SMEM_BYTES, Sh::C,
                         s, a);
     }
@@ -71,7 +75,7 @@ struct ShapeOps {
     {
         static std::once_flag f;
         static cudaError_t e = cudaSuccess;
-        if (cudaError_t r = smem_attr(k_negacyclic<LOG_B, LOG_C, LOG_E>, 2 * Sh::SMEM_BYTES, f, e)) return r;
+        if (cudaError_t r = smem_attr(k_negacyclic<LOG_B, LOG_C, LOG_E>, 2 * Sh::SMEM_BYTES, f, e, Sh::C)) return r;
         return launch_k(k_negacyclic<LOG_B, LOG_C, LOG_E>, a.items * Sh::C, Sh::T, 2 * Sh::SMEM_BYTES, Sh::C, s, a);
     }
 
@@ -91,7 +95,7 @@ struct ShapeOps {
     {
         static std::once_flag f;
         static cudaError_t e = cudaSuccess;
-        if (smem_attr(k_ntt_persistent<LOG_B, LOG_C, LOG_E, INV, OCC>, Sh::SMEM_BYTES, f, e) != cudaSuccess) return 0;
+        if (smem_attr(k_ntt_persistent<LOG_B, LOG_C, LOG_E, INV, OCC>, Sh::SMEM_BYTES, f, e, Sh::C) != cudaSuccess) return 0;
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(Sh::C * 1024, 1, 1);
         cfg.blockDim = dim3(Sh::T, 1, 1);

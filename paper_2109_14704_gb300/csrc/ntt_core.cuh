@@ -251,7 +251,7 @@ struct NttShape {
     // shared memory allows anyway), 64 with 8
     static constexpr int NEGA_REGS = LOG_E == 4 ? 80 : 64;
     static constexpr int NEGA_MIN_CTAS = (65536 / (int)(T * NEGA_REGS)) > 0 ? 65536 / (int)(T * NEGA_REGS) : 1;
-    static_assert(LOG_C <= 3, "portable clusters hold at most 8 CTAs");
+    static_assert(LOG_C <= 4, "clusters of at most 16 CTAs (more than 8: the non-portable size)");
     static_assert(LOG_C <= LOG_E, "a thread holds whole columns of the cross stages");
     static_assert(LOG_E == 3 || LOG_E == 4, "radix 8 or 16 rounds");
     static_assert(T >= 32 && T <= 1024, "one to 32 warps per CTA");

@@ -74,7 +74,7 @@ def test_forward_store_forms(log_n, offset_words):
 
 SHAPES = [(10, 10, 3), (11, 11, 3), (11, 10, 4), (12, 12, 3), (12, 11, 4), (12, 10, 4), (13, 13, 4),
           (13, 12, 3), (13, 11, 4), (14, 13, 4), (14, 12, 3), (14, 12, 4), (15, 13, 4), (15, 12, 3),
-          (15, 13, 3), (16, 13, 3)]
+          (15, 13, 3), (16, 13, 3), (16, 12, 4)]
 
 
 @pytest.mark.parametrize("log_n,log_b,log_e", SHAPES)
