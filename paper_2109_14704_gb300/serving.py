@@ -408,6 +408,13 @@ class Server:
                 self.waiting.append(pending.popleft())
             while self.waiting:
                 if not self._admit(self.waiting[0], now):
+                    if not self.inflight and not self.open:
+                        # nothing holds memory that could be freed: this
+                        # request's batch alone exceeds the budget
+                        req = self.waiting[0]
+                        raise MemoryError(f"a batch of (N={req.N}, level={req.level}) needs more than the "
+                                          f"{self.budget} bytes budgeted ({self.static_bytes} held by keys "
+                                          f"and tables)")
                     break
                 self.waiting.popleft()
             for key, b in list(self.open.items()):
