@@ -25,14 +25,17 @@
  *           canonical. Lazy ranges never cross this interface.
  * Memory.   Pointers named *_host are host memory; every other data pointer
  *           is device memory owned by the caller. The library owns only the
- *           opaque handles (tables, contexts, keys, plans), until *_destroy.
+ *           opaque handles (tables, contexts, keys, plans, encoders), until
+ *           *_destroy; a *_destroy of NULL does nothing and returns HE_OK.
  *           Scratch buffers are passed in by the caller; he_*_scratch_bytes
  *           gives their size.
  * Streams.  Work is enqueued on `stream` (a cudaStream_t; NULL is the legacy
  *           default stream). Only *_create, *_upload and *_destroy
  *           synchronise; no other call blocks the host (Sec. III: the host
  *           synchronises only when results are read back).
- * Errors.   Every call returns an he_status. Argument checks run on the host
+ * Errors.   Every call returns an he_status, except he_version,
+ *           he_plan_launches and the size queries (he_*_scratch_bytes, 0
+ *           for bad arguments). Argument checks run on the host
  *           before anything is enqueued and return HE_EINVAL without side
  *           effects. A failed CUDA call returns HE_ECUDA; errors raised later
  *           by enqueued work surface at the caller's next synchronisation.

@@ -1346,7 +1346,7 @@ extern "C" he_status he_encoder_create(const he_context *ctx, he_encoder **out)
 
 extern "C" he_status he_encoder_destroy(he_encoder *enc)
 {
-    if (!enc) return fail(HE_EINVAL, "encoder is NULL");
+    if (!enc) return HE_OK;   // like every *_destroy: NULL is a no-op
     encoder_free(enc);
     return HE_OK;
 }

@@ -114,3 +114,35 @@ def test_binding_rejects_short_device_buffers():
     with pytest.raises(ValueError, match="needs 100"):
         he._ptr(fake, 100)
     assert he._ptr(12345, 1 << 40) == 12345      # raw addresses pass unchecked
+
+
+# Entry points that accept all-NULL / zero arguments as a no-op.
+_NOOP_OK = {"he_ntt_tables_destroy", "he_context_destroy", "he_relin_key_destroy", "he_plan_destroy",
+            "he_encoder_destroy", "he_mul_relin_rescale_multi"}   # the last: zero jobs, nothing to do
+
+
+def test_every_entry_point_rejects_null_arguments_on_the_host():
+    """Each status-returning call, given NULL for every pointer and 0 for
+    every number, returns HE_EINVAL with a message (or HE_OK where that is a
+    no-op: a destroy of NULL, an empty job list), before any device work; the
+    size queries return 0. Runs without a GPU."""
+    lib = he.load()
+    checked = 0
+    for name in he.declared_symbols():
+        f = getattr(lib, name)
+        args = [0.0 if t is ctypes.c_double else
+                0 if t in (ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32, ctypes.c_size_t) else None
+                for t in f.argtypes]
+        r = f(*args)
+        if name in ("he_version",):
+            continue
+        if f.restype is ctypes.c_size_t or name == "he_plan_launches":
+            assert r == 0, name
+        elif name in _NOOP_OK:
+            assert r == he.HE_OK, name
+        else:
+            assert r == he.HE_EINVAL, name
+            if name != "he_last_error":
+                assert he.last_error(), name
+        checked += 1
+    assert checked >= 60
