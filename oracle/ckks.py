@@ -1,8 +1,8 @@
 """Host-side CKKS routines of the oracle -- TEST INFRASTRUCTURE.
 
 KeyGen, Encode, Decode, Encrypt and Decrypt as the paper describes them in
-Sec. II-A; the paper keeps all five on the CPU (Sec. III) and so does this
-build. Encoding is FP64 (numpy FFT as a library step), the CRT lift of
+Sec. II-A; the paper keeps all five on the CPU (Sec. III), and so does this
+oracle. Encoding is FP64 (numpy FFT as a library step), the CRT lift of
 decoding uses Python integers, and every ring product goes through the oracle
 NTT (``oracle.negacyclic_mul``). Random draws (secret, errors, masks) come
 from the shared seeded generator and are inputs here, never drawn inside the
