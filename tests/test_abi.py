@@ -146,3 +146,37 @@ def test_every_entry_point_rejects_null_arguments_on_the_host():
                 assert he.last_error(), name
         checked += 1
     assert checked >= 60
+
+
+def test_last_error_is_per_thread():
+    """he_last_error reports the calling thread's own last failure: two
+    threads failing in different ways at the same time each read their own
+    message (ctypes releases the interpreter lock around every call)."""
+    import threading
+    lib = he.load()
+    out = np.zeros(1, dtype=np.uint64)
+    op = out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+    start = threading.Barrier(2)
+    wrong = []
+
+    def worker(kind):
+        buf = ctypes.create_string_buffer(256)
+        h = ctypes.c_void_p()
+        start.wait()
+        for _ in range(2000):
+            if kind == 0:
+                assert lib.he_ntt_tables_create(3000, 1, op, ctypes.byref(h)) == he.HE_EINVAL
+                want = b"power of two"
+            else:
+                assert lib.he_primes_generate(61, 8192, 1, None, 0, op) == he.HE_EINVAL
+                want = b"bits must be"
+            lib.he_last_error(buf, 256)
+            if want not in buf.value:
+                wrong.append((kind, buf.value))
+
+    ts = [threading.Thread(target=worker, args=(k,)) for k in (0, 1)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    assert not wrong, wrong[:3]
