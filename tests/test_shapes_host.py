@@ -2,7 +2,7 @@
 work: he_ntt_shapes and he_ntt_set_shape are host calls). For every degree
 2^10 .. 2^16: the default comes first, every listed shape is a valid split
 of the transform (blocks of at most N words, clusters of 1 to 16 CTAs,
-radix-8 or radix-16 register rounds, 256 threads or fewer per CTA), every
+radix-8 or radix-16 register rounds, at most 1024 threads per CTA), every
 listed shape is accepted for either direction and both launch forms, a shape
 that is not listed is refused with HE_EUNSUPPORTED, and the all-zero call
 restores the default. The shapes themselves are checked against the oracle
